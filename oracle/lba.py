@@ -1,0 +1,141 @@
+"""Linear analysis and linearized buckling analysis (exact and multilevel).
+
+  linear_analysis       Algorithm 1 step 2 (LA): u = K[x]^{-1} f, compliance J = f^T u.
+  buckling_pencil       Algorithm 1 step 4 (EA) / Sec. 2.1 step 1: the q lowest positive load factors
+                        of (K + lambda G) phi = 0 (eq. eigenvalueProblem0), modes normalised as
+                        phi_i^T K phi_j = delta_ij (Sec. 2).
+  exact_lba             Algorithm 1 on the fine grid.
+  multilevel_lba        Sec. 2.1 steps 1-4 (Algorithm 2 without the optional per-level smoothing):
+                        Galerkin K^l, G^l; coarse eigenpairs; prolongation Psi^j = I^j_{j+1} Psi^{j+1};
+                        fine solve K Phi~ = G Psi (eq. FineScaleBVP); Rayleigh quotients (eq. FineScaleRQ).
+
+All vectors returned on the full DOF set (zeros at fixed DOFs).  Readings of the paper used here:
+only positive load factors are kept (negative ones belong to the reversed load); modes are scaled
+to phi^T K phi = 1 and signed so that their entry of largest magnitude is positive; the fine-grid
+load factors are per-column Rayleigh quotients, re-sorted ascending.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import assembly, transfer
+
+
+class Problem:
+    """Oracle view of a synthetic.Problem: assembled operators on the free DOFs."""
+
+    def __init__(self, prob):
+        self.p = prob
+        self.dim = prob.dim
+        self.nel = prob.nel
+        self.fixed = np.asarray(prob.fixed, dtype=np.uint8)
+        self.free = np.flatnonzero(self.fixed == 0)
+        self.n = prob.num_dofs
+        self.K = assembly.assemble_K(prob.nel, prob.dim, prob.x, prob.nu, prob.penal, prob.E0, prob.Emin)
+        self.Kf = assembly.restrict_free(self.K, self.fixed)
+        self._lu = None
+
+    def solve(self, B: np.ndarray) -> np.ndarray:
+        """K_ff^{-1} B on free DOFs by sparse LU (SuperLU)."""
+        if self._lu is None:
+            self._lu = spla.splu(self.Kf.tocsc())
+        return self._lu.solve(np.asarray(B, dtype=np.float64))
+
+    def to_full(self, vf: np.ndarray) -> np.ndarray:
+        shape = (self.n,) + vf.shape[1:]
+        out = np.zeros(shape)
+        out[self.free] = vf
+        return out
+
+    def G(self, u: np.ndarray) -> sp.csr_matrix:
+        p = self.p
+        return assembly.assemble_G(p.nel, p.dim, p.x, u, p.nu, p.penal, p.E0, p.Emin)
+
+
+def linear_analysis(op: Problem):
+    """Algorithm 1 step 2: u = K^{-1} f (direct), J = f^T u."""
+    f = np.asarray(op.p.f, dtype=np.float64)
+    u = op.to_full(op.solve(f[op.free]))
+    return u, float(f @ u)
+
+
+def _normalise_modes(Kf, Phi):
+    """Scale to phi^T K phi = 1 (Sec. 2) and fix the sign (largest-magnitude entry positive)."""
+    Phi = np.array(Phi, dtype=np.float64, copy=True)
+    for i in range(Phi.shape[1]):
+        c = Phi[:, i]
+        c /= np.sqrt(c @ (Kf @ c))
+        if c[np.argmax(np.abs(c))] < 0:
+            c *= -1.0
+        Phi[:, i] = c
+    return Phi
+
+
+def buckling_pencil(Kf, Gf, q: int, dense_limit: int = 4000):
+    """q lowest positive lambda of (K + lambda G) phi = 0 on free DOFs.
+
+    With mu = 1/lambda the pencil is -G phi = mu K phi (K SPD); the q largest positive mu give the q
+    smallest positive lambda.  Dense generalized eigh for small systems, otherwise ARPACK Lanczos
+    on the same pencil (which='LA', tight tolerance).  Returns (lambda [q] ascending, Phi [nf, q])."""
+    n = Kf.shape[0]
+    if n <= dense_limit:
+        mu, V = sla.eigh(-Gf.toarray(), Kf.toarray())
+    else:
+        k = min(n - 2, q + 10)
+        mu, V = spla.eigsh(-Gf.tocsc(), k=k, M=Kf.tocsc(), which="LA", tol=1e-14,
+                           ncv=min(n - 1, max(4 * k, 60)))
+    pos = np.flatnonzero(mu > 0)
+    order = pos[np.argsort(-mu[pos])][:q]
+    if order.size < q:
+        raise RuntimeError("fewer than q positive buckling load factors found")
+    lam = 1.0 / mu[order]
+    return lam, _normalise_modes(Kf, V[:, order])
+
+
+def exact_lba(op: Problem, u: np.ndarray, q: int, dense_limit: int = 4000):
+    """Algorithm 1 on the fine grid: (lambda_i, phi_i), i = 1..q, phi full-length."""
+    G = op.G(u)
+    Gf = assembly.restrict_free(G, op.fixed)
+    lam, Phi = buckling_pencil(op.Kf, Gf, q, dense_limit)
+    return lam, op.to_full(Phi), Gf
+
+
+def galerkin_levels(op: Problem, Gf, eig_level: int):
+    """K^l = P^T ... K ... P and G^l likewise (Sec. 2.1 step 1; Algorithm 2 'restrict'), with the
+    chain of free interpolations from level eig_level up to level 1."""
+    nels, fixeds, Ps = transfer.hierarchy(op.nel, op.dim, op.fixed, eig_level)
+    Kl, Gl = op.Kf, Gf
+    for P in Ps:
+        Kl = (P.T @ Kl @ P).tocsr()
+        Gl = (P.T @ Gl @ P).tocsr()
+    return Kl, Gl, Ps, nels, fixeds
+
+
+def multilevel_lba(op: Problem, u: np.ndarray, q: int, eig_level: int, dense_limit: int = 4000):
+    """Sec. 2.1 steps 1-4.  Returns dict with the fine pairs (lam, Phi), the coarse eigenpairs
+    (lam_coarse, Psi_coarse on level eig_level free DOFs) and the prolongated Psi (fine, full)."""
+    G = op.G(u)
+    Gf = assembly.restrict_free(G, op.fixed)
+    Kl, Gl, Ps, nels, fixeds = galerkin_levels(op, Gf, eig_level)
+    lam_c, Psi_c = buckling_pencil(Kl, Gl, q, dense_limit)          # step 1
+    Psi = Psi_c
+    for P in reversed(Ps):                                           # step 2
+        Psi = P @ Psi
+    Phi = op.solve(Gf @ Psi)                                         # step 3
+    num = np.einsum("ij,ij->j", Phi, op.Kf @ Phi)
+    den = np.einsum("ij,ij->j", Phi, Gf @ Phi)
+    lam = -num / den                                                 # step 4
+    order = np.argsort(lam)
+    lam = lam[order]
+    Phi = _normalise_modes(op.Kf, Phi[:, order])
+    return dict(lam=lam, Phi=op.to_full(Phi), lam_coarse=lam_c, Psi_coarse=Psi_c,
+                Psi=op.to_full(Psi), Gf=Gf, Kl=Kl, Gl=Gl, fixed_levels=fixeds, nels=nels)
+
+
+def eig_residual(Kf, Gf, lam, phi_free):
+    """||(K + lambda G) phi|| / ||K phi||, the residual measure of eq. eigResidual."""
+    Kp = Kf @ phi_free
+    return float(np.linalg.norm(Kp + lam * (Gf @ phi_free)) / np.linalg.norm(Kp))
