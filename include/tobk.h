@@ -1,0 +1,177 @@
+/*
+ * tobk.h — C-ABI of the GB300 multilevel linearized-buckling solver library (libtobk.so).
+ *
+ * The library implements, with hand-written CUDA kernels for sm_103a, the solver path of the
+ * multilevel buckling method of Ferrari & Sigmund ("Towards solving large-scale topology
+ * optimization problems with buckling constraints at the cost of linear analyses",
+ * arXiv 1909.13585):
+ *   - the linear analysis (LA) K[x] u = f by multigrid-preconditioned CG (Algorithm 1, step 2;
+ *     Appendix A "mgPCG"),
+ *   - the stress stiffness G[x, u] (Sec. 2),
+ *   - the buckling load factors and modes, either exactly on the fine grid (Algorithm 1, EA) or by
+ *     the multilevel procedure of Sec. 2.1 (coarse Galerkin eigenproblem, prolongation, one fine
+ *     block solve K Phi = G Psi, Rayleigh quotients),
+ *   - the adjoint systems K z_i = phi_i^T (grad_u G) phi_i and the sensitivities of the load factors
+ *     and of the compliance (Sec. 2, eq. SensitivityLambda / AdjointSystem).
+ *
+ * Problem model.  A structured grid of nel[0] x nel[1] (x nel[2]) unit elements: bilinear Q4 in plane
+ * stress (dim = 2, unit thickness) or trilinear H8 (dim = 3), unit element size, Young's modulus
+ * interpolated per element by SIMP (Sec. 2): E_kappa = Emin + x^p (E0 - Emin) for K and
+ * E_sigma = x^p E0 for G.
+ *
+ * Layouts (all arrays FP64 unless stated):
+ *   element (i,j,k) has index e = i + nel[0] * (j + nel[1] * k)                       [m elements]
+ *   node    (i,j,k) has index a = i + (nel[0]+1) * (j + (nel[1]+1) * k)
+ *   DOF c of node a is dim * a + c (node-interleaved)                                   [n DOFs]
+ *   blocks of vectors are stored vector after vector ([count][n]).
+ * Dirichlet DOFs are given by a byte mask (1 = fixed, u = 0); every vector the library returns is
+ * zero at fixed DOFs.
+ *
+ * Ownership and calling conventions.  The caller owns every buffer it passes; "on_device" flags say
+ * whether a pointer is a device pointer (the handle's device) or host memory.  The library owns its
+ * internal device memory (one allocation per handle, made by tobk_create).  All work is issued on the
+ * CUDA stream given to tobk_create; functions return after their results are available to the caller
+ * (host outputs are copied, device outputs are complete on that stream).  No C++ exception crosses
+ * this interface.  Every function returns a tobk_status; on failure tobk_last_error() gives a
+ * message.  Calls must follow the order of the method: set densities, load and fixed DOFs ->
+ * solve_equilibrium -> compute_buckling -> compute_sensitivities; otherwise TOBK_E_STATE.
+ * A handle must not be used from two threads at once.
+ */
+#ifndef TOBK_H_
+#define TOBK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TOBK_OK = 0,
+  TOBK_E_ARG = 1,            /* invalid argument (sizes, NaN/out-of-range densities, null pointers) */
+  TOBK_E_STATE = 2,          /* call out of order (e.g. buckling before equilibrium) */
+  TOBK_E_NOMEM = 3,          /* device allocation failed */
+  TOBK_E_CUDA = 4,           /* a CUDA call failed; the message names it */
+  TOBK_E_NOT_CONVERGED = 5,  /* iteration limit reached; outputs hold the last iterate */
+  TOBK_E_BREAKDOWN = 6,      /* CG breakdown (p^T K p <= 0): K not positive definite on the free DOFs */
+  TOBK_E_TIMEOUT = 7,        /* reserved: bounded device wait expired */
+  TOBK_E_NONFINITE = 8       /* a NaN/Inf appeared in an iterate */
+} tobk_status;
+
+typedef enum {
+  TOBK_FP64 = 0,             /* every multigrid operation in FP64 (plain mgPCG) */
+  TOBK_FP32_VCYCLE = 1       /* V-cycle (smoother, transfers, coarse matvecs) in FP32 storage and
+                                arithmetic as the preconditioner of FP64 flexible CG; the coarsest
+                                dense solve, residuals, dot products and updates stay FP64 */
+} tobk_precision;
+
+typedef enum {
+  TOBK_FIELD_U = 0,          /* displacement u [n] */
+  TOBK_FIELD_MODES = 1,      /* buckling modes [q][n], phi_i^T K phi_j = delta_ij */
+  TOBK_FIELD_ADJOINT = 2,    /* adjoint solutions z_i [q][n] */
+  TOBK_FIELD_ADJOINT_RHS = 3 /* adjoint right-hand sides phi_i^T (grad_u G) phi_i [q][n] */
+} tobk_field;
+
+typedef struct {
+  int dim;           /* 2 (Q4 plane stress) or 3 (H8) */
+  int nel[3];        /* elements per axis; nel[2] ignored in 2D.  Each axis divisible by 2^(mg_levels-1) */
+  double nu;         /* Poisson ratio (0.3 in the paper, Sec. 2) */
+  double E0;         /* solid Young's modulus (paper's E_1) */
+  double Emin;       /* void modulus of the stiffness interpolation (paper's E_0; E1/E0 = 1e6) */
+  double penal;      /* SIMP exponent p */
+  int mg_levels;     /* multigrid levels (1 = fine grid only; the coarsest level is solved densely,
+                        at most 6000 DOFs) */
+  int eig_level;     /* 1-based level of the buckling eigenproblem: 1 = exact LBA on the fine grid
+                        (Algorithm 1), l > 1 = multilevel procedure of Sec. 2.1 with Omega_l */
+  int num_modes;     /* q, number of buckling modes / load factors (<= 48) */
+  int precision;     /* tobk_precision of the V-cycle */
+  double rtol;       /* CG stop: ||f - K u||_2 / ||f||_2 <= rtol over free DOFs (e.g. 1e-8) */
+  int max_iter;      /* CG iteration limit per solve */
+  double omega;      /* damped-Jacobi weight (e.g. 0.6) */
+  int nu_pre;        /* pre-smoothing sweeps per level (>= 1) */
+  int nu_post;       /* post-smoothing sweeps per level */
+  double eig_tol;    /* eigenpair residual ||(K + lam G) phi|| / ||K phi|| target (1e-8, Appendix A) */
+  int eig_max_iter;  /* outer iterations of the block eigensolver */
+  int max_rhs;       /* largest multi-RHS block the caller will pass to tobk_solve (>= 1) */
+} tobk_desc;
+
+typedef struct {
+  int iterations;        /* CG iterations (max over RHS) or eigensolver outer iterations */
+  int converged;         /* 1 if every RHS / eigenpair met its tolerance */
+  int num_rhs;           /* right-hand sides solved in the call */
+  double rel_residual;   /* max over RHS of the true relative residual recomputed at exit, or the
+                            max eigen-residual */
+  double time_ms;        /* device time of the call */
+  int status_detail;     /* implementation detail code (0 = none) */
+} tobk_solve_info;
+
+typedef struct tobk_handle tobk_handle;
+
+/* Fills *desc with defaults: nu 0.3, E0 1, Emin 1e-6, p 3, 3 levels, eig_level 1, 6 modes, FP64,
+ * rtol 1e-8, max_iter 500, omega 0.6, nu_pre = nu_post = 2, eig_tol 1e-8, eig_max_iter 200,
+ * max_rhs = num_modes + 4.  Returns TOBK_OK. */
+int tobk_default_desc(tobk_desc* desc);
+
+/* Creates a handle on the current CUDA device and the given stream (cudaStream_t; NULL = legacy
+ * default stream).  Allocates all device memory the problem needs.  Errors: TOBK_E_ARG for
+ * inconsistent sizes, TOBK_E_NOMEM, TOBK_E_CUDA. */
+int tobk_create(const tobk_desc* desc, void* cuda_stream, tobk_handle** out);
+void tobk_destroy(tobk_handle* h);
+/* Message of the last failed call on h (or of the last failed tobk_create when h is NULL). */
+const char* tobk_last_error(const tobk_handle* h);
+
+/* Physical densities x [m], each finite and in [0, 1] (Sec. 2 design field after filtering and
+ * projection).  Builds the multigrid hierarchy: SIMP moduli, Galerkin coarse operators
+ * K^{j+1} = I^T K^j I (Sec. 2.1 step 1), Jacobi diagonals and the coarsest dense inverse. */
+int tobk_set_densities(tobk_handle* h, const double* x, int64_t m, int on_device);
+/* Reference load vector f [n] (Algorithm 1, step 1).  Entries at fixed DOFs are ignored. */
+int tobk_set_load(tobk_handle* h, const double* f, int64_t n, int on_device);
+/* Dirichlet mask [n] (uint8, 1 = fixed).  Coarse levels fix a DOF when the fine DOF at the
+ * coinciding node is fixed. */
+int tobk_set_fixed(tobk_handle* h, const uint8_t* fixed, int64_t n, int on_device);
+/* Optional initial guess for the next solve_equilibrium (length n; NULL clears it). */
+int tobk_set_initial_guess(tobk_handle* h, const double* u0, int64_t n, int on_device);
+
+/* LA (Algorithm 1 step 2): u = K^{-1} f by mgPCG to desc.rtol; *compliance = f^T u (may be NULL).
+ * Also builds the element stress stiffness G_e = E_sigma G_e0[u_e] (Algorithm 1 step 3). */
+int tobk_solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info);
+
+/* EA: the q lowest positive buckling load factors of (K + lambda G) phi = 0 (eq.
+ * eigenvalueProblem0), ascending, written to lambda [q] (host).  eig_level = 1: exact fine-grid
+ * eigenpairs.  eig_level = l > 1: Sec. 2.1 steps 1-4 (coarse eigenpairs of the Galerkin pencil
+ * (K^l, G^l), prolongation to Omega_1, fine solve K Phi = G Psi, per-column Rayleigh quotients,
+ * re-sorted ascending).  Modes are scaled to phi^T K phi = 1 and signed so that their entry of
+ * largest magnitude is positive. */
+int tobk_compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info);
+
+/* Sensitivities (Sec. 2): dlambda_dx [q][m] and dJ_dx [m] (either may be NULL), with
+ *   d lambda_i / d x_e = -[phi^T K' phi + lambda phi^T G' phi - lambda z^T K' u] / (phi^T G phi),
+ *   K z_i = phi_i^T (grad_u G) phi_i   (eq. AdjointSystem; all q systems in one multi-RHS solve),
+ *   dJ/dx_e = -dE_kappa/dx_e u_e^T K_e0 u_e.
+ * (eq. SensitivityLambda is the bracket; the factor -1/(phi^T G phi) equals lambda under the K
+ * normalisation.)  out_on_device selects device or host output pointers. */
+int tobk_compute_sensitivities(tobk_handle* h, double* dlambda_dx, double* dJ_dx, int out_on_device,
+                               tobk_solve_info* info);
+
+/* Copies a field (tobk_field) to out (len doubles). */
+int tobk_get_field(tobk_handle* h, int which, double* out, int64_t len, int out_on_device);
+
+/* ---- unit-level entry points (device pointers) ------------------------------------------------ */
+/* Element and DOF counts of a 1-based level: out[0..2] = nel, out[3] = n (DOFs), out[4] = m. */
+int tobk_level_info(tobk_handle* h, int level, int64_t* out5);
+/* y = K^level v for nrhs vectors of length n_level (level 1: matrix-free SIMP operator, Sec. 2;
+ * level > 1: Galerkin operator).  Requires densities. */
+int tobk_apply_K(tobk_handle* h, int level, const double* v, double* y, int nrhs);
+/* y = G^level v (requires solve_equilibrium; levels 1..eig_level). */
+int tobk_apply_G(tobk_handle* h, int level, const double* v, double* y, int nrhs);
+/* Multi-RHS mgPCG solve K^level X = B at the given level (nrhs <= desc.max_rhs), X overwritten. */
+int tobk_solve(tobk_handle* h, int level, const double* B, double* X, int nrhs, tobk_solve_info* info);
+/* Copies the stored Galerkin element matrices of a coarse level (which: 0 = K, 1 = G) to out
+ * [m_level][nd*nd] (device pointer), nd = dim * 2^dim. */
+int tobk_get_element_matrices(tobk_handle* h, int level, int which, double* out, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOBK_H_ */

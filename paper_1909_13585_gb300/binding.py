@@ -1,0 +1,235 @@
+"""ctypes binding of libtobk.so: the C-ABI of include/tobk.h, one Python function per C entry point
+with the same name, plus `Solver`, a thin owner of a handle that marshals numpy arrays and torch
+tensors (device pointers, stream) into those calls.  No computation happens here: every step of the
+solver runs in the library's CUDA kernels.  Importing fails loudly if the library is missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtobk.so")
+
+TOBK_OK, TOBK_E_ARG, TOBK_E_STATE, TOBK_E_NOMEM, TOBK_E_CUDA, TOBK_E_NOT_CONVERGED, \
+    TOBK_E_BREAKDOWN, TOBK_E_TIMEOUT, TOBK_E_NONFINITE = range(9)
+TOBK_FP64, TOBK_FP32_VCYCLE = 0, 1
+TOBK_FIELD_U, TOBK_FIELD_MODES, TOBK_FIELD_ADJOINT, TOBK_FIELD_ADJOINT_RHS = range(4)
+
+
+class tobk_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nel", C.c_int * 3), ("nu", C.c_double), ("E0", C.c_double),
+                ("Emin", C.c_double), ("penal", C.c_double), ("mg_levels", C.c_int),
+                ("eig_level", C.c_int), ("num_modes", C.c_int), ("precision", C.c_int),
+                ("rtol", C.c_double), ("max_iter", C.c_int), ("omega", C.c_double),
+                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("eig_tol", C.c_double),
+                ("eig_max_iter", C.c_int), ("max_rhs", C.c_int)]
+
+
+class tobk_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("num_rhs", C.c_int),
+                ("rel_residual", C.c_double), ("time_ms", C.c_double), ("status_detail", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_H = C.c_void_p
+_P = C.c_void_p
+_SIGS = {
+    "tobk_default_desc": (C.c_int, [C.POINTER(tobk_desc)]),
+    "tobk_create": (C.c_int, [C.POINTER(tobk_desc), C.c_void_p, C.POINTER(_H)]),
+    "tobk_destroy": (None, [_H]),
+    "tobk_last_error": (C.c_char_p, [_H]),
+    "tobk_set_densities": (C.c_int, [_H, _P, C.c_int64, C.c_int]),
+    "tobk_set_load": (C.c_int, [_H, _P, C.c_int64, C.c_int]),
+    "tobk_set_fixed": (C.c_int, [_H, _P, C.c_int64, C.c_int]),
+    "tobk_set_initial_guess": (C.c_int, [_H, _P, C.c_int64, C.c_int]),
+    "tobk_solve_equilibrium": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(tobk_solve_info)]),
+    "tobk_compute_buckling": (C.c_int, [_H, _P, C.POINTER(tobk_solve_info)]),
+    "tobk_compute_sensitivities": (C.c_int, [_H, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
+    "tobk_get_field": (C.c_int, [_H, C.c_int, _P, C.c_int64, C.c_int]),
+    "tobk_level_info": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int64)]),
+    "tobk_apply_K": (C.c_int, [_H, C.c_int, _P, _P, C.c_int]),
+    "tobk_apply_G": (C.c_int, [_H, C.c_int, _P, _P, C.c_int]),
+    "tobk_solve": (C.c_int, [_H, C.c_int, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
+    "tobk_get_element_matrices": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int64]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libtobk.so and declares every entry point; raises if the library was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtobk.so not found at {path}: run __graft_entry__.build() or "
+                           "python -m paper_1909_13585_gb300.build")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TobkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tobk error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+class Solver:
+    """Owner of one tobk handle.  Arrays may be numpy (host) or torch tensors (host or device).
+
+    `problem` is any object with dim, nel, nu, E0, Emin, penal, mg_levels, eig_level, num_modes,
+    x, f, fixed (e.g. synthetic.Problem)."""
+
+    def __init__(self, problem=None, *, stream=None, precision=TOBK_FP64, rtol=1e-8, max_iter=500,
+                 omega=0.6, nu_pre=2, nu_post=2, eig_tol=1e-8, eig_max_iter=200, max_rhs=None,
+                 desc=None, **overrides):
+        self.lib = load()
+        d = tobk_desc()
+        self.lib.tobk_default_desc(C.byref(d))
+        if problem is not None:
+            d.dim = problem.dim
+            d.nel[0], d.nel[1] = problem.nel[0], problem.nel[1]
+            d.nel[2] = problem.nel[2] if problem.dim == 3 else 1
+            d.nu, d.E0, d.Emin, d.penal = problem.nu, problem.E0, problem.Emin, problem.penal
+            d.mg_levels, d.eig_level, d.num_modes = problem.mg_levels, problem.eig_level, problem.num_modes
+        d.precision, d.rtol, d.max_iter, d.omega = precision, rtol, max_iter, omega
+        d.nu_pre, d.nu_post, d.eig_tol, d.eig_max_iter = nu_pre, nu_post, eig_tol, eig_max_iter
+        d.max_rhs = max_rhs if max_rhs is not None else d.num_modes + 4
+        for k, v in overrides.items():
+            setattr(d, k, v)
+        if desc is not None:
+            d = desc
+        self.desc = d
+        h = _H()
+        s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = self.lib.tobk_create(C.byref(d), C.c_void_p(s), C.byref(h))
+        if rc != TOBK_OK:
+            raise TobkError(rc, self.lib.tobk_last_error(None).decode())
+        self.h = h
+        self.dim = d.dim
+        self.q = d.num_modes
+        info = (C.c_int64 * 5)()
+        self.lib.tobk_level_info(self.h, 1, info)
+        self.n, self.m = int(info[3]), int(info[4])
+        if problem is not None:
+            self.set_problem(problem)
+
+    # -- lifetime --------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tobk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != TOBK_OK and rc not in allow:
+            raise TobkError(rc, self.lib.tobk_last_error(self.h).decode())
+        return rc
+
+    # -- inputs ----------------------------------------------------------------------------------
+    def set_problem(self, p):
+        self.set_fixed(np.ascontiguousarray(p.fixed, dtype=np.uint8))
+        self.set_load(np.ascontiguousarray(p.f, dtype=np.float64))
+        self.set_densities(np.ascontiguousarray(p.x, dtype=np.float64))
+
+    def set_densities(self, x):
+        ptr, dev = _ptr(x)
+        self._check(self.lib.tobk_set_densities(self.h, ptr, self.m, dev))
+
+    def set_load(self, f):
+        ptr, dev = _ptr(f)
+        self._check(self.lib.tobk_set_load(self.h, ptr, self.n, dev))
+
+    def set_fixed(self, fixed):
+        ptr, dev = _ptr(fixed)
+        self._check(self.lib.tobk_set_fixed(self.h, ptr, self.n, dev))
+
+    def set_initial_guess(self, u0):
+        if u0 is None:
+            self._check(self.lib.tobk_set_initial_guess(self.h, None, 0, 0))
+            return
+        ptr, dev = _ptr(u0)
+        self._check(self.lib.tobk_set_initial_guess(self.h, ptr, self.n, dev))
+
+    # -- the method ------------------------------------------------------------------------------
+    def solve_equilibrium(self, allow_not_converged=False):
+        J = C.c_double()
+        info = tobk_solve_info()
+        self._check(self.lib.tobk_solve_equilibrium(self.h, C.byref(J), C.byref(info)),
+                    (TOBK_E_NOT_CONVERGED,) if allow_not_converged else ())
+        return J.value, info.as_dict()
+
+    def compute_buckling(self):
+        lam = np.zeros(self.q)
+        info = tobk_solve_info()
+        self._check(self.lib.tobk_compute_buckling(self.h, lam.ctypes.data, C.byref(info)))
+        return lam, info.as_dict()
+
+    def compute_sensitivities(self, dlam=None, dJ=None):
+        if dlam is None:
+            dlam = np.zeros((self.q, self.m))
+        if dJ is None:
+            dJ = np.zeros(self.m)
+        p1, d1 = _ptr(dlam)
+        p2, d2 = _ptr(dJ)
+        assert d1 == d2
+        info = tobk_solve_info()
+        self._check(self.lib.tobk_compute_sensitivities(self.h, p1, p2, d1, C.byref(info)))
+        return dlam, dJ, info.as_dict()
+
+    def get_field(self, which, out=None):
+        size = self.n if which == TOBK_FIELD_U else self.q * self.n
+        if out is None:
+            out = np.zeros(size)
+        ptr, dev = _ptr(out)
+        self._check(self.lib.tobk_get_field(self.h, which, ptr, size, dev))
+        return out
+
+    # -- unit level (device tensors) -------------------------------------------------------------
+    def level_info(self, level):
+        info = (C.c_int64 * 5)()
+        self._check(self.lib.tobk_level_info(self.h, level, info))
+        return dict(nel=tuple(int(v) for v in info[:3]), n=int(info[3]), m=int(info[4]))
+
+    def apply_K(self, level, v, y, nrhs=1):
+        self._check(self.lib.tobk_apply_K(self.h, level, v.data_ptr(), y.data_ptr(), nrhs))
+
+    def apply_G(self, level, v, y, nrhs=1):
+        self._check(self.lib.tobk_apply_G(self.h, level, v.data_ptr(), y.data_ptr(), nrhs))
+
+    def solve(self, level, B, X, nrhs=1, allow_not_converged=False):
+        info = tobk_solve_info()
+        self._check(self.lib.tobk_solve(self.h, level, B.data_ptr(), X.data_ptr(), nrhs, C.byref(info)),
+                    (TOBK_E_NOT_CONVERGED,) if allow_not_converged else ())
+        return info.as_dict()
+
+    def element_matrices(self, level, which, out):
+        self._check(self.lib.tobk_get_element_matrices(self.h, level, which, out.data_ptr(), out.numel()))
+        return out

@@ -1,0 +1,90 @@
+// The solver handle behind the opaque tobk_handle* of the C-ABI, and the host-side entry points that
+// the C-ABI functions call.  One handle = one structured-grid problem on one CUDA stream.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tobk.h"
+#include "kernels.h"
+#include "tobk_internal.cuh"
+
+struct tobk_handle {
+  tobk_desc desc{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int dim = 2;
+  int L = 1;                 // multigrid levels
+  int eig = 0;               // 0-based level of the coarse eigenproblem
+  int q = 1;                 // modes
+  int rmax = 1;              // RHS capacity of the multi-RHS solver
+  tobk::ElementTables tab;
+  tobk::Arena arena;
+  tobk::Level lv[tobk::kMaxLevels];
+
+  // device tables
+  double* d_Ke0 = nullptr;   // [nd*nd]
+  double* d_W = nullptr;     // [2^d][nn][nn]
+  double* d_dN = nullptr;    // [ngp][d][nn]
+  double* d_D = nullptr;     // [nv][nv]
+  // fine-level design fields
+  double *x = nullptr, *Ek = nullptr, *Es = nullptr, *dEk = nullptr, *dEs = nullptr;
+  float* Ek32 = nullptr;
+  double *f = nullptr, *u = nullptr, *u0 = nullptr;
+  double *Gs0 = nullptr, *Gs = nullptr;  // [m][nn*nn] stress stiffness (unit modulus / with E_sigma)
+  // coarsest dense inverse
+  double *Adense = nullptr, *Awork = nullptr, *Ainv = nullptr;
+  // multi-RHS CG work (sized for the fine level)
+  tobk::CGWork cg{};
+  double* bwork = nullptr;   // [rmax][n] right-hand-side staging
+  double* xwork = nullptr;   // [rmax][n]
+  // buckling / sensitivity outputs
+  double* modes = nullptr;   // [q][n] fine-grid modes (K-normalised)
+  double* lam = nullptr;     // [q] device
+  double* adj = nullptr;     // [q][n] adjoint solutions
+  double* adj_rhs = nullptr; // [q][n]
+  double* dlam = nullptr;    // [q][m]
+  double* dJ = nullptr;      // [m]
+  double* esens = nullptr;   // [m][...] element scratch for adjoint RHS (Gauss-point vectors)
+  // eigen workspace at the eigen level
+  int eig_nb = 0, eig_mmax = 0;
+  double *V = nullptr, *KV = nullptr, *GV = nullptr, *EW = nullptr, *EKW = nullptr, *EGW = nullptr;
+  double *Hs = nullptr, *Bs = nullptr, *Ys = nullptr, *Cs = nullptr, *gram_partial = nullptr;
+  double* small_host = nullptr;  // pinned
+  // small scalars
+  double* dscal = nullptr;       // device scratch scalars [256]
+  double* hscal = nullptr;       // pinned host scratch [256]
+
+  double compliance = 0.0;
+  double lam_host[64];
+  bool have_x = false, have_f = false, have_fixed = false, setup_done = false, have_u = false,
+       have_G = false, have_modes = false, have_sens = false, have_u0 = false;
+  std::string err;
+};
+
+namespace tobk {
+
+int create_handle(const tobk_desc* desc, void* stream, tobk_handle** out);
+void destroy_handle(tobk_handle* h);
+int set_densities(tobk_handle* h, const double* x, bool on_device);
+int set_load(tobk_handle* h, const double* f, bool on_device);
+int set_fixed(tobk_handle* h, const uint8_t* fixed, bool on_device);
+int setup_hierarchy(tobk_handle* h);
+LevelOpDesc level_op(tobk_handle* h, int j);
+// Multi-RHS MGCG solve at level s (0-based): K_s X = B, nr RHS (device, [nr][n_s]).
+int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
+              int precision, tobk_solve_info* info);
+int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info);
+int setup_stress(tobk_handle* h);  // Gs from u, Galerkin G down to the eigen level
+int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info);
+int compute_sensitivities(tobk_handle* h, double* dlam, double* dJ, bool out_on_device, tobk_solve_info* info);
+// eigensolver at level j: q lowest positive load factors, modes K_j-normalised -> out [q][n_j]
+int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info);
+// G_j v at level j (fine: matrix-free from Gs; coarse: Galerkin Ge)
+void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
+void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
+int fail(tobk_handle* h, int code, const std::string& msg);
+int check_cuda(tobk_handle* h, const char* where);
+
+}  // namespace tobk

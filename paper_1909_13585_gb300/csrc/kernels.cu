@@ -1,0 +1,1083 @@
+// CUDA kernels of the multilevel buckling solver (sm_103a).
+//
+// Paper mapping (Ferrari & Sigmund, arXiv 1909.13585):
+//   SIMP moduli E_kappa, E_sigma ........................ Sec. 2, eq. interpolationSIMP2-SIMP
+//   K(x) v matrix-free (K_e = E_kappa K_e0) ............. Sec. 2; LA of Algorithm 1 / Algorithm 2
+//   G(x,u) from Gauss-point stresses (G_e = E_sigma G_e0) Sec. 2
+//   restriction / interpolation, Galerkin K^l, G^l ...... Sec. 2.1 step 1-2, Algorithm 2 'restrict'
+//   damped Jacobi smoother, coarsest dense solve ........ the multigrid preconditioner of the
+//                                                         mgPCG solves (Appendix A)
+//   PCG / flexible CG recurrences ........................ Appendix A (mgPCG / mgBPCG)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace tobk {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t count, int threads = kThreads) {
+  return (unsigned)((count + threads - 1) / threads);
+}
+
+template <int DIM, typename T>
+FineOp<DIM, T> make_fine(const LevelOpDesc& d, const T* scale) {
+  FineOp<DIM, T> op;
+  op.g = d.g;
+  op.scale_e = scale;
+  op.fixed = d.fixed;
+  constexpr int ND = Dims<DIM>::ND;
+  for (int i = 0; i < ND * ND; ++i) op.M[i] = (T)d.T0[i];
+  return op;
+}
+
+template <int DIM, typename T>
+StoredOp<DIM, T> make_stored(const LevelOpDesc& d, const T* Ke) {
+  StoredOp<DIM, T> op;
+  op.g = d.g;
+  op.Ke = Ke;
+  op.fixed = d.fixed;
+  return op;
+}
+
+}  // namespace
+
+// ================================================================================================
+// level operators
+// ================================================================================================
+template <int DIM, class Op, typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_apply(const __grid_constant__ Op op, const T* __restrict__ v, const T* __restrict__ b,
+                                                     const T* __restrict__ dinv, T* __restrict__ y, T omega,
+                                                     int64_t stride) {
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!node_coords(op.g, node, i, j, k)) return;
+  const int64_t off = (int64_t)blockIdx.y * stride;
+  v += off;
+  y += off;
+  if (MODE != APPLY_KV) b += off;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+  gather_rows<DIM, T>(op, i, j, k, LoadVec<T>{v}, acc);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t idx = DIM * node + c;
+    T out;
+    if (op.fixed[idx]) {
+      out = T(0);
+    } else if (MODE == APPLY_KV) {
+      out = acc[c];
+    } else if (MODE == APPLY_RES) {
+      out = b[idx] - acc[c];
+    } else {
+      out = v[idx] + omega * dinv[idx] * (b[idx] - acc[c]);
+    }
+    y[idx] = out;
+  }
+}
+
+template <int DIM, class Op, typename T>
+void apply_dispatch(const Op& op, int mode, const T* v, const T* b, const T* dinv, T* y, T omega, int nr,
+                    int64_t stride, cudaStream_t s) {
+  dim3 grid(blocks_for(op.g.nnode), nr);
+  if (mode == APPLY_KV)
+    k_apply<DIM, Op, T, APPLY_KV><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride);
+  else if (mode == APPLY_RES)
+    k_apply<DIM, Op, T, APPLY_RES><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride);
+  else
+    k_apply<DIM, Op, T, APPLY_JAC><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride);
+}
+
+template <int DIM>
+void apply_dim(const LevelOpDesc& d, int mode, const double* v, const double* b, const double* dinv, double* y,
+               double omega, int nr, int64_t stride, cudaStream_t s) {
+  if (d.stored)
+    apply_dispatch<DIM>(make_stored<DIM, double>(d, d.Ke64), mode, v, b, dinv, y, omega, nr, stride, s);
+  else
+    apply_dispatch<DIM>(make_fine<DIM, double>(d, d.scale64), mode, v, b, dinv, y, omega, nr, stride, s);
+}
+
+template <int DIM>
+void apply_dim32(const LevelOpDesc& d, int mode, const float* v, const float* b, const float* dinv, float* y,
+                 float omega, int nr, int64_t stride, cudaStream_t s) {
+  if (d.stored)
+    apply_dispatch<DIM>(make_stored<DIM, float>(d, d.Ke32), mode, v, b, dinv, y, omega, nr, stride, s);
+  else
+    apply_dispatch<DIM>(make_fine<DIM, float>(d, d.scale32), mode, v, b, dinv, y, omega, nr, stride, s);
+}
+
+void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double* b, const double* dinv,
+                  double* y, double omega, int nr, int64_t stride, cudaStream_t s) {
+  if (op.g.dim == 2)
+    apply_dim<2>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+  else
+    apply_dim<3>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+}
+
+void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
+                    float* y, float omega, int nr, int64_t stride, cudaStream_t s) {
+  if (op.g.dim == 2)
+    apply_dim32<2>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+  else
+    apply_dim32<3>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+}
+
+// ---- stress stiffness operator (fine level) -----------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_apply_kron(ScalarKronOp<DIM, double> op, const double* __restrict__ v,
+                                                         double* __restrict__ y, int64_t stride) {
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!node_coords(op.g, node, i, j, k)) return;
+  const int64_t off = (int64_t)blockIdx.y * stride;
+  double acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+  gather_rows_kron<DIM, double>(op, i, j, k, LoadVec<double>{v + off}, acc);
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t idx = DIM * node + c;
+    y[off + idx] = op.fixed[idx] ? 0.0 : acc[c];
+  }
+}
+
+void launch_apply_kron(const Grid& g, const uint8_t* fixed, const double* Gs, const double* v, double* y, int nr,
+                       int64_t stride, cudaStream_t s) {
+  dim3 grid(blocks_for(g.nnode), nr);
+  if (g.dim == 2) {
+    ScalarKronOp<2, double> op{g, Gs, fixed};
+    k_apply_kron<2><<<grid, kThreads, 0, s>>>(op, v, y, stride);
+  } else {
+    ScalarKronOp<3, double> op{g, Gs, fixed};
+    k_apply_kron<3><<<grid, kThreads, 0, s>>>(op, v, y, stride);
+  }
+}
+
+// ---- diagonal -----------------------------------------------------------------------------------
+template <int DIM, class Op>
+__global__ void k_diag(const __grid_constant__ Op op, double* dinv, float* dinv32) {
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!node_coords(op.g, node, i, j, k)) return;
+  const Grid& g = op.g;
+  double d[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) d[c] = 0.0;
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const int ei = i - cx, ej = j - cy, ek = k - cz;
+        if (ei < 0 || ei >= g.nel[0] || ej < 0 || ej >= g.nel[1]) continue;
+        if (DIM == 3 && (ek < 0 || ek >= g.nel[2])) continue;
+        const int64_t e = ei + (int64_t)g.nel[0] * (ej + (int64_t)g.nel[1] * ek);
+        const int ln = local_node(cx, cy, cz);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+          d[c] += (double)op.scale(e) * (double)op.entry(e, ln * DIM + c, ln * DIM + c);
+      }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t idx = DIM * node + c;
+    const double v = (op.fixed[idx] || !(d[c] > 0.0)) ? 0.0 : 1.0 / d[c];
+    dinv[idx] = v;
+    if (dinv32) dinv32[idx] = (float)v;
+  }
+}
+
+void launch_diag(const LevelOpDesc& d, double* dinv, float* dinv32, cudaStream_t s) {
+  const unsigned grid = blocks_for(d.g.nnode);
+  if (d.g.dim == 2) {
+    if (d.stored)
+      k_diag<2><<<grid, kThreads, 0, s>>>(make_stored<2, double>(d, d.Ke64), dinv, dinv32);
+    else
+      k_diag<2><<<grid, kThreads, 0, s>>>(make_fine<2, double>(d, d.scale64), dinv, dinv32);
+  } else {
+    if (d.stored)
+      k_diag<3><<<grid, kThreads, 0, s>>>(make_stored<3, double>(d, d.Ke64), dinv, dinv32);
+    else
+      k_diag<3><<<grid, kThreads, 0, s>>>(make_fine<3, double>(d, d.scale64), dinv, dinv32);
+  }
+}
+
+// ---- first Jacobi sweep from zero --------------------------------------------------------------
+template <typename T>
+__global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ z, T omega,
+                          int64_t n, int64_t stride) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t off = (int64_t)blockIdx.y * stride;
+  z[off + i] = omega * dinv[i] * b[off + i];
+}
+
+void launch_jacobi0(const double* b, const double* dinv, double* z, double omega, int64_t n, int nr,
+                    int64_t stride, cudaStream_t s) {
+  k_jacobi0<double><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride);
+}
+void launch_jacobi0_32(const float* b, const float* dinv, float* z, float omega, int64_t n, int nr, int64_t stride,
+                       cudaStream_t s) {
+  k_jacobi0<float><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride);
+}
+
+// ---- transfers ----------------------------------------------------------------------------------
+// Interpolation weights of nested 2:1 grids: fine node f and coarse node C along one axis are
+// coupled with weight 1 when f = 2C and 1/2 when |f - 2C| = 1.
+template <int DIM, typename T>
+__global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c, const T* __restrict__ rf,
+                           T* __restrict__ bc, int64_t sf, int64_t sc) {
+  const int64_t cn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int I, J, K;
+  if (!node_coords(gc, cn, I, J, K)) return;
+  rf += (int64_t)blockIdx.y * sf;
+  bc += (int64_t)blockIdx.y * sc;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    const int fk = 2 * K + dz;
+    if (DIM == 3 && (fk < 0 || fk >= gf.nn[2])) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int fj = 2 * J + dy;
+      if (fj < 0 || fj >= gf.nn[1]) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int fi = 2 * I + dx;
+        if (fi < 0 || fi >= gf.nn[0]) continue;
+        const T w = T((dx == 0 ? 1.0 : 0.5) * (dy == 0 ? 1.0 : 0.5) * (dz == 0 ? 1.0 : 0.5));
+        const int64_t fn = fi + (int64_t)gf.nn[0] * (fj + (int64_t)gf.nn[1] * (DIM == 3 ? fk : 0));
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += w * rf[DIM * fn + c];
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t idx = DIM * cn + c;
+    bc[idx] = fixed_c[idx] ? T(0) : acc[c];
+  }
+}
+
+template <int DIM, typename T>
+__global__ void k_prolong_add(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_f, const T* __restrict__ zc,
+                              T* __restrict__ zf, int64_t sf, int64_t sc) {
+  const int64_t fn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!node_coords(gf, fn, i, j, k)) return;
+  zc += (int64_t)blockIdx.y * sc;
+  zf += (int64_t)blockIdx.y * sf;
+  const int ix0 = i >> 1, ix1 = (i + 1) >> 1;
+  const int iy0 = j >> 1, iy1 = (j + 1) >> 1;
+  const int iz0 = k >> 1, iz1 = (k + 1) >> 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1), wz = (k & 1) ? T(0.5) : T(1);
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int bz = 0; bz < (DIM == 3 ? 2 : 1); ++bz) {
+    if (bz == 1 && !(k & 1)) continue;
+    const int K = bz ? iz1 : iz0;
+#pragma unroll
+    for (int by = 0; by < 2; ++by) {
+      if (by == 1 && !(j & 1)) continue;
+      const int J = by ? iy1 : iy0;
+#pragma unroll
+      for (int bx = 0; bx < 2; ++bx) {
+        if (bx == 1 && !(i & 1)) continue;
+        const int I = bx ? ix1 : ix0;
+        const T w = wx * wy * (DIM == 3 ? wz : T(1));
+        const int64_t cn = I + (int64_t)gc.nn[0] * (J + (int64_t)gc.nn[1] * (DIM == 3 ? K : 0));
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += w * zc[DIM * cn + c];
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t idx = DIM * fn + c;
+    if (!fixed_f[idx]) zf[idx] += acc[c];
+  }
+}
+
+template <typename T>
+static void restrict_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const T* rf, T* bc, int nr,
+                          int64_t sf, int64_t sc, cudaStream_t s) {
+  dim3 grid(blocks_for(gc.nnode), nr);
+  if (gf.dim == 2)
+    k_restrict<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc);
+  else
+    k_restrict<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc);
+}
+template <typename T>
+static void prolong_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const T* zc, T* zf, int nr,
+                         int64_t sf, int64_t sc, cudaStream_t s) {
+  dim3 grid(blocks_for(gf.nnode), nr);
+  if (gf.dim == 2)
+    k_prolong_add<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc);
+  else
+    k_prolong_add<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc);
+}
+
+void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc, int nr,
+                     int64_t sf, int64_t sc, cudaStream_t s) {
+  restrict_impl<double>(gf, gc, fixed_c, rf, bc, nr, sf, sc, s);
+}
+void launch_restrict32(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const float* rf, float* bc, int nr,
+                       int64_t sf, int64_t sc, cudaStream_t s) {
+  restrict_impl<float>(gf, gc, fixed_c, rf, bc, nr, sf, sc, s);
+}
+void launch_prolong_add(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* zc, double* zf,
+                        int nr, int64_t sf, int64_t sc, cudaStream_t s) {
+  prolong_impl<double>(gf, gc, fixed_f, zc, zf, nr, sf, sc, s);
+}
+void launch_prolong_add32(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const float* zc, float* zf,
+                          int nr, int64_t sf, int64_t sc, cudaStream_t s) {
+  prolong_impl<float>(gf, gc, fixed_f, zc, zf, nr, sf, sc, s);
+}
+
+// ---- coarsest level: dense inverse --------------------------------------------------------------
+template <typename T>
+__global__ void k_dense_gemv(const double* __restrict__ A, const T* __restrict__ b, T* __restrict__ z, int64_t n,
+                             int64_t stride) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  b += (int64_t)blockIdx.y * stride;
+  z += (int64_t)blockIdx.y * stride;
+  const double* a = A + row * n;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s += a[j] * (double)b[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) z[row] = (T)s;
+}
+
+void launch_dense_gemv(const double* Ainv, const double* b, double* z, int64_t n, int nr, int64_t stride,
+                       cudaStream_t s) {
+  k_dense_gemv<double><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride);
+}
+void launch_dense_gemv32(const double* Ainv, const float* b, float* z, int64_t n, int nr, int64_t stride,
+                         cudaStream_t s) {
+  k_dense_gemv<float><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride);
+}
+
+template <int DIM, class Op>
+__global__ void k_dense_assemble(Op op, double* A) {
+  constexpr int NN = Dims<DIM>::NN;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!node_coords(op.g, node, i, j, k)) return;
+  const Grid& g = op.g;
+  const int64_t n = g.n;
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t row = DIM * node + c;
+    double* Ar = A + row * n;
+    if (op.fixed[row]) {
+      Ar[row] = 1.0;
+      continue;
+    }
+    for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+      for (int cy = 0; cy < 2; ++cy)
+        for (int cx = 0; cx < 2; ++cx) {
+          const int ei = i - cx, ej = j - cy, ek = k - cz;
+          if (ei < 0 || ei >= g.nel[0] || ej < 0 || ej >= g.nel[1]) continue;
+          if (DIM == 3 && (ek < 0 || ek >= g.nel[2])) continue;
+          const int64_t e = ei + (int64_t)g.nel[0] * (ej + (int64_t)g.nel[1] * ek);
+          const int64_t n0 = ei + (int64_t)g.nn[0] * (ej + (int64_t)g.nn[1] * ek);
+          const int ln = local_node(cx, cy, cz);
+          const double sc = (double)op.scale(e);
+          for (int lb = 0; lb < NN; ++lb) {
+            const int64_t nb = n0 + corner_x(lb) + (int64_t)g.nn[0] * (corner_y(lb) + (int64_t)g.nn[1] * corner_z(lb));
+            for (int cc = 0; cc < DIM; ++cc) {
+              const int64_t col = DIM * nb + cc;
+              if (op.fixed[col]) continue;
+              Ar[col] += sc * (double)op.entry(e, ln * DIM + c, lb * DIM + cc);
+            }
+          }
+        }
+  }
+}
+
+// The fine-level FineOp carries its table in kernel parameters with runtime indices here, so the
+// dense assembly of a fine level uses a global-memory copy of the table instead.
+template <int DIM>
+struct FineOpGlobal {
+  Grid g;
+  const double* scale_e;
+  const uint8_t* fixed;
+  const double* M;
+  __device__ double scale(int64_t e) const { return scale_e[e]; }
+  __device__ double entry(int64_t, int r, int c) const { return M[r * Dims<DIM>::ND + c]; }
+};
+
+void launch_dense_assemble(const LevelOpDesc& d, double* A, cudaStream_t s) {
+  cudaMemsetAsync(A, 0, sizeof(double) * d.g.n * d.g.n, s);
+  const unsigned grid = blocks_for(d.g.nnode, 128);
+  if (d.stored) {
+    if (d.g.dim == 2)
+      k_dense_assemble<2><<<grid, 128, 0, s>>>(make_stored<2, double>(d, d.Ke64), A);
+    else
+      k_dense_assemble<3><<<grid, 128, 0, s>>>(make_stored<3, double>(d, d.Ke64), A);
+  } else {
+    if (d.g.dim == 2)
+      k_dense_assemble<2><<<grid, 128, 0, s>>>(FineOpGlobal<2>{d.g, d.scale64, d.fixed, d.T0dev}, A);
+    else
+      k_dense_assemble<3><<<grid, 128, 0, s>>>(FineOpGlobal<3>{d.g, d.scale64, d.fixed, d.T0dev}, A);
+  }
+}
+
+// One Gauss-Jordan elimination step on an SPD matrix (no pivoting): after steps k = 0..n-1 the
+// buffer holds the inverse.
+__global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int64_t n, int64_t k) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  const double p = A[k * n + k];
+  double v;
+  if (i == k && j == k)
+    v = 1.0 / p;
+  else if (i == k)
+    v = A[k * n + j] / p;
+  else if (j == k)
+    v = -A[i * n + k] / p;
+  else
+    v = A[i * n + j] - A[i * n + k] * A[k * n + j] / p;
+  B[idx] = v;
+}
+
+double* launch_dense_invert(double* A, double* work, int64_t n, cudaStream_t s) {
+  double* src = A;
+  double* dst = work;
+  for (int64_t k = 0; k < n; ++k) {
+    k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k);
+    std::swap(src, dst);
+  }
+  return src;
+}
+
+// ================================================================================================
+// Galerkin coarse element matrices: K_c = sum_children W_k^T (masked child K) W_k
+// ================================================================================================
+enum { GAL_FINE_K = 0, GAL_FINE_G = 1, GAL_STORED = 2 };
+
+template <int DIM, int SRC>
+__global__ void k_galerkin(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_f, const double* __restrict__ src,
+                           const double* __restrict__ T0, const double* __restrict__ W, double* __restrict__ Kc) {
+  constexpr int NN = Dims<DIM>::NN;
+  constexpr int ND = Dims<DIM>::ND;
+  __shared__ double sK[ND * ND];
+  __shared__ double sT[ND * ND];
+  __shared__ double sW[NN * NN * NN];
+  const int t = threadIdx.x;  // blockDim.x == ND*ND
+  for (int q = t; q < NN * NN * NN; q += blockDim.x) sW[q] = W[q];
+  const int64_t E = blockIdx.x;
+  const int EI = (int)(E % gc.nel[0]);
+  const int64_t rest = E / gc.nel[0];
+  const int EJ = (int)(rest % gc.nel[1]);
+  const int EK = (int)(rest / gc.nel[1]);
+  const int row = t / ND, col = t % ND;
+  const int lr = row / DIM, cr = row % DIM, lc = col / DIM, cc = col % DIM;
+  double acc = 0.0;
+  __syncthreads();
+  for (int kc = 0; kc < NN; ++kc) {
+    const int fi = 2 * EI + corner_x(kc), fj = 2 * EJ + corner_y(kc), fk = 2 * EK + corner_z(kc);
+    const int64_t ef = fi + (int64_t)gf.nel[0] * (fj + (int64_t)gf.nel[1] * fk);
+    const int64_t n0 = fi + (int64_t)gf.nn[0] * (fj + (int64_t)gf.nn[1] * fk);
+    const int64_t nr_ = n0 + corner_x(lr) + (int64_t)gf.nn[0] * (corner_y(lr) + (int64_t)gf.nn[1] * corner_z(lr));
+    const int64_t nc_ = n0 + corner_x(lc) + (int64_t)gf.nn[0] * (corner_y(lc) + (int64_t)gf.nn[1] * corner_z(lc));
+    double val;
+    if (SRC == GAL_FINE_K)
+      val = src[ef] * T0[row * ND + col];
+    else if (SRC == GAL_FINE_G)
+      val = (cr == cc) ? src[ef * NN * NN + lr * NN + lc] : 0.0;
+    else
+      val = src[ef * ND * ND + row * ND + col];
+    if (fixed_f[DIM * nr_ + cr] || fixed_f[DIM * nc_ + cc]) val = 0.0;
+    sK[t] = val;
+    __syncthreads();
+    {  // T[r][b*DIM+c'] = sum_l K[r][l*DIM+c'] W[kc][l][b]
+      const int b = col / DIM, cp = col % DIM;
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < NN; ++l) s += sK[row * ND + l * DIM + cp] * sW[(kc * NN + l) * NN + b];
+      sT[t] = s;
+    }
+    __syncthreads();
+    {  // out[a*DIM+c][col] += sum_i W[kc][i][a] T[i*DIM+c][col]
+      const int a = row / DIM, c = row % DIM;
+#pragma unroll
+      for (int i = 0; i < NN; ++i) acc += sW[(kc * NN + i) * NN + a] * sT[(i * DIM + c) * ND + col];
+    }
+    __syncthreads();
+  }
+  Kc[E * ND * ND + t] = acc;
+}
+
+template <int SRC>
+static void galerkin_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* src,
+                          const double* T0, const double* W, double* Kc, cudaStream_t s) {
+  if (gf.dim == 2)
+    k_galerkin<2, SRC><<<(unsigned)gc.m, 64, 0, s>>>(gf, gc, fixed_f, src, T0, W, Kc);
+  else
+    k_galerkin<3, SRC><<<(unsigned)gc.m, 576, 0, s>>>(gf, gc, fixed_f, src, T0, W, Kc);
+}
+
+void launch_galerkin_fine_K(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* scale,
+                            const double* Ke0, const double* W, double* Kc, cudaStream_t s) {
+  galerkin_impl<GAL_FINE_K>(gf, gc, fixed_f, scale, Ke0, W, Kc, s);
+}
+void launch_galerkin_fine_G(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Gs,
+                            const double* W, double* Gc, cudaStream_t s) {
+  galerkin_impl<GAL_FINE_G>(gf, gc, fixed_f, Gs, nullptr, W, Gc, s);
+}
+void launch_galerkin_stored(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Kf,
+                            const double* W, double* Kc, cudaStream_t s) {
+  galerkin_impl<GAL_STORED>(gf, gc, fixed_f, Kf, nullptr, W, Kc, s);
+}
+
+// ================================================================================================
+// element stress stiffness from the Gauss-point stresses of u (Sec. 2)
+// ================================================================================================
+template <int DIM>
+__global__ void k_stress_gs(Grid g, const double* __restrict__ u, const double* __restrict__ Es,
+                            const double* __restrict__ dN, const double* __restrict__ D, double wdet,
+                            double* __restrict__ Gs0, double* __restrict__ Gs) {
+  constexpr int NN = Dims<DIM>::NN;
+  constexpr int NV = Dims<DIM>::NV;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.m) return;
+  const int ei = (int)(e % g.nel[0]);
+  const int64_t rest = e / g.nel[0];
+  const int ej = (int)(rest % g.nel[1]);
+  const int ek = (int)(rest / g.nel[1]);
+  const int64_t n0 = ei + (int64_t)g.nn[0] * (ej + (int64_t)g.nn[1] * ek);
+  double ue[NN][DIM];
+#pragma unroll
+  for (int l = 0; l < NN; ++l) {
+    const int64_t nb = n0 + corner_x(l) + (int64_t)g.nn[0] * (corner_y(l) + (int64_t)g.nn[1] * corner_z(l));
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) ue[l][c] = u[DIM * nb + c];
+  }
+  double G[NN][NN];
+#pragma unroll
+  for (int a = 0; a < NN; ++a)
+#pragma unroll
+    for (int b = 0; b < NN; ++b) G[a][b] = 0.0;
+  for (int gp = 0; gp < NN; ++gp) {
+    const double* dn = dN + gp * DIM * NN;
+    double H[DIM][DIM];  // H[a][c] = d u_c / d x_a
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < NN; ++l) s += dn[a * NN + l] * ue[l][c];
+        H[a][c] = s;
+      }
+    double eps[NV];
+    if (DIM == 2) {
+      eps[0] = H[0][0];
+      eps[1] = H[1][1];
+      eps[2] = H[0][1] + H[1][0];
+    } else {
+      eps[0] = H[0][0];
+      eps[1] = H[1][1];
+      eps[2] = H[DIM - 1][DIM - 1];
+      eps[3] = H[0][1] + H[1][0];
+      eps[4] = H[1][DIM - 1] + H[DIM - 1][1];
+      eps[5] = H[DIM - 1][0] + H[0][DIM - 1];
+    }
+    double sig[NV];
+#pragma unroll
+    for (int p = 0; p < NV; ++p) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) s += D[p * NV + q] * eps[q];
+      sig[p] = s;
+    }
+    double S[DIM][DIM];
+    if (DIM == 2) {
+      S[0][0] = sig[0];
+      S[1][1] = sig[1];
+      S[0][1] = S[1][0] = sig[2];
+    } else {
+      S[0][0] = sig[0];
+      S[1][1] = sig[1];
+      S[DIM - 1][DIM - 1] = sig[2];
+      S[0][1] = S[1][0] = sig[3];
+      S[1][DIM - 1] = S[DIM - 1][1] = sig[4];
+      S[DIM - 1][0] = S[0][DIM - 1] = sig[5];
+    }
+    double SdN[DIM][NN];
+#pragma unroll
+    for (int p = 0; p < DIM; ++p)
+#pragma unroll
+      for (int b = 0; b < NN; ++b) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) s += S[p][q] * dn[q * NN + b];
+        SdN[p][b] = s;
+      }
+#pragma unroll
+    for (int a = 0; a < NN; ++a)
+#pragma unroll
+      for (int b = 0; b < NN; ++b) {
+        double s = 0.0;
+#pragma unroll
+        for (int p = 0; p < DIM; ++p) s += dn[p * NN + a] * SdN[p][b];
+        G[a][b] += wdet * s;
+      }
+  }
+  const double es = Es[e];
+#pragma unroll
+  for (int a = 0; a < NN; ++a)
+#pragma unroll
+    for (int b = 0; b < NN; ++b) {
+      Gs0[e * NN * NN + a * NN + b] = G[a][b];
+      Gs[e * NN * NN + a * NN + b] = es * G[a][b];
+    }
+}
+
+void launch_stress_gs_dev(const Grid& g, const double* u, const double* Es, const double* dN, const double* D,
+                          double wdet, double* Gs0, double* Gs, cudaStream_t s) {
+  if (g.dim == 2)
+    k_stress_gs<2><<<blocks_for(g.m, 128), 128, 0, s>>>(g, u, Es, dN, D, wdet, Gs0, Gs);
+  else
+    k_stress_gs<3><<<blocks_for(g.m, 128), 128, 0, s>>>(g, u, Es, dN, D, wdet, Gs0, Gs);
+}
+
+// ================================================================================================
+// SIMP and elementwise helpers
+// ================================================================================================
+__global__ void k_simp(const double* __restrict__ x, int64_t m, double penal, double E0, double Emin, double* Ek,
+                       double* Es, double* dEk, double* dEs, float* Ek32) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const double xe = x[e];
+  const double xp = pow(xe, penal);
+  const double dxp = penal * pow(xe, penal - 1.0);
+  const double ek = Emin + xp * (E0 - Emin);
+  Ek[e] = ek;
+  Es[e] = xp * E0;
+  dEk[e] = dxp * (E0 - Emin);
+  dEs[e] = dxp * E0;
+  if (Ek32) Ek32[e] = (float)ek;
+}
+
+void launch_simp(const double* x, int64_t m, double penal, double E0, double Emin, double* Ek, double* Es,
+                 double* dEk, double* dEs, float* Ek32, cudaStream_t s) {
+  k_simp<<<blocks_for(m), kThreads, 0, s>>>(x, m, penal, E0, Emin, Ek, Es, dEk, dEs, Ek32);
+}
+
+__global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_f32_to_f64(const float* a, double* b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  k_f64_to_f32<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
+}
+void launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
+  k_f32_to_f64<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
+}
+
+__global__ void k_mask_copy(const double* __restrict__ src, const uint8_t* __restrict__ fixed, double* __restrict__ dst,
+                            int64_t n, int64_t stride) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t off = (int64_t)blockIdx.y * stride;
+  dst[off + i] = fixed[i] ? 0.0 : src[off + i];
+}
+void launch_mask_copy(const double* src, const uint8_t* fixed, double* dst, int64_t n, int nr, int64_t stride,
+                      cudaStream_t s) {
+  k_mask_copy<<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(src, fixed, dst, n, stride);
+}
+
+// ================================================================================================
+// multi-RHS preconditioned CG (Appendix A: mgPCG); one RHS per blockIdx.y, scalars on the device
+// ================================================================================================
+constexpr int kVecBlocks = 4 * 152;  // vector kernels: grid-stride over DOFs with a fixed grid
+
+__device__ __forceinline__ double* rhs_sc(double* sc, int r) { return sc + (size_t)r * kScStride; }
+
+template <int DIM, class Op>
+__global__ void __launch_bounds__(kThreads) k_cg_init(const __grid_constant__ Op op, const double* __restrict__ b, double* __restrict__ x,
+                                                       double* __restrict__ r, int use_x0, double rtol,
+                                                       int64_t stride, double* sc, double* partial,
+                                                       unsigned* counters, int64_t pstride) {
+  __shared__ double smem[64];
+  const int rhs = blockIdx.y;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t off = (int64_t)rhs * stride;
+  int i, j, k;
+  double v[2] = {0.0, 0.0};  // b.b, r.r
+  if (node_coords(op.g, node, i, j, k)) {
+    double acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+    if (use_x0) gather_rows<DIM, double>(op, i, j, k, LoadVec<double>{x + off}, acc);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t idx = DIM * node + c;
+      const double bi = op.fixed[idx] ? 0.0 : b[off + idx];
+      const double ri = op.fixed[idx] ? 0.0 : bi - acc[c];
+      r[off + idx] = ri;
+      if (!use_x0) x[off + idx] = 0.0;
+      v[0] += bi * bi;
+      v[1] += ri * ri;
+    }
+  }
+  double tot[2];
+  if (grid_sum_last<2>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
+    double* s = rhs_sc(sc, rhs);
+    for (int q = 0; q < kScStride; ++q) s[q] = 0.0;
+    s[SC_BB] = tot[0];
+    s[SC_RR] = tot[1];
+    s[SC_RTOL] = rtol;
+    s[SC_ZR_OLD] = 1.0;
+    s[SC_PQ] = 1.0;
+    const double rel = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+    s[SC_RELRES] = rel;
+    s[SC_ACTIVE] = (tot[0] > 0.0 && rel > rtol) ? 1.0 : 0.0;
+    if (!isfinite(tot[1])) {
+      s[SC_STATUS] = 2.0;
+      s[SC_ACTIVE] = 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_dots(int64_t n, const double* __restrict__ z,
+                                                       const double* __restrict__ r, const double* __restrict__ q,
+                                                       const double* __restrict__ p, int flexible, int64_t stride,
+                                                       double* sc, double* partial, unsigned* counters,
+                                                       int64_t pstride) {
+  __shared__ double smem[96];
+  const int rhs = blockIdx.y;
+  double* s = rhs_sc(sc, rhs);
+  if (s[SC_ACTIVE] == 0.0) return;
+  const int64_t off = (int64_t)rhs * stride;
+  double v[3] = {0.0, 0.0, 0.0};  // z.r, z.q_old, p_old.r
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = z[off + i], ri = r[off + i];
+    v[0] += zi * ri;
+    v[1] += zi * q[off + i];
+    v[2] += p[off + i] * ri;
+  }
+  double tot[3];
+  if (grid_sum_last<3>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
+    const double zr = tot[0], zq = tot[1], pr = tot[2];
+    double beta = 0.0;
+    if (s[SC_ITERS] > 0.0) beta = flexible ? -zq / s[SC_PQ] : zr / s[SC_ZR_OLD];
+    s[SC_BETA] = beta;
+    s[SC_ZR] = zr;
+    s[SC_ZR_OLD] = zr;
+    s[SC_PR] = zr + beta * pr;
+    if (!isfinite(beta) || !isfinite(zr)) {
+      s[SC_STATUS] = 2.0;
+      s[SC_ACTIVE] = 0.0;
+    }
+  }
+}
+
+template <int DIM, class Op>
+__global__ void __launch_bounds__(kThreads) k_cg_direction(const __grid_constant__ Op op, const double* __restrict__ z,
+                                                            const double* __restrict__ p_old,
+                                                            double* __restrict__ p_new, double* __restrict__ q,
+                                                            int64_t stride, double* sc, double* partial,
+                                                            unsigned* counters, int64_t pstride) {
+  __shared__ double smem[64];
+  const int rhs = blockIdx.y;
+  double* s = rhs_sc(sc, rhs);
+  if (s[SC_ACTIVE] == 0.0) return;
+  const int64_t off = (int64_t)rhs * stride;
+  const LoadAxpy ld{z + off, p_old + off, s[SC_BETA]};
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  double v[1] = {0.0};
+  if (node_coords(op.g, node, i, j, k)) {
+    double acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+    gather_rows<DIM, double>(op, i, j, k, ld, acc);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t idx = DIM * node + c;
+      const bool fx = op.fixed[idx];
+      const double pi = fx ? 0.0 : ld(idx);
+      const double qi = fx ? 0.0 : acc[c];
+      p_new[off + idx] = pi;
+      q[off + idx] = qi;
+      v[0] += pi * qi;
+    }
+  }
+  double tot[1];
+  if (grid_sum_last<1>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    s[SC_PQ] = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      s[SC_STATUS] = 1.0;  // breakdown: K not positive on the search direction
+      s[SC_ACTIVE] = 0.0;
+      s[SC_ALPHA] = 0.0;
+    } else {
+      s[SC_ALPHA] = s[SC_PR] / pq;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         int64_t stride, double* sc, double* partial,
+                                                         unsigned* counters, int64_t pstride) {
+  __shared__ double smem[64];
+  const int rhs = blockIdx.y;
+  double* s = rhs_sc(sc, rhs);
+  if (s[SC_ACTIVE] == 0.0) return;
+  const int64_t off = (int64_t)rhs * stride;
+  const double alpha = s[SC_ALPHA];
+  double v[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[off + i] += alpha * p[off + i];
+    const double ri = r[off + i] - alpha * q[off + i];
+    r[off + i] = ri;
+    v[0] += ri * ri;
+  }
+  double tot[1];
+  if (grid_sum_last<1>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
+    s[SC_RR] = tot[0];
+    const double rel = sqrt(tot[0] / s[SC_BB]);
+    s[SC_RELRES] = rel;
+    s[SC_ITERS] += 1.0;
+    if (!isfinite(rel)) {
+      s[SC_STATUS] = 2.0;
+      s[SC_ACTIVE] = 0.0;
+    } else if (rel <= s[SC_RTOL]) {
+      s[SC_ACTIVE] = 0.0;
+    }
+  }
+}
+
+template <int DIM, class Op>
+__global__ void __launch_bounds__(kThreads) k_true_residual(const __grid_constant__ Op op, const double* __restrict__ b,
+                                                             const double* __restrict__ x, double* __restrict__ r,
+                                                             int64_t stride, double* sc, double* partial,
+                                                             unsigned* counters, int64_t pstride) {
+  __shared__ double smem[64];
+  const int rhs = blockIdx.y;
+  const int64_t off = (int64_t)rhs * stride;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  double v[2] = {0.0, 0.0};
+  if (node_coords(op.g, node, i, j, k)) {
+    double acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+    gather_rows<DIM, double>(op, i, j, k, LoadVec<double>{x + off}, acc);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t idx = DIM * node + c;
+      const double bi = op.fixed[idx] ? 0.0 : b[off + idx];
+      const double ri = op.fixed[idx] ? 0.0 : bi - acc[c];
+      r[off + idx] = ri;
+      v[0] += ri * ri;
+      v[1] += bi * bi;
+    }
+  }
+  double tot[2];
+  if (grid_sum_last<2>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
+    double* s = rhs_sc(sc, rhs);
+    s[SC_RR] = tot[0];
+    s[SC_BB] = tot[1];
+    s[SC_RELRES] = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : sqrt(tot[0]);
+  }
+}
+
+int64_t cg_partial_stride(int64_t nnode) {
+  const int64_t a = (nnode + kThreads - 1) / kThreads;
+  return 4 * std::max<int64_t>(a, kVecBlocks);
+}
+
+template <int DIM, class Op>
+static void cg_init_impl(const Op& op, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
+                         int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  const int64_t ps = cg_partial_stride(op.g.nnode);
+  k_cg_init<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, use_x0 ? 1 : 0, rtol,
+                                                                            stride, sc, partial, counters, ps);
+}
+
+void launch_cg_init(const LevelOpDesc& d, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
+                    int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  if (d.g.dim == 2) {
+    if (d.stored)
+      cg_init_impl<2>(make_stored<2, double>(d, d.Ke64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+    else
+      cg_init_impl<2>(make_fine<2, double>(d, d.scale64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+  } else {
+    if (d.stored)
+      cg_init_impl<3>(make_stored<3, double>(d, d.Ke64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+    else
+      cg_init_impl<3>(make_fine<3, double>(d, d.scale64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+  }
+}
+
+void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q, const double* p, bool flexible,
+                    int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  const int64_t ps = 4 * kVecBlocks;
+  const unsigned g = (unsigned)std::min<int64_t>(kVecBlocks, (n + kThreads - 1) / kThreads);
+  k_cg_dots<<<dim3(g, nr), kThreads, 0, s>>>(n, z, r, q, p, flexible ? 1 : 0, stride, sc, partial, counters + kMaxRhs, ps);
+}
+
+template <int DIM, class Op>
+static void cg_dir_impl(const Op& op, const double* z, const double* p_old, double* p_new, double* q, int nr,
+                        int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  const int64_t ps = cg_partial_stride(op.g.nnode);
+  k_cg_direction<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, z, p_old, p_new, q, stride, sc,
+                                                                                 partial, counters + 2 * kMaxRhs, ps);
+}
+
+void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_old, double* p_new, double* q,
+                         int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  if (d.g.dim == 2) {
+    if (d.stored)
+      cg_dir_impl<2>(make_stored<2, double>(d, d.Ke64), z, p_old, p_new, q, nr, stride, sc, partial, counters, s);
+    else
+      cg_dir_impl<2>(make_fine<2, double>(d, d.scale64), z, p_old, p_new, q, nr, stride, sc, partial, counters, s);
+  } else {
+    if (d.stored)
+      cg_dir_impl<3>(make_stored<3, double>(d, d.Ke64), z, p_old, p_new, q, nr, stride, sc, partial, counters, s);
+    else
+      cg_dir_impl<3>(make_fine<3, double>(d, d.scale64), z, p_old, p_new, q, nr, stride, sc, partial, counters, s);
+  }
+}
+
+void launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, int nr, int64_t stride,
+                      double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  const int64_t ps = 4 * kVecBlocks;
+  const unsigned g = (unsigned)std::min<int64_t>(kVecBlocks, (n + kThreads - 1) / kThreads);
+  k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial, counters + 3 * kMaxRhs, ps);
+}
+
+template <int DIM, class Op>
+static void true_res_impl(const Op& op, const double* b, const double* x, double* r, int nr, int64_t stride,
+                          double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  const int64_t ps = cg_partial_stride(op.g.nnode);
+  k_true_residual<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, stride, sc, partial,
+                                                                                  counters + 4 * kMaxRhs, ps);
+}
+
+void launch_true_residual(const LevelOpDesc& d, const double* b, const double* x, double* r, int nr, int64_t stride,
+                          double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  if (d.g.dim == 2) {
+    if (d.stored)
+      true_res_impl<2>(make_stored<2, double>(d, d.Ke64), b, x, r, nr, stride, sc, partial, counters, s);
+    else
+      true_res_impl<2>(make_fine<2, double>(d, d.scale64), b, x, r, nr, stride, sc, partial, counters, s);
+  } else {
+    if (d.stored)
+      true_res_impl<3>(make_stored<3, double>(d, d.Ke64), b, x, r, nr, stride, sc, partial, counters, s);
+    else
+      true_res_impl<3>(make_fine<3, double>(d, d.scale64), b, x, r, nr, stride, sc, partial, counters, s);
+  }
+}
+
+// ================================================================================================
+// tall-skinny block products for the block eigensolver
+// ================================================================================================
+constexpr int kGramChunk = 64;
+
+// partial[chunk][i][j] = sum_{k in chunk} A[i][k] B[j][k]
+__global__ void k_gram_partial(const double* __restrict__ A, int na, const double* __restrict__ B, int nb, int64_t n,
+                               int64_t stride, double* __restrict__ partial) {
+  extern __shared__ double sm[];
+  double* sA = sm;                       // [na][chunk]
+  double* sB = sm + na * kGramChunk;     // [nb][chunk]
+  const int64_t k0 = (int64_t)blockIdx.x * kGramChunk;
+  const int len = (n - k0) < kGramChunk ? (int)(n - k0) : kGramChunk;
+  for (int t = threadIdx.x; t < na * kGramChunk; t += blockDim.x) {
+    const int i = t / kGramChunk, kk = t % kGramChunk;
+    sA[t] = kk < len ? A[(int64_t)i * stride + k0 + kk] : 0.0;
+  }
+  for (int t = threadIdx.x; t < nb * kGramChunk; t += blockDim.x) {
+    const int j = t / kGramChunk, kk = t % kGramChunk;
+    sB[t] = kk < len ? B[(int64_t)j * stride + k0 + kk] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
+    const int i = t / nb, j = t % nb;
+    double s = 0.0;
+#pragma unroll 8
+    for (int kk = 0; kk < kGramChunk; ++kk) s += sA[i * kGramChunk + kk] * sB[j * kGramChunk + kk];
+    partial[(size_t)blockIdx.x * na * nb + t] = s;
+  }
+}
+
+__global__ void k_gram_final(const double* __restrict__ partial, int nchunks, int nout, double* __restrict__ C) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nout) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * nout + t];
+  C[t] = s;
+}
+
+int gram_partial_blocks(int64_t n) { return (int)((n + kGramChunk - 1) / kGramChunk); }
+
+void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
+                 double* partial, cudaStream_t s) {
+  const int chunks = gram_partial_blocks(n);
+  const size_t smem = sizeof(double) * (size_t)(na + nb) * kGramChunk;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    configured = true;
+  }
+  k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, partial);
+  k_gram_final<<<blocks_for((int64_t)na * nb), kThreads, 0, s>>>(partial, chunks, na * nb, C);
+}
+
+// Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j]; one thread per row index, up to 32 outputs per
+// pass over blockIdx.y tiles of columns.
+__global__ void k_combine(const double* __restrict__ X, int nx, const double* __restrict__ C, int ldc, int ny,
+                          double alpha, double beta, double* __restrict__ Y, int64_t n, int64_t stride) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * 32;
+  const int nj = min(32, ny - j0);
+  if (k >= n) return;
+  double acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+  for (int i = 0; i < nx; ++i) {
+    const double xi = X[(int64_t)i * stride + k];
+    const double* ci = C + (size_t)i * ldc + j0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nj) acc[j] += xi * ci[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (j < nj) {
+      double* y = Y + (int64_t)(j0 + j) * stride + k;
+      *y = (beta == 0.0 ? 0.0 : beta * *y) + alpha * acc[j];
+    }
+  }
+}
+
+void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta, double* Y,
+                    int64_t n, int64_t stride, cudaStream_t s) {
+  dim3 grid(blocks_for(n), (ny + 31) / 32);
+  k_combine<<<grid, kThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n, stride);
+}
+
+}  // namespace tobk

@@ -1,0 +1,113 @@
+// Host-side launch wrappers for the CUDA kernels of the library (all kernels live in kernels.cu).
+// Every wrapper enqueues work on the given stream and returns immediately; pointers are device
+// pointers; multi-RHS blocks are RHS-major with the given stride (elements between RHS columns).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tobk_internal.cuh"
+
+namespace tobk {
+
+// Which element operator a level uses.
+struct LevelOpDesc {
+  Grid g;
+  const uint8_t* fixed;
+  // fine (level 1): matrix-free scale_e * T0 with T0 = Ke0 (double) / Ke0f (float)
+  const double* scale64;
+  const float* scale32;
+  const double* T0;     // host pointer to the nd*nd table (copied into kernel parameters)
+  const double* T0dev;  // device copy of the same table
+  // coarse: stored element matrices
+  const double* Ke64;
+  const float* Ke32;
+  bool stored;
+};
+
+enum ApplyMode { APPLY_KV = 0, APPLY_RES = 1, APPLY_JAC = 2 };
+
+// y = K v | y = b - K v | y = v + omega dinv (b - K v), for nr RHS (double or float vectors).
+void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double* b, const double* dinv,
+                  double* y, double omega, int nr, int64_t stride, cudaStream_t s);
+void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
+                    float* y, float omega, int nr, int64_t stride, cudaStream_t s);
+// y = G v with G_e = Gs_e (x) I (Gs includes E_sigma), fine level.
+void launch_apply_kron(const Grid& g, const uint8_t* fixed, const double* Gs, const double* v, double* y,
+                       int nr, int64_t stride, cudaStream_t s);
+// dinv = 1/diag(K) (0 at fixed DOFs); also a float copy when dinv32 != nullptr.
+void launch_diag(const LevelOpDesc& op, double* dinv, float* dinv32, cudaStream_t s);
+// z = omega dinv b (first damped-Jacobi sweep from a zero guess)
+void launch_jacobi0(const double* b, const double* dinv, double* z, double omega, int64_t n, int nr,
+                    int64_t stride, cudaStream_t s);
+void launch_jacobi0_32(const float* b, const float* dinv, float* z, float omega, int64_t n, int nr,
+                       int64_t stride, cudaStream_t s);
+// coarse b = P^T r_fine (masked); fine z += P z_coarse (masked)
+void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc,
+                     int nr, int64_t sf, int64_t sc, cudaStream_t s);
+void launch_restrict32(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const float* rf, float* bc,
+                       int nr, int64_t sf, int64_t sc, cudaStream_t s);
+void launch_prolong_add(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* zc, double* zf,
+                        int nr, int64_t sf, int64_t sc, cudaStream_t s);
+void launch_prolong_add32(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const float* zc, float* zf,
+                          int nr, int64_t sf, int64_t sc, cudaStream_t s);
+// z = Ainv b (dense, n x n, FP64 matrix), nr RHS
+void launch_dense_gemv(const double* Ainv, const double* b, double* z, int64_t n, int nr, int64_t stride,
+                       cudaStream_t s);
+void launch_dense_gemv32(const double* Ainv, const float* b, float* z, int64_t n, int nr, int64_t stride,
+                         cudaStream_t s);
+// Dense assembly of a level operator (identity rows/cols at fixed DOFs), then in-place-free
+// Gauss-Jordan inversion (SPD, no pivoting) ping-ponging between A and work.
+void launch_dense_assemble(const LevelOpDesc& op, double* A, cudaStream_t s);
+// returns the buffer holding the inverse (A or work)
+double* launch_dense_invert(double* A, double* work, int64_t n, cudaStream_t s);
+
+// Galerkin coarse element matrices.  child source: fine K (scale * table), fine G (Es * Gs0 (x) I),
+// or stored matrices of the previous level.  Rows/cols of fixed fine DOFs are masked.
+void launch_galerkin_fine_K(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* scale,
+                            const double* Ke0, const double* W, double* Kc, cudaStream_t s);
+void launch_galerkin_fine_G(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Gs,
+                            const double* W, double* Gc, cudaStream_t s);
+void launch_galerkin_stored(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Kf,
+                            const double* W, double* Kc, cudaStream_t s);
+
+// Element stress stiffness: Gs0[e] = sum_gp w|J| dN^T S(D B u_e) dN (unit modulus), Gs = E_sigma Gs0.
+// dN [ngp][dim][nn] and D [nv][nv] are device tables.
+void launch_stress_gs_dev(const Grid& g, const double* u, const double* Es, const double* dN, const double* D,
+                          double wdet, double* Gs0, double* Gs, cudaStream_t s);
+int64_t cg_partial_stride(int64_t nnode);
+
+// SIMP moduli (paper Sec. 2): Ek = Emin + x^p (E0 - Emin), Es = x^p E0, derivatives.
+void launch_simp(const double* x, int64_t m, double penal, double E0, double Emin, double* Ek, double* Es,
+                 double* dEk, double* dEs, float* Ek32, cudaStream_t s);
+
+// elementwise helpers
+void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+void launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
+void launch_mask_copy(const double* src, const uint8_t* fixed, double* dst, int64_t n, int nr, int64_t stride,
+                      cudaStream_t s);
+
+// ---- multi-RHS PCG kernels (FP64).  sc: [nr][kScStride] scalars; partial/counters: scratch.
+void launch_cg_init(const LevelOpDesc& op, const double* b, double* x, double* r, bool use_x0, double rtol,
+                    int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
+void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q, const double* p, bool flexible,
+                    int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
+void launch_cg_direction(const LevelOpDesc& op, const double* z, const double* p_old, double* p_new, double* q,
+                         int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
+void launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, int nr, int64_t stride,
+                      double* sc, double* partial, unsigned* counters, cudaStream_t s);
+// true residual: r = b - K x; sc[SC_RELRES] = ||r|| / ||b||
+void launch_true_residual(const LevelOpDesc& op, const double* b, const double* x, double* r, int nr,
+                          int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
+
+// ---- dense small-block kernels for block methods: C[i][j] = sum_k A[i][k] B[j][k] over rows
+//      of A [na][n] and B [nb][n] (RHS-major vectors).  Deterministic two-stage reduction.
+void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
+                 double* partial, cudaStream_t s);
+// Y[j][:] (+)= sum_i X[i][:] * C[i][j]  (X [nx][n], C [nx][ny] row-major, Y [ny][n]); beta: 0 or 1
+// for overwrite / accumulate; alpha scales the product.
+void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta,
+                    double* Y, int64_t n, int64_t stride, cudaStream_t s);
+int gram_partial_blocks(int64_t n);
+
+}  // namespace tobk

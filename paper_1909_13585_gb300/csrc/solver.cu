@@ -1,0 +1,642 @@
+// Host orchestration: element tables, handle memory, multigrid hierarchy set-up, V-cycle and the
+// multi-RHS preconditioned CG driver (paper Appendix A: mgPCG / mgBPCG), linear analysis
+// (Algorithm 1 step 2) and the stress-stiffness set-up (Algorithm 1 step 3, Algorithm 2 line 5).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "handle.h"
+
+namespace tobk {
+
+// ================================================================================================
+// element tables (Gauss-Legendre 2-point rule per axis; exact for Q4/H8 on unit elements)
+// ================================================================================================
+ElementTables make_element_tables(int dim, double nu) {
+  ElementTables t;
+  t.dim = dim;
+  t.nn = 1 << dim;
+  t.nd = dim * t.nn;
+  t.ngp = t.nn;
+  t.nv = dim == 2 ? 3 : 6;
+  const int nn = t.nn, nd = t.nd, nv = t.nv;
+  // natural coordinates (+-1) of the local nodes, Q4 order then the same on the upper face
+  auto xi_node = [&](int l, int a) -> double {
+    const int cx = ((l & 3) == 1 || (l & 3) == 2) ? 1 : 0;
+    const int cy = ((l & 3) >= 2) ? 1 : 0;
+    const int cz = l >> 2;
+    const int c = a == 0 ? cx : (a == 1 ? cy : cz);
+    return c ? 1.0 : -1.0;
+  };
+  const double g = 1.0 / std::sqrt(3.0);
+  t.wdet = std::pow(0.5, dim);  // weight 1 per point, |J| = (1/2)^dim on the unit element
+  t.dN.assign((size_t)t.ngp * dim * nn, 0.0);
+  for (int q = 0; q < t.ngp; ++q) {
+    double gp[3];
+    for (int a = 0; a < dim; ++a) gp[a] = ((q >> a) & 1) ? g : -g;
+    for (int l = 0; l < nn; ++l)
+      for (int a = 0; a < dim; ++a) {
+        double v = xi_node(l, a) / std::pow(2.0, dim);
+        for (int b = 0; b < dim; ++b)
+          if (b != a) v *= 1.0 + xi_node(l, b) * gp[b];
+        t.dN[((size_t)q * dim + a) * nn + l] = 2.0 * v;  // d/dx = 2 d/dxi on the unit element
+      }
+  }
+  // unit-modulus constitutive matrix; Voigt order 2D [xx yy xy], 3D [xx yy zz xy yz zx]
+  t.D.assign((size_t)nv * nv, 0.0);
+  if (dim == 2) {
+    const double c = 1.0 / (1.0 - nu * nu);
+    t.D[0] = c;
+    t.D[1] = c * nu;
+    t.D[3] = c * nu;
+    t.D[4] = c;
+    t.D[8] = c * (1.0 - nu) / 2.0;
+  } else {
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = 1.0 / (2.0 * (1.0 + nu));
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) t.D[a * 6 + b] = lam + (a == b ? 2.0 * mu : 0.0);
+    for (int a = 3; a < 6; ++a) t.D[a * 6 + a] = mu;
+  }
+  // K_e0 = sum_gp wdet B^T D B
+  t.Ke0.assign((size_t)nd * nd, 0.0);
+  std::vector<double> B((size_t)nv * nd);
+  for (int q = 0; q < t.ngp; ++q) {
+    std::fill(B.begin(), B.end(), 0.0);
+    const double* dn = &t.dN[(size_t)q * dim * nn];
+    for (int l = 0; l < nn; ++l) {
+      const double dx = dn[0 * nn + l], dy = dn[1 * nn + l];
+      if (dim == 2) {
+        B[0 * nd + 2 * l] = dx;
+        B[1 * nd + 2 * l + 1] = dy;
+        B[2 * nd + 2 * l] = dy;
+        B[2 * nd + 2 * l + 1] = dx;
+      } else {
+        const double dz = dn[2 * nn + l];
+        B[0 * nd + 3 * l] = dx;
+        B[1 * nd + 3 * l + 1] = dy;
+        B[2 * nd + 3 * l + 2] = dz;
+        B[3 * nd + 3 * l] = dy;
+        B[3 * nd + 3 * l + 1] = dx;
+        B[4 * nd + 3 * l + 1] = dz;
+        B[4 * nd + 3 * l + 2] = dy;
+        B[5 * nd + 3 * l] = dz;
+        B[5 * nd + 3 * l + 2] = dx;
+      }
+    }
+    for (int r = 0; r < nd; ++r)
+      for (int c = 0; c < nd; ++c) {
+        double s = 0.0;
+        for (int a = 0; a < nv; ++a)
+          for (int b = 0; b < nv; ++b) s += B[a * nd + r] * t.D[a * nv + b] * B[b * nd + c];
+        t.Ke0[(size_t)r * nd + c] += t.wdet * s;
+      }
+  }
+  // interpolation weights child node -> coarse element node, per child position
+  t.W.assign((size_t)nn * nn * nn, 0.0);
+  for (int kc = 0; kc < nn; ++kc)
+    for (int l = 0; l < nn; ++l)
+      for (int b = 0; b < nn; ++b) {
+        double w = 1.0;
+        for (int a = 0; a < dim; ++a) {
+          const int ka = xi_node(kc, a) > 0 ? 1 : 0;
+          const int la = xi_node(l, a) > 0 ? 1 : 0;
+          const int ba = xi_node(b, a) > 0 ? 1 : 0;
+          const double p = 0.5 * (ka + la);
+          w *= ba ? p : 1.0 - p;
+        }
+        t.W[((size_t)kc * nn + l) * nn + b] = w;
+      }
+  return t;
+}
+
+// ================================================================================================
+// errors
+// ================================================================================================
+int fail(tobk_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int check_cuda(tobk_handle* h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, TOBK_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return TOBK_OK;
+}
+
+// ================================================================================================
+// handle memory
+// ================================================================================================
+static void layout(tobk_handle* h, Arena& a) {
+  const int nn = h->tab.nn, nd = h->tab.nd;
+  const bool mixed = h->desc.precision == TOBK_FP32_VCYCLE;
+  const int rm = h->rmax;
+  for (int j = 0; j < h->L; ++j) {
+    Level& L = h->lv[j];
+    const int64_t n = L.g.n, m = L.g.m;
+    L.fixed = a.take<uint8_t>(n);
+    if (j > 0) {
+      L.Ke = a.take<double>(m * nd * nd);
+      if (mixed) L.Ke32 = a.take<float>(m * nd * nd);
+    }
+    if (j > 0 && j <= h->eig) L.Ge = a.take<double>(m * nd * nd);
+    L.dinv = a.take<double>(n);
+    if (mixed) L.dinv32 = a.take<float>(n);
+    L.b = a.take<double>(rm * n);
+    L.z = a.take<double>(rm * n);
+    L.t = a.take<double>(rm * n);
+    L.r = a.take<double>(rm * n);
+    if (mixed) {
+      L.b32 = a.take<float>(rm * n);
+      L.z32 = a.take<float>(rm * n);
+      L.t32 = a.take<float>(rm * n);
+      L.r32 = a.take<float>(rm * n);
+    }
+  }
+  const Grid& g = h->lv[0].g;
+  h->d_Ke0 = a.take<double>(nd * nd);
+  h->d_W = a.take<double>(nn * nn * nn);
+  h->d_dN = a.take<double>(h->tab.dN.size());
+  h->d_D = a.take<double>(h->tab.D.size());
+  h->x = a.take<double>(g.m);
+  h->Ek = a.take<double>(g.m);
+  h->Es = a.take<double>(g.m);
+  h->dEk = a.take<double>(g.m);
+  h->dEs = a.take<double>(g.m);
+  h->Ek32 = a.take<float>(g.m);
+  h->f = a.take<double>(g.n);
+  h->u = a.take<double>(g.n);
+  h->u0 = a.take<double>(g.n);
+  h->Gs0 = a.take<double>(g.m * nn * nn);
+  h->Gs = a.take<double>(g.m * nn * nn);
+  const int64_t nc = h->lv[h->L - 1].g.n;
+  h->Adense = a.take<double>(nc * nc);
+  h->Awork = a.take<double>(nc * nc);
+  const int64_t nf = g.n;
+  h->cg.x = a.take<double>(rm * nf);
+  h->cg.r = a.take<double>(rm * nf);
+  h->cg.z = a.take<double>(rm * nf);
+  h->cg.zt = a.take<double>(rm * nf);
+  h->cg.p0 = a.take<double>(rm * nf);
+  h->cg.p1 = a.take<double>(rm * nf);
+  h->cg.q = a.take<double>(rm * nf);
+  h->cg.sc = a.take<double>((size_t)kMaxRhs * kScStride);
+  h->cg.partial = a.take<double>((size_t)kMaxRhs * cg_partial_stride(g.nnode));
+  h->cg.counters = a.take<unsigned>((size_t)kNumCounterSets * kMaxRhs);
+  h->bwork = a.take<double>(rm * nf);
+  h->xwork = a.take<double>(rm * nf);
+  const int q = h->q;
+  h->modes = a.take<double>((size_t)q * nf);
+  h->lam = a.take<double>(q);
+  h->adj = a.take<double>((size_t)q * nf);
+  h->adj_rhs = a.take<double>((size_t)q * nf);
+  h->dlam = a.take<double>((size_t)q * g.m);
+  h->dJ = a.take<double>(g.m);
+  h->esens = a.take<double>((size_t)g.m * h->tab.ngp * h->tab.nv);
+  // eigen workspace at the eigen level
+  const int64_t ne = h->lv[h->eig].g.n;
+  const int mm = h->eig_mmax, nb = h->eig_nb;
+  h->V = a.take<double>((size_t)mm * ne);
+  h->KV = a.take<double>((size_t)mm * ne);
+  h->GV = a.take<double>((size_t)mm * ne);
+  h->EW = a.take<double>((size_t)4 * nb * ne);   // X, KX, GX, W blocks
+  h->EKW = a.take<double>((size_t)2 * nb * ne);
+  h->EGW = a.take<double>((size_t)nb * ne);
+  h->Hs = a.take<double>((size_t)mm * mm);
+  h->Bs = a.take<double>((size_t)mm * mm);
+  h->Ys = a.take<double>((size_t)mm * mm);
+  h->Cs = a.take<double>((size_t)mm * mm);
+  const int64_t gp_rows = std::max<int64_t>(gram_partial_blocks(ne), gram_partial_blocks(nf));
+  h->gram_partial = a.take<double>((size_t)gp_rows * mm * std::max(mm, nb));
+  h->dscal = a.take<double>(1024);
+}
+
+int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
+  if (!d || !out) return TOBK_E_ARG;
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return TOBK_E_ARG;
+  if (d->mg_levels < 1 || d->mg_levels > kMaxLevels) return TOBK_E_ARG;
+  if (d->eig_level < 1 || d->eig_level > d->mg_levels) return TOBK_E_ARG;
+  if (d->num_modes < 1 || d->num_modes > 48) return TOBK_E_ARG;
+  if (d->nu_pre < 1 || d->nu_post < 0 || !(d->omega > 0.0) || !(d->rtol > 0.0) || d->max_iter < 1) return TOBK_E_ARG;
+  if (!(d->nu > -1.0 && d->nu < 0.5) || !(d->E0 > 0.0) || !(d->Emin > 0.0) || !(d->penal >= 1.0)) return TOBK_E_ARG;
+  if (d->precision != TOBK_FP64 && d->precision != TOBK_FP32_VCYCLE) return TOBK_E_ARG;
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->nel[a] < 1) return TOBK_E_ARG;
+    if (d->nel[a] % (1 << (d->mg_levels - 1)) != 0) return TOBK_E_ARG;
+  }
+  tobk_handle* h = new tobk_handle();
+  h->desc = *d;
+  h->stream = (cudaStream_t)stream;
+  cudaGetDevice(&h->device);
+  h->dim = d->dim;
+  h->L = d->mg_levels;
+  h->eig = d->eig_level - 1;
+  h->q = d->num_modes;
+  h->eig_nb = std::min(h->q + 4, 2 * h->q + 2);
+  h->eig_mmax = 4 * h->eig_nb;
+  h->rmax = std::max({d->max_rhs, h->eig_nb, h->q + 1, 1});
+  if (h->rmax > kMaxRhs || h->eig_mmax > 96) {
+    delete h;
+    return TOBK_E_ARG;
+  }
+  h->tab = make_element_tables(d->dim, d->nu);
+  int nel[3] = {d->nel[0], d->nel[1], d->dim == 3 ? d->nel[2] : 1};
+  for (int j = 0; j < h->L; ++j) {
+    h->lv[j].g = make_grid(d->dim, nel);
+    for (int a = 0; a < d->dim; ++a) nel[a] /= 2;
+  }
+  if (h->lv[h->L - 1].g.n > 6000) {
+    delete h;
+    return TOBK_E_ARG;
+  }
+  Arena sizing;
+  sizing.base = nullptr;
+  sizing.cap = ~size_t(0) >> 1;
+  layout(h, sizing);
+  const size_t bytes = sizing.used + 4096;
+  void* base = nullptr;
+  if (cudaMalloc(&base, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return TOBK_E_NOMEM;
+  }
+  h->arena.base = (char*)base;
+  h->arena.cap = bytes;
+  h->arena.used = 0;
+  layout(h, h->arena);
+  if (cudaMallocHost(&h->cg.host_sc, sizeof(double) * kMaxRhs * kScStride) != cudaSuccess ||
+      cudaMallocHost(&h->hscal, sizeof(double) * 1024) != cudaSuccess ||
+      cudaMallocHost(&h->small_host, sizeof(double) * 4 * 96 * 96) != cudaSuccess) {
+    cudaGetLastError();
+    destroy_handle(h);
+    return TOBK_E_NOMEM;
+  }
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(h->arena.base, 0, bytes, s);
+  cudaMemcpyAsync(h->d_Ke0, h->tab.Ke0.data(), sizeof(double) * h->tab.Ke0.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->d_W, h->tab.W.data(), sizeof(double) * h->tab.W.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->d_dN, h->tab.dN.data(), sizeof(double) * h->tab.dN.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->d_D, h->tab.D.data(), sizeof(double) * h->tab.D.size(), cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  if (check_cuda(h, "tobk_create") != TOBK_OK) {
+    destroy_handle(h);
+    return TOBK_E_CUDA;
+  }
+  *out = h;
+  return TOBK_OK;
+}
+
+void destroy_handle(tobk_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->arena.base) cudaFree(h->arena.base);
+  if (h->cg.host_sc) cudaFreeHost(h->cg.host_sc);
+  if (h->hscal) cudaFreeHost(h->hscal);
+  if (h->small_host) cudaFreeHost(h->small_host);
+  delete h;
+}
+
+// ================================================================================================
+// inputs
+// ================================================================================================
+static int copy_in(tobk_handle* h, void* dst, const void* src, size_t bytes, bool on_device) {
+  cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  return check_cuda(h, "copy");
+}
+
+int set_densities(tobk_handle* h, const double* x, bool on_device) {
+  const int64_t m = h->lv[0].g.m;
+  if (!x) return fail(h, TOBK_E_ARG, "null densities");
+  if (!on_device) {
+    for (int64_t e = 0; e < m; ++e)
+      if (!(x[e] >= 0.0 && x[e] <= 1.0)) return fail(h, TOBK_E_ARG, "density not finite or outside [0,1]");
+  }
+  int rc = copy_in(h, h->x, x, sizeof(double) * m, on_device);
+  if (rc) return rc;
+  h->have_x = true;
+  h->setup_done = h->have_u = h->have_G = h->have_modes = h->have_sens = false;
+  return TOBK_OK;
+}
+
+int set_load(tobk_handle* h, const double* f, bool on_device) {
+  if (!f) return fail(h, TOBK_E_ARG, "null load");
+  int rc = copy_in(h, h->f, f, sizeof(double) * h->lv[0].g.n, on_device);
+  if (rc) return rc;
+  h->have_f = true;
+  h->have_u = h->have_G = h->have_modes = h->have_sens = false;
+  return TOBK_OK;
+}
+
+__global__ void k_coarsen_fixed(Grid gf, Grid gc, const uint8_t* ff, uint8_t* fc) {
+  const int64_t cn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cn >= gc.nnode) return;
+  const int I = (int)(cn % gc.nn[0]);
+  const int64_t t = cn / gc.nn[0];
+  const int J = (int)(t % gc.nn[1]);
+  const int K = (int)(t / gc.nn[1]);
+  const int64_t fn = 2 * I + (int64_t)gf.nn[0] * (2 * J + (int64_t)gf.nn[1] * 2 * K);
+  for (int c = 0; c < gc.dim; ++c) fc[gc.dim * cn + c] = ff[gf.dim * fn + c] ? 1 : 0;
+}
+
+__global__ void k_normalize_fixed(uint8_t* f, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = f[i] ? 1 : 0;
+}
+
+int set_fixed(tobk_handle* h, const uint8_t* fixed, bool on_device) {
+  if (!fixed) return fail(h, TOBK_E_ARG, "null fixed mask");
+  const int64_t n = h->lv[0].g.n;
+  int rc = copy_in(h, h->lv[0].fixed, fixed, n, on_device);
+  if (rc) return rc;
+  k_normalize_fixed<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->lv[0].fixed, n);
+  for (int j = 1; j < h->L; ++j) {
+    const Grid& gc = h->lv[j].g;
+    k_coarsen_fixed<<<(unsigned)((gc.nnode + 255) / 256), 256, 0, h->stream>>>(h->lv[j - 1].g, gc, h->lv[j - 1].fixed,
+                                                                                h->lv[j].fixed);
+  }
+  h->have_fixed = true;
+  h->setup_done = h->have_u = h->have_G = h->have_modes = h->have_sens = false;
+  return check_cuda(h, "set_fixed");
+}
+
+// ================================================================================================
+// hierarchy
+// ================================================================================================
+LevelOpDesc level_op(tobk_handle* h, int j) {
+  LevelOpDesc d{};
+  d.g = h->lv[j].g;
+  d.fixed = h->lv[j].fixed;
+  if (j == 0) {
+    d.stored = false;
+    d.scale64 = h->Ek;
+    d.scale32 = h->Ek32;
+    d.T0 = h->tab.Ke0.data();
+    d.T0dev = h->d_Ke0;
+  } else {
+    d.stored = true;
+    d.Ke64 = h->lv[j].Ke;
+    d.Ke32 = h->lv[j].Ke32;
+  }
+  return d;
+}
+
+int setup_hierarchy(tobk_handle* h) {
+  if (!h->have_x) return fail(h, TOBK_E_STATE, "densities not set");
+  if (!h->have_fixed) return fail(h, TOBK_E_STATE, "fixed DOFs not set");
+  cudaStream_t s = h->stream;
+  const tobk_desc& d = h->desc;
+  const bool mixed = d.precision == TOBK_FP32_VCYCLE;
+  const Grid& g0 = h->lv[0].g;
+  launch_simp(h->x, g0.m, d.penal, d.E0, d.Emin, h->Ek, h->Es, h->dEk, h->dEs, h->Ek32, s);
+  launch_diag(level_op(h, 0), h->lv[0].dinv, mixed ? h->lv[0].dinv32 : nullptr, s);
+  const int nd2 = h->tab.nd * h->tab.nd;
+  for (int j = 1; j < h->L; ++j) {
+    Level& Lc = h->lv[j];
+    const Level& Lf = h->lv[j - 1];
+    if (j == 1)
+      launch_galerkin_fine_K(Lf.g, Lc.g, Lf.fixed, h->Ek, h->d_Ke0, h->d_W, Lc.Ke, s);
+    else
+      launch_galerkin_stored(Lf.g, Lc.g, Lf.fixed, Lf.Ke, h->d_W, Lc.Ke, s);
+    if (mixed) launch_f64_to_f32(Lc.Ke, Lc.Ke32, Lc.g.m * nd2, s);
+    launch_diag(level_op(h, j), Lc.dinv, mixed ? Lc.dinv32 : nullptr, s);
+  }
+  const int jc = h->L - 1;
+  launch_dense_assemble(level_op(h, jc), h->Adense, s);
+  h->Ainv = launch_dense_invert(h->Adense, h->Awork, h->lv[jc].g.n, s);
+  int rc = check_cuda(h, "setup_hierarchy");
+  if (rc) return rc;
+  h->setup_done = true;
+  return TOBK_OK;
+}
+
+// ================================================================================================
+// V-cycle (multigrid preconditioner)
+// ================================================================================================
+static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* z, double* t) {
+  cudaStream_t s = h->stream;
+  Level& L = h->lv[j];
+  const int64_t n = L.g.n;
+  const double om = h->desc.omega;
+  if (j == h->L - 1) {
+    launch_dense_gemv(h->Ainv, b, z, n, nr, n, s);
+    return z;
+  }
+  const LevelOpDesc op = level_op(h, j);
+  launch_jacobi0(b, L.dinv, z, om, n, nr, n, s);
+  for (int it = 1; it < h->desc.nu_pre; ++it) {
+    launch_apply(op, APPLY_JAC, z, b, L.dinv, t, om, nr, n, s);
+    std::swap(z, t);
+  }
+  launch_apply(op, APPLY_RES, z, b, nullptr, L.r, 0.0, nr, n, s);
+  Level& C = h->lv[j + 1];
+  launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s);
+  double* zc = vcycle64(h, j + 1, nr, C.b, C.z, C.t);
+  launch_prolong_add(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
+  for (int it = 0; it < h->desc.nu_post; ++it) {
+    launch_apply(op, APPLY_JAC, z, b, L.dinv, t, om, nr, n, s);
+    std::swap(z, t);
+  }
+  return z;
+}
+
+static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, float* t) {
+  cudaStream_t s = h->stream;
+  Level& L = h->lv[j];
+  const int64_t n = L.g.n;
+  const float om = (float)h->desc.omega;
+  if (j == h->L - 1) {
+    launch_dense_gemv32(h->Ainv, b, z, n, nr, n, s);
+    return z;
+  }
+  const LevelOpDesc op = level_op(h, j);
+  launch_jacobi0_32(b, L.dinv32, z, om, n, nr, n, s);
+  for (int it = 1; it < h->desc.nu_pre; ++it) {
+    launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, om, nr, n, s);
+    std::swap(z, t);
+  }
+  launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, 0.0f, nr, n, s);
+  Level& C = h->lv[j + 1];
+  launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s);
+  float* zc = vcycle32(h, j + 1, nr, C.b32, C.z32, C.t32);
+  launch_prolong_add32(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
+  for (int it = 0; it < h->desc.nu_post; ++it) {
+    launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, om, nr, n, s);
+    std::swap(z, t);
+  }
+  return z;
+}
+
+// z = M r at level s (FP64 result in one of z / zt)
+static double* precondition(tobk_handle* h, int s, int nr, const double* r, double* z, double* zt, int precision) {
+  if (precision == TOBK_FP64) return vcycle64(h, s, nr, r, z, zt);
+  Level& L = h->lv[s];
+  const int64_t n = L.g.n;
+  launch_f64_to_f32(r, L.b32, (int64_t)nr * n, h->stream);
+  float* z32 = vcycle32(h, s, nr, L.b32, L.z32, L.t32);
+  launch_f32_to_f64(z32, z, (int64_t)nr * n, h->stream);
+  return z;
+}
+
+// ================================================================================================
+// multi-RHS preconditioned CG
+// ================================================================================================
+int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
+              int precision, tobk_solve_info* info) {
+  if (nr < 1 || nr > h->rmax) return fail(h, TOBK_E_ARG, "bad RHS count");
+  if (!h->setup_done) {
+    int rc = setup_hierarchy(h);
+    if (rc) return rc;
+  }
+  cudaStream_t st = h->stream;
+  const LevelOpDesc op = level_op(h, s);
+  const int64_t n = op.g.n;
+  CGWork& w = h->cg;
+  double* p_old = w.p0;
+  double* p_new = w.p1;
+  cudaMemsetAsync(p_old, 0, sizeof(double) * nr * n, st);
+  cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  const bool flexible = precision != TOBK_FP64;
+  int total_it = 0;
+  int rc = TOBK_OK;
+  double worst = 0.0;
+  bool all_conv = true;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    launch_cg_init(op, B, X, w.r, use_x0 || attempt > 0, rtol, nr, n, w.sc, w.partial, w.counters, st);
+    if (attempt > 0) {
+      cudaMemsetAsync(p_old, 0, sizeof(double) * nr * n, st);
+      cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+    }
+    const int check_every = 2;
+    for (int it = 0; it < max_iter; ++it) {
+      double* z = precondition(h, s, nr, w.r, w.z, w.zt, precision);
+      launch_cg_dots(n, z, w.r, w.q, p_old, flexible, nr, n, w.sc, w.partial, w.counters, st);
+      launch_cg_direction(op, z, p_old, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
+      launch_cg_update(n, X, w.r, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
+      std::swap(p_old, p_new);
+      ++total_it;
+      if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
+        cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        bool any = false;
+        for (int r = 0; r < nr; ++r) any |= w.host_sc[r * kScStride + SC_ACTIVE] != 0.0;
+        if (!any) break;
+      }
+    }
+    cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    int status = 0;
+    for (int r = 0; r < nr; ++r) status = std::max(status, (int)w.host_sc[r * kScStride + SC_STATUS]);
+    // true residual recomputed at exit
+    launch_true_residual(op, B, X, w.zt, nr, n, w.sc, w.partial, w.counters, st);
+    cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    rc = check_cuda(h, "pcg_solve");
+    if (rc) break;
+    worst = 0.0;
+    all_conv = true;
+    for (int r = 0; r < nr; ++r) {
+      const double rel = w.host_sc[r * kScStride + SC_RELRES];
+      worst = std::max(worst, std::isfinite(rel) ? rel : INFINITY);
+      if (!(rel <= rtol)) all_conv = false;
+    }
+    if (status == 1) {
+      rc = fail(h, TOBK_E_BREAKDOWN, "CG breakdown: p^T K p <= 0");
+      break;
+    }
+    if (status == 2 || !std::isfinite(worst)) {
+      rc = fail(h, TOBK_E_NONFINITE, "non-finite value in CG");
+      break;
+    }
+    if (all_conv || total_it >= max_iter) break;
+    // the recursive residual met the target but the true one did not: restart from X
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = total_it;
+    info->converged = all_conv ? 1 : 0;
+    info->num_rhs = nr;
+    info->rel_residual = worst;
+    info->time_ms = ms;
+    info->status_detail = 0;
+  }
+  if (rc == TOBK_OK && !all_conv) rc = fail(h, TOBK_E_NOT_CONVERGED, "CG iteration limit reached");
+  return rc;
+}
+
+void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride) {
+  launch_apply(level_op(h, j), APPLY_KV, v, nullptr, nullptr, y, 0.0, nr, stride, h->stream);
+}
+
+void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride) {
+  if (j == 0) {
+    launch_apply_kron(h->lv[0].g, h->lv[0].fixed, h->Gs, v, y, nr, stride, h->stream);
+  } else {
+    LevelOpDesc d{};
+    d.g = h->lv[j].g;
+    d.fixed = h->lv[j].fixed;
+    d.stored = true;
+    d.Ke64 = h->lv[j].Ge;
+    launch_apply(d, APPLY_KV, v, nullptr, nullptr, y, 0.0, nr, stride, h->stream);
+  }
+}
+
+// ================================================================================================
+// linear analysis and stress stiffness
+// ================================================================================================
+int setup_stress(tobk_handle* h) {
+  cudaStream_t s = h->stream;
+  const Grid& g = h->lv[0].g;
+  launch_stress_gs_dev(g, h->u, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->Gs0, h->Gs, s);
+  for (int j = 1; j <= h->eig; ++j) {
+    Level& Lc = h->lv[j];
+    const Level& Lf = h->lv[j - 1];
+    if (j == 1)
+      launch_galerkin_fine_G(Lf.g, Lc.g, Lf.fixed, h->Gs, h->d_W, Lc.Ge, s);
+    else
+      launch_galerkin_stored(Lf.g, Lc.g, Lf.fixed, Lf.Ge, h->d_W, Lc.Ge, s);
+  }
+  int rc = check_cuda(h, "setup_stress");
+  if (rc) return rc;
+  h->have_G = true;
+  return TOBK_OK;
+}
+
+int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info) {
+  if (!h->have_x || !h->have_f || !h->have_fixed) return fail(h, TOBK_E_STATE, "densities, load and fixed DOFs must be set");
+  if (!h->setup_done) {
+    int rc = setup_hierarchy(h);
+    if (rc) return rc;
+  }
+  cudaStream_t s = h->stream;
+  const int64_t n = h->lv[0].g.n;
+  launch_mask_copy(h->f, h->lv[0].fixed, h->bwork, n, 1, n, s);
+  if (h->have_u0) cudaMemcpyAsync(h->u, h->u0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  int rc = pcg_solve(h, 0, h->bwork, h->u, 1, h->desc.rtol, h->desc.max_iter, h->have_u0, h->desc.precision, info);
+  if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+  launch_gram(h->bwork, 1, h->u, 1, n, n, h->dscal, h->gram_partial, s);
+  cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  h->compliance = h->hscal[0];
+  if (compliance) *compliance = h->compliance;
+  int rc2 = setup_stress(h);
+  if (rc2) return rc2;
+  h->have_u = true;
+  h->have_modes = h->have_sens = false;
+  return rc;
+}
+
+}  // namespace tobk

@@ -1,0 +1,122 @@
+// Internal declarations of the GB300 multilevel buckling solver library (not part of the C-ABI).
+//
+// Data layout in device memory (all levels):
+//   element (i,j,k) -> e = i + nelx*(j + nely*k); node (i,j,k) -> a = i + nnx*(j + nny*k);
+//   DOF c of node a -> d*a + c (node-interleaved).  Multi-RHS blocks are RHS-major: [r][n].
+//   Dirichlet DOFs hold 0 in every vector the solver produces.
+// Level 1 (fine) operators are matrix-free: y = sum_e E_kappa(x_e) K_e0 v_e (paper Sec. 2).
+// Levels >= 2 store one dense (d 2^d)^2 element matrix per coarse element: the Galerkin product
+// P^T K P of nested bi/trilinear grids assembles element by element (paper Sec. 2.1 step 1).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+namespace tobk {
+
+constexpr int kMaxLevels = 12;
+constexpr int kMaxRhs = 64;      // RHS per multi-RHS solve (per-kernel reduction counters)
+constexpr int kNumCounterSets = 6;
+constexpr int kScStride = 16;  // doubles of per-RHS scalar state in the CG driver
+
+// per-RHS CG scalar slots
+enum ScSlot {
+  SC_ZR = 0,      // z.r of the current iteration
+  SC_ZQ = 1,      // z.q_old (flexible beta)
+  SC_PR = 2,      // p_old.r
+  SC_PQ = 3,      // p.q of the current direction
+  SC_ALPHA = 4,
+  SC_BETA = 5,
+  SC_RR = 6,      // r.r
+  SC_BB = 7,      // b.b (free DOFs)
+  SC_RELRES = 8,  // sqrt(r.r / b.b)
+  SC_ACTIVE = 9,  // 1: iterating, 0: converged or stopped
+  SC_ITERS = 10,
+  SC_ZR_OLD = 11,
+  SC_PQ_OLD = 12,
+  SC_STATUS = 13, // 0 ok, 1 breakdown (p.q <= 0), 2 non-finite
+  SC_RTOL = 14,
+};
+
+struct Grid {
+  int dim;
+  int nel[3];
+  int nn[3];
+  int64_t m;      // elements
+  int64_t nnode;  // nodes
+  int64_t n;      // DOFs
+};
+
+inline Grid make_grid(int dim, const int nel[3]) {
+  Grid g;
+  g.dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    g.nel[a] = (a < dim) ? nel[a] : 1;
+    g.nn[a] = (a < dim) ? nel[a] + 1 : 1;
+  }
+  g.m = (int64_t)g.nel[0] * g.nel[1] * g.nel[2];
+  g.nnode = (int64_t)g.nn[0] * g.nn[1] * g.nn[2];
+  g.n = g.nnode * dim;
+  return g;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Element tables computed on the host (Gauss quadrature written independently for this library).
+// ------------------------------------------------------------------------------------------------
+struct ElementTables {
+  int dim, nn, nd, ngp, nv;
+  std::vector<double> Ke0;  // [nd*nd] unit-modulus stiffness
+  std::vector<double> dN;   // [ngp][dim][nn] shape-function gradients in physical coordinates
+  std::vector<double> D;    // [nv*nv] unit-modulus constitutive matrix
+  double wdet;              // Gauss weight x |J| (same at every Gauss point)
+  std::vector<double> W;    // [2^dim children][nn child nodes][nn coarse nodes] interpolation weights
+};
+ElementTables make_element_tables(int dim, double nu);
+
+// ------------------------------------------------------------------------------------------------
+// device memory arena (one cudaMalloc per handle)
+// ------------------------------------------------------------------------------------------------
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = ((count * sizeof(T)) + 255) & ~size_t(255);
+    if (used + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+struct Level {
+  Grid g;
+  uint8_t* fixed = nullptr;   // [n]
+  // stored Galerkin element matrices (levels >= 2)
+  double* Ke = nullptr;       // [m][nd*nd]
+  float* Ke32 = nullptr;      // FP32 copy for the mixed-precision V-cycle
+  double* Ge = nullptr;       // [m][nd*nd] Galerkin G (only down to the eigen level)
+  double* dinv = nullptr;     // [n] inverse diagonal (0 at fixed DOFs)
+  float* dinv32 = nullptr;
+  // V-cycle work vectors, capacity rmax RHS: b, z, t (ping-pong), r
+  double *b = nullptr, *z = nullptr, *t = nullptr, *r = nullptr;
+  float *b32 = nullptr, *z32 = nullptr, *t32 = nullptr, *r32 = nullptr;
+};
+
+// Multi-RHS PCG work space for solves that start at a given level.
+struct CGWork {
+  double *x, *r, *z, *zt, *p0, *p1, *q;
+  double* sc;          // [rmax][kScStride]
+  double* partial;     // reduction partials
+  unsigned* counters;  // last-block counters
+  double* host_sc;     // pinned host copy of sc
+};
+
+}  // namespace tobk
+
+// The opaque handle of the C-ABI.
+struct tobk_handle;
