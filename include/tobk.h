@@ -84,7 +84,7 @@ typedef struct {
                         at most 6000 DOFs) */
   int eig_level;     /* 1-based level of the buckling eigenproblem: 1 = exact LBA on the fine grid
                         (Algorithm 1), l > 1 = multilevel procedure of Sec. 2.1 with Omega_l */
-  int num_modes;     /* q, number of buckling modes / load factors (<= 48) */
+  int num_modes;     /* q, number of buckling modes / load factors (<= 24) */
   int precision;     /* tobk_precision of the V-cycle */
   double rtol;       /* CG stop: ||f - K u||_2 / ||f||_2 <= rtol over free DOFs (e.g. 1e-8) */
   int max_iter;      /* CG iteration limit per solve */

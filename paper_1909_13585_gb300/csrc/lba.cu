@@ -1,20 +1,445 @@
-// Buckling analysis and sensitivities (placeholder until the eigensolver lands).
+// Linearized buckling analysis and sensitivities on the GPU.
+//
+//   exact LBA (eig_level 1) ........ Algorithm 1: eigenpairs of (K + lambda G) phi = 0 on Omega_1
+//   multilevel LBA (eig_level l) .... Sec. 2.1 steps 1-4 / Algorithm 2 lines 5-18 without the
+//                                     optional per-level smoothing: coarse Galerkin eigenpairs,
+//                                     Psi^j = I^j_{j+1} Psi^{j+1}, fine solve K Phi = G Psi,
+//                                     Rayleigh quotients (eq. FineScaleRQ)
+//   adjoint right-hand sides ........ phi^T (grad_u G) phi (eq. AdjointSystem)
+//   sensitivities ................... eq. SensitivityLambda with the factor -1/(phi^T G phi)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "device_common.cuh"
 #include "handle.h"
 
 namespace tobk {
 
-int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
-  (void)lambda;
-  (void)info;
-  return fail(h, TOBK_E_STATE, "buckling analysis not available in this build");
+void launch_coldots(const double* A, const double* B, int ncols, int64_t n, int64_t stride, double* out,
+                    double* partial, cudaStream_t s);
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------------------------------------
+// mode post-processing: scale to phi^T K phi = 1, sign (largest-magnitude entry positive), order
+// ------------------------------------------------------------------------------------------------
+// per column: index of the entry of largest magnitude (smallest index on ties), two stages
+__global__ void k_argmax_partial(const double* A, int64_t n, int64_t stride, double* pv, long long* pi) {
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  const int col = blockIdx.y;
+  double best = -1.0;
+  long long bi = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = fabs(A[(int64_t)col * stride + k]);
+    if (v > best) {
+      best = v;
+      bi = k;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double a = sv[threadIdx.x], b = sv[threadIdx.x + o];
+      const long long ia = si[threadIdx.x], ib = si[threadIdx.x + o];
+      if (b > a || (b == a && ib < ia)) {
+        sv[threadIdx.x] = b;
+        si[threadIdx.x] = ib;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[(size_t)col * gridDim.x + blockIdx.x] = sv[0];
+    pi[(size_t)col * gridDim.x + blockIdx.x] = si[0];
+  }
 }
 
-int compute_sensitivities(tobk_handle* h, double* dlam, double* dJ, bool out_on_device, tobk_solve_info* info) {
-  (void)dlam;
-  (void)dJ;
-  (void)out_on_device;
-  (void)info;
-  return fail(h, TOBK_E_STATE, "sensitivities not available in this build");
+// One thread: per column the sign entry, the scale 1/sqrt(num) and the ascending order of lambda.
+// lam_in[i] = lambda of column i; num[i] = phi_i^T K phi_i.  Outputs: perm[r] = source column of
+// rank r, scale[r], lam_out[r].
+__global__ void k_order_modes(const double* A, int64_t stride, const double* pv, const long long* pi, int chunks,
+                              const double* lam_in, const double* num, int q, int* perm, double* scale,
+                              double* lam_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int order[64];
+  for (int i = 0; i < q; ++i) order[i] = i;
+  for (int i = 1; i < q; ++i) {  // insertion sort, stable
+    const int c = order[i];
+    int k = i - 1;
+    while (k >= 0 && lam_in[order[k]] > lam_in[c]) {
+      order[k + 1] = order[k];
+      --k;
+    }
+    order[k + 1] = c;
+  }
+  for (int r = 0; r < q; ++r) {
+    const int c = order[r];
+    double best = -1.0;
+    long long bi = 0;
+    for (int b = 0; b < chunks; ++b) {
+      const double v = pv[(size_t)c * chunks + b];
+      const long long ii = pi[(size_t)c * chunks + b];
+      if (v > best || (v == best && ii < bi)) {
+        best = v;
+        bi = ii;
+      }
+    }
+    const double sg = A[(int64_t)c * stride + bi] < 0.0 ? -1.0 : 1.0;
+    perm[r] = c;
+    scale[r] = sg / sqrt(num[c]);
+    lam_out[r] = lam_in[c];
+  }
+}
+
+__global__ void k_permute_scale(const double* A, const int* perm, const double* scale, double* B, int64_t n,
+                                int64_t stride) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int r = blockIdx.y;
+  B[(int64_t)r * stride + k] = scale[r] * A[(int64_t)perm[r] * stride + k];
+}
+
+__global__ void k_rq(const double* num, const double* den, int q, double* lam) {
+  const int i = threadIdx.x;
+  if (i < q) lam[i] = -num[i] / den[i];
+}
+
+// Normalises the q columns of A (length n) into `out` (may alias neither): K scaling, sign, order.
+static void finalize_modes(tobk_handle* h, const double* A, const double* lam_dev, const double* num_dev, double* out,
+                           double* lam_out_dev) {
+  cudaStream_t st = h->stream;
+  const int64_t n = h->lv[0].g.n;
+  const int q = h->q;
+  const int chunks = 64;
+  double* pv = h->gram_partial;
+  long long* pi = (long long*)(h->gram_partial + (size_t)q * chunks);
+  k_argmax_partial<<<dim3(chunks, q), 256, 0, st>>>(A, n, n, pv, pi);
+  int* perm = (int*)(h->dscal + 640);
+  double* scale = h->dscal + 704;
+  k_order_modes<<<1, 32, 0, st>>>(A, n, pv, pi, chunks, lam_dev, num_dev, q, perm, scale, lam_out_dev);
+  k_permute_scale<<<dim3(nblk(n), q), 256, 0, st>>>(A, perm, scale, out, n, n);
+}
+
+int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
+  if (!h->have_u || !h->have_G) return fail(h, TOBK_E_STATE, "solve_equilibrium must come first");
+  cudaStream_t st = h->stream;
+  const int q = h->q;
+  const int64_t n = h->lv[0].g.n;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  tobk_solve_info ei{};
+  double lam_h[64];
+  int rc = TOBK_OK;
+  double* num = h->dscal + 768;   // [q]
+  double* den = h->dscal + 832;   // [q]
+  double* lraw = h->dscal + 896;  // [q]
+  if (h->eig == 0) {
+    // Algorithm 1 EA on the fine grid
+    double* Phi = h->lv[0].b;     // [q][n] scratch
+    rc = eigen_solve(h, 0, q, Phi, lam_h, &ei);
+    if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+    double* KP = h->xwork;
+    apply_K_level(h, 0, Phi, KP, q, n);
+    launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
+    cudaMemcpyAsync(lraw, lam_h, sizeof(double) * q, cudaMemcpyHostToDevice, st);
+    finalize_modes(h, Phi, lraw, num, h->modes, h->lam);
+  } else {
+    // Sec. 2.1 step 1: coarse eigenpairs on Omega_l of the Galerkin pencil
+    const int l = h->eig;
+    double* Psi = h->lv[l].b;
+    rc = eigen_solve(h, l, q, Psi, lam_h, &ei);
+    if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+    // step 2: Psi^j = I^j_{j+1} Psi^{j+1}
+    for (int j = l; j >= 1; --j) {
+      Level& C = h->lv[j];
+      Level& F = h->lv[j - 1];
+      cudaMemsetAsync(F.b, 0, sizeof(double) * q * F.g.n, st);
+      launch_prolong_add(F.g, C.g, F.fixed, C.b, F.b, q, F.g.n, C.g.n, st);
+    }
+    // step 3: K Phi = G Psi (one multi-RHS mgPCG solve on the fine grid)
+    double* rhs = h->bwork;
+    apply_G_level(h, 0, h->lv[0].b, rhs, q, n);
+    double* Phi = h->xwork;
+    tobk_solve_info si{};
+    int src = pcg_solve(h, 0, rhs, Phi, q, h->desc.rtol, h->desc.max_iter, false, h->desc.precision, &si);
+    if (src && src != TOBK_E_NOT_CONVERGED) return src;
+    // step 4: Rayleigh quotients lambda_i = -phi^T K phi / phi^T G phi
+    double* KP = h->lv[0].z;
+    double* GP = h->lv[0].t;
+    apply_K_level(h, 0, Phi, KP, q, n);
+    apply_G_level(h, 0, Phi, GP, q, n);
+    launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
+    launch_coldots(Phi, GP, q, n, n, den, h->gram_partial, st);
+    k_rq<<<1, 64, 0, st>>>(num, den, q, lraw);
+    finalize_modes(h, Phi, lraw, num, h->modes, h->lam);
+    ei.iterations += si.iterations;
+  }
+  cudaMemcpyAsync(h->hscal, h->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  int crc = check_cuda(h, "compute_buckling");
+  if (crc) return crc;
+  for (int i = 0; i < q; ++i) h->lam_host[i] = h->hscal[i];
+  if (lambda)
+    for (int i = 0; i < q; ++i) lambda[i] = h->lam_host[i];
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    *info = ei;
+    info->time_ms = ms;
+  }
+  h->have_modes = true;
+  h->have_sens = false;
+  return rc;
+}
+
+// ------------------------------------------------------------------------------------------------
+// adjoint right-hand side  b = phi^T (grad_u G) phi
+//   element part: sum_gp w|J| B^T D h(phi_e),  h = Voigt(sum_c d_a phi_c d_b phi_c), shear doubled
+// ------------------------------------------------------------------------------------------------
+template <int DIM>
+__global__ void k_adjoint_gp(Grid g, const double* __restrict__ phi, const double* __restrict__ Es,
+                             const double* __restrict__ dN, const double* __restrict__ D, double wdet,
+                             double* __restrict__ sgp) {
+  constexpr int NN = Dims<DIM>::NN, NV = Dims<DIM>::NV;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.m) return;
+  const int ei = (int)(e % g.nel[0]);
+  const int64_t rest = e / g.nel[0];
+  const int ej = (int)(rest % g.nel[1]);
+  const int ek = (int)(rest / g.nel[1]);
+  const int64_t n0 = ei + (int64_t)g.nn[0] * (ej + (int64_t)g.nn[1] * ek);
+  double pe[NN][DIM];
+#pragma unroll
+  for (int l = 0; l < NN; ++l) {
+    const int64_t nb = n0 + corner_x(l) + (int64_t)g.nn[0] * (corner_y(l) + (int64_t)g.nn[1] * corner_z(l));
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) pe[l][c] = phi[DIM * nb + c];
+  }
+  const double es = Es[e] * wdet;
+  for (int gp = 0; gp < NN; ++gp) {
+    const double* dn = dN + gp * DIM * NN;
+    double Gr[DIM][DIM];  // Gr[a][c] = d phi_c / d x_a
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < NN; ++l) s += dn[a * NN + l] * pe[l][c];
+        Gr[a][c] = s;
+      }
+    double Hm[DIM][DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) s += Gr[a][c] * Gr[b][c];
+        Hm[a][b] = s;
+      }
+    double hv[NV];
+    if (DIM == 2) {
+      hv[0] = Hm[0][0];
+      hv[1] = Hm[1][1];
+      hv[2] = 2.0 * Hm[0][1];
+    } else {
+      hv[0] = Hm[0][0];
+      hv[1] = Hm[1][1];
+      hv[2] = Hm[DIM - 1][DIM - 1];
+      hv[3] = 2.0 * Hm[0][1];
+      hv[4] = 2.0 * Hm[1][DIM - 1];
+      hv[5] = 2.0 * Hm[DIM - 1][0];
+    }
+#pragma unroll
+    for (int p = 0; p < NV; ++p) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) s += D[p * NV + q] * hv[q];
+      sgp[(e * NN + gp) * NV + p] = es * s;
+    }
+  }
+}
+
+// b[a,c] = sum_{e adj a} sum_gp (B(gp)^T s_{e,gp})[local row of (a,c)]  (masked)
+template <int DIM>
+__global__ void k_adjoint_gather(Grid g, const uint8_t* __restrict__ fixed, const double* __restrict__ sgp,
+                                 const double* __restrict__ dN, double* __restrict__ b) {
+  constexpr int NN = Dims<DIM>::NN, NV = Dims<DIM>::NV;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!node_coords(g, node, i, j, k)) return;
+  double acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        const int ei = i - cx, ej = j - cy, ek = k - cz;
+        if (ei < 0 || ei >= g.nel[0] || ej < 0 || ej >= g.nel[1]) continue;
+        if (DIM == 3 && (ek < 0 || ek >= g.nel[2])) continue;
+        const int64_t e = ei + (int64_t)g.nel[0] * (ej + (int64_t)g.nel[1] * ek);
+        const int ln = local_node(cx, cy, cz);
+        for (int gp = 0; gp < NN; ++gp) {
+          const double* s = sgp + (e * NN + gp) * NV;
+          const double* dn = dN + gp * DIM * NN;
+          const double dx = dn[0 * NN + ln], dy = dn[1 * NN + ln];
+          if (DIM == 2) {
+            acc[0] += dx * s[0] + dy * s[2];
+            acc[1] += dy * s[1] + dx * s[2];
+          } else {
+            const double dz = dn[(DIM - 1) * NN + ln];
+            acc[0] += dx * s[0] + dy * s[3] + dz * s[5];
+            acc[1] += dy * s[1] + dx * s[3] + dz * s[4];
+            acc[DIM - 1] += dz * s[2] + dy * s[4] + dx * s[5];
+          }
+        }
+      }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t idx = DIM * node + c;
+    b[idx] = fixed[idx] ? 0.0 : acc[c];
+  }
+}
+
+// per element: dJ and, for every mode, dlambda (eq. SensitivityLambda with -1/(phi^T G phi))
+template <int DIM>
+__global__ void k_sensitivities(Grid g, int q, const double* __restrict__ u, const double* __restrict__ modes,
+                                const double* __restrict__ adj, const double* __restrict__ Gs0,
+                                const double* __restrict__ Ke0, const double* __restrict__ dEk,
+                                const double* __restrict__ dEs, const double* __restrict__ lam,
+                                const double* __restrict__ pGp_glob, double* __restrict__ dlam,
+                                double* __restrict__ dJ) {
+  constexpr int NN = Dims<DIM>::NN, ND = Dims<DIM>::ND;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.m) return;
+  const int ei = (int)(e % g.nel[0]);
+  const int64_t rest = e / g.nel[0];
+  const int ej = (int)(rest % g.nel[1]);
+  const int ek = (int)(rest / g.nel[1]);
+  const int64_t n0 = ei + (int64_t)g.nn[0] * (ej + (int64_t)g.nn[1] * ek);
+  int64_t dof[ND];
+#pragma unroll
+  for (int l = 0; l < NN; ++l) {
+    const int64_t nb = n0 + corner_x(l) + (int64_t)g.nn[0] * (corner_y(l) + (int64_t)g.nn[1] * corner_z(l));
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) dof[l * DIM + c] = DIM * nb + c;
+  }
+  double Ku[ND];
+  double uKu = 0.0;
+  {
+    double ue[ND];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) ue[a] = u[dof[a]];
+    for (int a = 0; a < ND; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int b = 0; b < ND; ++b) s += Ke0[a * ND + b] * ue[b];
+      Ku[a] = s;
+      uKu += ue[a] * s;
+    }
+  }
+  const double dek = dEk[e], des = dEs[e];
+  dJ[e] = -dek * uKu;
+  const double* G0 = Gs0 + e * NN * NN;
+  const int64_t n = g.n;
+  for (int i = 0; i < q; ++i) {
+    double pe[ND];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) pe[a] = modes[(int64_t)i * n + dof[a]];
+    double pKp = 0.0;
+    for (int a = 0; a < ND; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int b = 0; b < ND; ++b) s += Ke0[a * ND + b] * pe[b];
+      pKp += pe[a] * s;
+    }
+    double pGp = 0.0;
+    for (int a = 0; a < NN; ++a)
+      for (int b = 0; b < NN; ++b) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) s += pe[a * DIM + c] * pe[b * DIM + c];
+        pGp += G0[a * NN + b] * s;
+      }
+    double zKu = 0.0;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) zKu += adj[(int64_t)i * n + dof[a]] * Ku[a];
+    const double li = lam[i];
+    dlam[(int64_t)i * g.m + e] = -(dek * pKp + li * des * pGp - li * dek * zKu) / pGp_glob[i];
+  }
+}
+
+int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool out_on_device,
+                          tobk_solve_info* info) {
+  if (!h->have_modes) return fail(h, TOBK_E_STATE, "compute_buckling must come first");
+  cudaStream_t st = h->stream;
+  const Grid& g = h->lv[0].g;
+  const int64_t n = g.n;
+  const int q = h->q;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  // adjoint right-hand sides, one mode at a time through the element Gauss-point scratch
+  for (int i = 0; i < q; ++i) {
+    const double* phi = h->modes + (size_t)i * n;
+    double* b = h->adj_rhs + (size_t)i * n;
+    if (g.dim == 2) {
+      k_adjoint_gp<2><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
+      k_adjoint_gather<2><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
+    } else {
+      k_adjoint_gp<3><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
+      k_adjoint_gather<3><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
+    }
+  }
+  // adjoint systems K z_i = b_i: one multi-RHS mgPCG solve
+  tobk_solve_info si{};
+  int rc = pcg_solve(h, 0, h->adj_rhs, h->adj, q, h->desc.rtol, h->desc.max_iter, false, h->desc.precision, &si);
+  if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+  // phi_i^T G phi_i
+  double* GP = h->lv[0].z;
+  apply_G_level(h, 0, h->modes, GP, q, n);
+  double* pGp = h->dscal + 960;
+  launch_coldots(h->modes, GP, q, n, n, pGp, h->gram_partial, st);
+  if (g.dim == 2)
+    k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk,
+                                                       h->dEs, h->lam, pGp, h->dlam, h->dJ);
+  else
+    k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk, h->dEs,
+                                                     h->lam, pGp, h->dlam, h->dJ);
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (dlam_out) cudaMemcpyAsync(dlam_out, h->dlam, sizeof(double) * q * g.m, kind, st);
+  if (dJ_out) cudaMemcpyAsync(dJ_out, h->dJ, sizeof(double) * g.m, kind, st);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  int crc = check_cuda(h, "compute_sensitivities");
+  if (crc) return crc;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    *info = si;
+    info->time_ms = ms;
+  }
+  h->have_sens = true;
+  return rc;
 }
 
 }  // namespace tobk

@@ -220,7 +220,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
   if (d->dim != 2 && d->dim != 3) return TOBK_E_ARG;
   if (d->mg_levels < 1 || d->mg_levels > kMaxLevels) return TOBK_E_ARG;
   if (d->eig_level < 1 || d->eig_level > d->mg_levels) return TOBK_E_ARG;
-  if (d->num_modes < 1 || d->num_modes > 48) return TOBK_E_ARG;
+  if (d->num_modes < 1 || d->num_modes > 24) return TOBK_E_ARG;
   if (d->nu_pre < 1 || d->nu_post < 0 || !(d->omega > 0.0) || !(d->rtol > 0.0) || d->max_iter < 1) return TOBK_E_ARG;
   if (!(d->nu > -1.0 && d->nu < 0.5) || !(d->E0 > 0.0) || !(d->Emin > 0.0) || !(d->penal >= 1.0)) return TOBK_E_ARG;
   if (d->precision != TOBK_FP64 && d->precision != TOBK_FP32_VCYCLE) return TOBK_E_ARG;
@@ -236,10 +236,10 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
   h->L = d->mg_levels;
   h->eig = d->eig_level - 1;
   h->q = d->num_modes;
-  h->eig_nb = std::min(h->q + 4, 2 * h->q + 2);
-  h->eig_mmax = 4 * h->eig_nb;
+  h->eig_nb = h->q + 4;
+  h->eig_mmax = std::min(4 * h->eig_nb, 64);
   h->rmax = std::max({d->max_rhs, h->eig_nb, h->q + 1, 1});
-  if (h->rmax > kMaxRhs || h->eig_mmax > 96) {
+  if (h->rmax > kMaxRhs || h->eig_mmax < 2 * h->eig_nb) {
     delete h;
     return TOBK_E_ARG;
   }
