@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the multilevel buckling hot path: DOF x RHS solved per second to relative
+residual 1e-8.
+
+One step = one pass of the whole path over one synthetic design: set densities (SIMP moduli,
+Galerkin hierarchy, coarsest inverse), linear analysis K u = f (1 RHS), stress stiffness, coarse
+Galerkin eigenproblem + prolongation + fine block solve K Phi = G Psi (q RHS) + Rayleigh quotients,
+adjoint right-hand sides + adjoint block solve (q RHS) + sensitivities.  DOF x RHS per step =
+n * (1 + q + q) for the multilevel path (n * (1 + q) for the exact fine-grid path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic  # noqa: E402
+
+METRIC = "DOF*RHS solved/s at rel. residual 1e-8"
+UNIT = "DOF*RHS/s"
+WORKLOAD = "column480x160"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 ALU roofline: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz (maximum SM clock); a
+# register-only FMA probe measured 1.194 TFLOP/s at 1995 MHz, i.e. the same 2 FMA/clk/SM.
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+FP32_PEAK_GFLOPS = 152 * 256 * 2.070
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="one untimed step only (for an external profiler's launch list)")
+    return ap.parse_args()
+
+
+def rhs_per_step(p):
+    return 1 + (2 * p.num_modes if p.eig_level > 1 else p.num_modes)
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): runs in a child process, single-threaded BLAS
+# ------------------------------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import synthetic
+from oracle import lba, sensitivity
+p = synthetic.config({workload!r})
+times = []
+for k in range({reps}):
+    t0 = time.perf_counter()
+    op = lba.Problem(p)
+    u, J = lba.linear_analysis(op)
+    if p.eig_level > 1:
+        ml = lba.multilevel_lba(op, u, p.num_modes, p.eig_level)
+        lam, Phi = ml["lam"], ml["Phi"]
+    else:
+        lam, Phi, _ = lba.exact_lba(op, u, p.num_modes)
+    dlam, dJ, Z = sensitivity.sensitivities(op, u, lam, Phi)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times}}))
+"""
+
+
+def run_oracle(workload, reps):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, workload=workload, reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = synthetic.config(args.workload)
+    units = p.num_dofs * rhs_per_step(p)
+    times = run_oracle(args.workload, args.warmup + args.steps)[args.warmup:]
+    total = sum(times)
+    value = units * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(p, "fp64"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full step of {args.workload} per timed step (SciPy SuperLU + ARPACK, "
+                                   "single-threaded BLAS)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(p, precision):
+    return {"workload": p.name, "dim": p.dim, "nel": list(p.nel[:p.dim]), "dofs": p.num_dofs,
+            "mg_levels": p.mg_levels, "eig_level": p.eig_level, "modes": p.num_modes,
+            "rhs_per_step": rhs_per_step(p), "precision": precision,
+            "l2": "flushed between timed steps (512 MiB write)", "seed": p.meta.get("seed")}
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline of the dominant kernel class
+# ------------------------------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1909_13585_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(ROOT, "paper_1909_13585_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kclass, workload):
+    """DRAM bytes per launch of the kernel class from a committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kclass}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    hm = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not hm or hm.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def roofline(prof, p, peaks, precision):
+    """Dominant kernel class by device time; algorithmic work per launch from its DOF x RHS."""
+    name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    nd = p.dim * 2 ** p.dim
+    m, n = p.num_elements, p.num_dofs
+    out = {"kernel_class": name, "launches": rec["launches"], "avg_launch_us": 1e3 * rec["ms"] / max(rec["launches"], 1)}
+    rhs_total = rec["dof_rhs"] / n if name.startswith("fine") else None
+    per_launch_s = 1e-3 * rec["ms"] / max(rec["launches"], 1)
+    if name.startswith("fine") and rhs_total is not None:
+        # element products: 2 nd^2 flop per element per RHS (+ 3 flop per DOF of the update)
+        flops = rhs_total * (2.0 * nd * nd * m + 3.0 * n) / rec["launches"]
+        word = 8 if precision == "fp64" else 4
+        bytes_ = rhs_total * (4 * word * n) / rec["launches"] + 8 * m + n
+        peak = FP64_PEAK_GFLOPS if precision == "fp64" else FP32_PEAK_GFLOPS
+        achieved = flops / per_launch_s / 1e9
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (FP32: x128)",
+                    "hbm_gbs_at_same_time": bytes_ / per_launch_s / 1e9,
+                    "hbm_frac_of_measured": (bytes_ / per_launch_s / 1e9) / peaks.get("hbm_gbs", 6792.7),
+                    "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_})
+    else:
+        bytes_ = 8.0 * 4 * rec["dof_rhs"] / max(rec["launches"], 1)
+        achieved = bytes_ / per_launch_s / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6792.7), "unit": "GB/s",
+                    "frac": achieved / peaks.get("hbm_gbs", 6792.7), "peak_source": "of measured",
+                    "algorithmic_bytes_per_launch": bytes_})
+    out["traffic"] = profiled_traffic(name, p.name)
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def ours(args):
+    import torch
+    import paper_1909_13585_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+
+    p = synthetic.config(args.workload)
+    precision = pkg.TOBK_FP64 if args.precision == "fp64" else pkg.TOBK_FP32_VCYCLE
+    stream = torch.cuda.Stream(device=dev)
+    s = pkg.Solver(p, stream=stream, precision=precision)
+    q, m, n = p.num_modes, p.num_elements, p.num_dofs
+    units = n * rhs_per_step(p)
+
+    x_d = torch.from_numpy(p.x).to(dev)
+    dlam_d = torch.zeros((q, m), dtype=torch.float64, device=dev)
+    dJ_d = torch.zeros(m, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        s.set_densities(x_d)
+        s.solve_equilibrium()
+        s.compute_buckling()
+        s.compute_sensitivities(dlam_d, dJ_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if args.profile_run:
+        step()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_run": p.name, "gpu_launches_total": pkg.launch_count()}))
+        s.close()
+        return 0
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = pkg.launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = pkg.launch_count() - launches0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * units * args.steps / (total_ms / 1e3)
+
+    # per-phase times and kernel-class profile over K more steps (profiling on)
+    phases = {}
+    s.profile(True)
+    for _ in range(args.steps):
+        s.set_densities(x_d)
+        _, i1 = s.solve_equilibrium()
+        _, i2 = s.compute_buckling()
+        _, _, i3 = s.compute_sensitivities(dlam_d, dJ_d)
+        for k, inf in (("linear_analysis", i1), ("buckling", i2), ("sensitivities", i3)):
+            phases.setdefault(k, []).append(inf["time_ms"])
+            phases.setdefault(k + "_iters", []).append(inf["iterations"])
+    prof = s.profile_read()
+    s.profile(False)
+    roof = roofline(prof, p, peaks, args.precision)
+
+    # end-to-end through the public API with pinned host buffers (H2D inputs, D2H outputs)
+    e2e = None
+    if not args.no_e2e:
+        x_h = torch.from_numpy(p.x.copy()).pin_memory()
+        f_h = torch.from_numpy(p.f.copy()).pin_memory()
+        fx_h = torch.from_numpy(p.fixed.astype(np.uint8)).pin_memory()
+        dlam_h = torch.zeros((q, m), dtype=torch.float64).pin_memory()
+        dJ_h = torch.zeros(m, dtype=torch.float64).pin_memory()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        lam_sum = 0.0
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[k][0].record(stream)
+            s.set_fixed(fx_h)
+            s.set_load(f_h)
+            s.set_densities(x_h)
+            J, _ = s.solve_equilibrium()
+            lam, _ = s.compute_buckling()
+            s.compute_sensitivities(dlam_h, dJ_h)
+            ev[k][1].record(stream)
+            lam_sum += float(lam[0]) + J
+        torch.cuda.synchronize()
+        e2e_ms = sum(a.elapsed_time(b) for a, b in ev)
+        e2e = {"value": world * units * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * m + 8 * n + n, "d2h_bytes_per_step": 8 * q + 8 * q * m + 8 * m + 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times = run_oracle(args.workload, 1)
+        cpu = {"value": units / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full step of {args.workload} ({times[0]:.1f} s: assembly, SuperLU LA, "
+                         "multilevel LBA with ARPACK, adjoint sensitivities), single-threaded BLAS"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic", "config": config_dict(p, args.precision),
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "wall_s_timed_region": t_wall,
+            "phases_ms": {k: statistics.median(v) for k, v in phases.items()},
+            "kernel_classes": prof,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    s.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,6 +157,29 @@ int tobk_compute_sensitivities(tobk_handle* h, double* dlambda_dx, double* dJ_dx
 /* Copies a field (tobk_field) to out (len doubles). */
 int tobk_get_field(tobk_handle* h, int which, double* out, int64_t len, int out_on_device);
 
+/* Number of CUDA kernels the library has launched in this process (all handles). */
+long long tobk_launch_count(void);
+
+/* Kernel classes timed by the profiler (CUDA events around each launch of the class, on the
+ * handle's stream, while profiling is enabled). */
+typedef enum {
+  TOBK_KC_FINE_SMOOTH = 0,     /* damped-Jacobi sweep on the fine grid (matrix-free K v fused) */
+  TOBK_KC_FINE_RESIDUAL = 1,   /* residual b - K z on the fine grid */
+  TOBK_KC_FINE_CG_MATVEC = 2,  /* CG direction update fused with q = K p on the fine grid */
+  TOBK_KC_COARSE = 3,          /* smoother / residual / CG matvec on Galerkin levels */
+  TOBK_KC_TRANSFER = 4,        /* restriction and prolongation */
+  TOBK_KC_COARSEST = 5,        /* dense coarsest-level solve */
+  TOBK_KC_VECTOR = 6,          /* CG dot products and vector updates, first Jacobi sweep */
+  TOBK_KC_COUNT = 7
+} tobk_kernel_class;
+
+/* Enables (1) or disables (0) kernel-class timing on h; enabling resets the counters. */
+int tobk_profile_enable(tobk_handle* h, int enable);
+/* Launch count, total device milliseconds and total work (DOF x RHS processed) of a kernel class
+ * since profiling was enabled (any output pointer may be NULL). */
+int tobk_profile_read(tobk_handle* h, int kernel_class, long long* launches, double* total_ms,
+                      double* dof_rhs);
+
 /* ---- unit-level entry points (device pointers) ------------------------------------------------ */
 /* Element and DOF counts of a 1-based level: out[0..2] = nel, out[3] = n (DOFs), out[4] = m. */
 int tobk_level_info(tobk_handle* h, int level, int64_t* out5);

@@ -55,7 +55,18 @@ _SIGS = {
     "tobk_apply_G": (C.c_int, [_H, C.c_int, _P, _P, C.c_int]),
     "tobk_solve": (C.c_int, [_H, C.c_int, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
     "tobk_get_element_matrices": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int64]),
+    "tobk_launch_count": (C.c_longlong, []),
+    "tobk_profile_enable": (C.c_int, [_H, C.c_int]),
+    "tobk_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
 }
+
+KERNEL_CLASSES = ("fine_smooth", "fine_residual", "fine_cg_matvec", "coarse", "transfer", "coarsest",
+                  "vector")
+
+
+def launch_count():
+    return int(load().tobk_launch_count())
 
 EXPORTED = tuple(_SIGS)
 
@@ -229,6 +240,17 @@ class Solver:
         self._check(self.lib.tobk_solve(self.h, level, B.data_ptr(), X.data_ptr(), nrhs, C.byref(info)),
                     (TOBK_E_NOT_CONVERGED,) if allow_not_converged else ())
         return info.as_dict()
+
+    def profile(self, enable=True):
+        self._check(self.lib.tobk_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            cnt, ms, units = C.c_longlong(), C.c_double(), C.c_double()
+            self._check(self.lib.tobk_profile_read(self.h, k, C.byref(cnt), C.byref(ms), C.byref(units)))
+            out[name] = dict(launches=int(cnt.value), ms=float(ms.value), dof_rhs=float(units.value))
+        return out
 
     def element_matrices(self, level, which, out):
         self._check(self.lib.tobk_get_element_matrices(self.h, level, which, out.data_ptr(), out.numel()))

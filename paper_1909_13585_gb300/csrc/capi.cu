@@ -143,6 +143,31 @@ int tobk_get_field(tobk_handle* h, int which, double* out, int64_t len, int out_
   return check_cuda(h, "get_field");
 }
 
+long long tobk_launch_count(void) { return g_launch_count.load(); }
+
+int tobk_profile_enable(tobk_handle* h, int enable) {
+  TOBK_GUARD(h);
+  prof_flush(h);
+  h->prof_on = enable != 0;
+  if (h->prof_on)
+    for (int k = 0; k < TOBK_KC_COUNT; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_cnt[k] = 0;
+      h->prof_units[k] = 0.0;
+    }
+  return TOBK_OK;
+}
+
+int tobk_profile_read(tobk_handle* h, int kc, long long* launches, double* total_ms, double* dof_rhs) {
+  TOBK_GUARD(h);
+  if (kc < 0 || kc >= TOBK_KC_COUNT) return fail(h, TOBK_E_ARG, "bad kernel class");
+  prof_flush(h);
+  if (launches) *launches = h->prof_cnt[kc];
+  if (total_ms) *total_ms = h->prof_ms[kc];
+  if (dof_rhs) *dof_rhs = h->prof_units[kc];
+  return check_cuda(h, "profile_read");
+}
+
 int tobk_level_info(tobk_handle* h, int level, int64_t* out5) {
   TOBK_GUARD(h);
   if (!out5 || level < 1 || level > h->L) return fail(h, TOBK_E_ARG, "bad level");

@@ -26,6 +26,12 @@ __host__ __device__ constexpr int local_node(int cx, int cy, int cz) {
   return (cy ? (cx ? 2 : 3) : (cx ? 1 : 0)) + 4 * cz;
 }
 
+// True in blocks whose right-hand side (blockIdx.y) has stopped iterating: multi-RHS kernels of the
+// V-cycle skip converged columns when the CG driver passes its per-RHS scalar state.
+__device__ __forceinline__ bool rhs_done(const double* act) {
+  return act != nullptr && act[(size_t)blockIdx.y * kScStride + SC_ACTIVE] == 0.0;
+}
+
 // ------------------------------------------------------------------------------------------------
 // element operators
 // ------------------------------------------------------------------------------------------------

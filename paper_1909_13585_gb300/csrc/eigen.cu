@@ -316,8 +316,8 @@ __global__ void k_coldots_final(const double* partial, int chunks, int ncols, do
 void launch_coldots(const double* A, const double* B, int ncols, int64_t n, int64_t stride, double* out,
                     double* partial, cudaStream_t s) {
   const int chunks = (int)((n + kColChunk - 1) / kColChunk);
-  k_coldots_partial<<<dim3(chunks, ncols), 256, 0, s>>>(A, B, n, stride, partial);
-  k_coldots_final<<<(ncols + 63) / 64, 64, 0, s>>>(partial, chunks, ncols, out);
+  ::tobk::note_launch(), k_coldots_partial<<<dim3(chunks, ncols), 256, 0, s>>>(A, B, n, stride, partial);
+  ::tobk::note_launch(), k_coldots_final<<<(ncols + 63) / 64, 64, 0, s>>>(partial, chunks, ncols, out);
 }
 
 // R_i = KX_i + (1/theta_i) GX_i written to R (i < q)
@@ -376,7 +376,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
 
-  k_random_block<<<dim3(nblk(n), nb), 256, 0, st>>>(W, n, sd, h->lv[j].fixed, 0x5EEDull + 977ull * j);
+  ::tobk::note_launch(), k_random_block<<<dim3(nblk(n), nb), 256, 0, st>>>(W, n, sd, h->lv[j].fixed, 0x5EEDull + 977ull * j);
   int nadd = nb, m = 0, it = 0, inner_total = 0;
   bool converged = false;
   double worst = INFINITY;
@@ -392,7 +392,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     for (int pass = 0; pass < 2; ++pass) {
       apply_K_level(h, j, W, KW, nadd, sd);
       launch_gram(W, nadd, KW, nadd, n, sd, M, h->gram_partial, st);
-      k_small_cholinv<<<1, 256, 0, st>>>(M, nadd, Rinv, sinfo);
+      ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, nadd, Rinv, sinfo);
       launch_combine(W, nadd, Rinv, nadd, nadd, 1.0, 0.0, Tb, n, sd, st);
       cudaMemcpyAsync(W, Tb, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
     }
@@ -404,17 +404,17 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     cudaMemcpyAsync(h->GV + (size_t)m * n, GW, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
     const int mn = m + nadd;
     launch_gram(h->V, mn, GW, nadd, n, sd, Cs, h->gram_partial, st);
-    k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, -1.0, h->Hs, mmax);
+    ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, -1.0, h->Hs, mmax);
     launch_gram(h->V, mn, KW, nadd, n, sd, Cs, h->gram_partial, st);
-    k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, 1.0, h->Bs, mmax);
+    ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, 1.0, h->Bs, mmax);
     m = mn;
     // ---- Rayleigh-Ritz
-    k_small_rr<<<1, 512, rr_smem, st>>>(h->Hs, h->Bs, m, mmax, theta, h->Ys, mmax, sinfo + 2, 40);
+    ::tobk::note_launch(), k_small_rr<<<1, 512, rr_smem, st>>>(h->Hs, h->Bs, m, mmax, theta, h->Ys, mmax, sinfo + 2, 40);
     const int kk = std::min(nb, m);
     launch_combine(h->V, m, h->Ys, mmax, kk, 1.0, 0.0, X, n, sd, st);
     launch_combine(h->KV, m, h->Ys, mmax, kk, 1.0, 0.0, KX, n, sd, st);
     launch_combine(h->GV, m, h->Ys, mmax, kk, 1.0, 0.0, GX, n, sd, st);
-    k_eig_residual_vec<<<dim3(nblk(n), q), 256, 0, st>>>(KX, GX, theta, Tb, n, sd);
+    ::tobk::note_launch(), k_eig_residual_vec<<<dim3(nblk(n), q), 256, 0, st>>>(KX, GX, theta, Tb, n, sd);
     launch_coldots(Tb, Tb, q, n, sd, resn, h->gram_partial, st);
     launch_coldots(KX, KX, q, n, sd, kxn, h->gram_partial, st);
     cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double) * 512, cudaMemcpyDeviceToHost, st);
@@ -442,7 +442,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     // ---- expansion block W = T X_sel = K^{-1} (-G X_sel)
     nadd = (int)sel.size();
     cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st);
-    k_gather_neg<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, dsel, nadd, Tb, n, sd);
+    ::tobk::note_launch(), k_gather_neg<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, dsel, nadd, Tb, n, sd);
     tobk_solve_info si{};
     int src = pcg_solve(h, j, Tb, W, nadd, 1e-10, h->desc.max_iter, false, TOBK_FP64, &si);
     inner_total += si.iterations;
@@ -456,9 +456,9 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       cudaMemcpyAsync(h->KV, KX, sizeof(double) * kk * n, cudaMemcpyDeviceToDevice, st);
       cudaMemcpyAsync(h->GV, GX, sizeof(double) * kk * n, cudaMemcpyDeviceToDevice, st);
       launch_gram(h->V, kk, h->GV, kk, n, sd, Cs, h->gram_partial, st);
-      k_scatter_sym<<<nblk((int64_t)kk * kk), 256, 0, st>>>(Cs, kk, kk, 0, -1.0, h->Hs, mmax);
+      ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)kk * kk), 256, 0, st>>>(Cs, kk, kk, 0, -1.0, h->Hs, mmax);
       launch_gram(h->V, kk, h->KV, kk, n, sd, Cs, h->gram_partial, st);
-      k_scatter_sym<<<nblk((int64_t)kk * kk), 256, 0, st>>>(Cs, kk, kk, 0, 1.0, h->Bs, mmax);
+      ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)kk * kk), 256, 0, st>>>(Cs, kk, kk, 0, 1.0, h->Bs, mmax);
       m = kk;
     }
   }

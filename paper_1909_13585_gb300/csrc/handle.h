@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,26 @@ struct tobk_handle {
   double* dscal = nullptr;       // device scratch scalars [256]
   double* hscal = nullptr;       // pinned host scratch [256]
 
+  // CUDA graphs of CG iteration pairs, keyed by (level, RHS count, precision)
+  struct CGGraph {
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::map<uint64_t, CGGraph> cg_graphs;
+  bool use_graphs = true;
+
+  // kernel-class timing
+  struct ProfPending {
+    int kc;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<ProfPending> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[TOBK_KC_COUNT] = {0};
+  long long prof_cnt[TOBK_KC_COUNT] = {0};
+  double prof_units[TOBK_KC_COUNT] = {0};  // DOF x RHS processed by the timed launches
+
   double compliance = 0.0;
   double lam_host[64];
   bool have_x = false, have_f = false, have_fixed = false, setup_done = false, have_u = false,
@@ -84,6 +105,9 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
 // G_j v at level j (fine: matrix-free from Gs; coarse: Galerkin Ge)
 void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
 void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
+void prof_begin(tobk_handle* h, int kc, double units);
+void prof_end(tobk_handle* h);
+void prof_flush(tobk_handle* h);
 int fail(tobk_handle* h, int code, const std::string& msg);
 int check_cuda(tobk_handle* h, const char* where);
 

@@ -54,7 +54,8 @@ StoredOp<DIM, T> make_stored(const LevelOpDesc& d, const T* Ke) {
 template <int DIM, class Op, typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_apply(const __grid_constant__ Op op, const T* __restrict__ v, const T* __restrict__ b,
                                                      const T* __restrict__ dinv, T* __restrict__ y, T omega,
-                                                     int64_t stride) {
+                                                     int64_t stride, const double* __restrict__ act) {
+  if (rhs_done(act)) return;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
   if (!node_coords(op.g, node, i, j, k)) return;
@@ -88,11 +89,11 @@ void apply_dispatch(const Op& op, int mode, const T* v, const T* b, const T* din
                     int64_t stride, cudaStream_t s) {
   dim3 grid(blocks_for(op.g.nnode), nr);
   if (mode == APPLY_KV)
-    k_apply<DIM, Op, T, APPLY_KV><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride);
+    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_KV><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride, active_rhs());
   else if (mode == APPLY_RES)
-    k_apply<DIM, Op, T, APPLY_RES><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride);
+    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_RES><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride, active_rhs());
   else
-    k_apply<DIM, Op, T, APPLY_JAC><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride);
+    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_JAC><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride, active_rhs());
 }
 
 template <int DIM>
@@ -153,10 +154,10 @@ void launch_apply_kron(const Grid& g, const uint8_t* fixed, const double* Gs, co
   dim3 grid(blocks_for(g.nnode), nr);
   if (g.dim == 2) {
     ScalarKronOp<2, double> op{g, Gs, fixed};
-    k_apply_kron<2><<<grid, kThreads, 0, s>>>(op, v, y, stride);
+    ::tobk::note_launch(), k_apply_kron<2><<<grid, kThreads, 0, s>>>(op, v, y, stride);
   } else {
     ScalarKronOp<3, double> op{g, Gs, fixed};
-    k_apply_kron<3><<<grid, kThreads, 0, s>>>(op, v, y, stride);
+    ::tobk::note_launch(), k_apply_kron<3><<<grid, kThreads, 0, s>>>(op, v, y, stride);
   }
 }
 
@@ -198,21 +199,22 @@ void launch_diag(const LevelOpDesc& d, double* dinv, float* dinv32, cudaStream_t
   const unsigned grid = blocks_for(d.g.nnode);
   if (d.g.dim == 2) {
     if (d.stored)
-      k_diag<2><<<grid, kThreads, 0, s>>>(make_stored<2, double>(d, d.Ke64), dinv, dinv32);
+      ::tobk::note_launch(), k_diag<2><<<grid, kThreads, 0, s>>>(make_stored<2, double>(d, d.Ke64), dinv, dinv32);
     else
-      k_diag<2><<<grid, kThreads, 0, s>>>(make_fine<2, double>(d, d.scale64), dinv, dinv32);
+      ::tobk::note_launch(), k_diag<2><<<grid, kThreads, 0, s>>>(make_fine<2, double>(d, d.scale64), dinv, dinv32);
   } else {
     if (d.stored)
-      k_diag<3><<<grid, kThreads, 0, s>>>(make_stored<3, double>(d, d.Ke64), dinv, dinv32);
+      ::tobk::note_launch(), k_diag<3><<<grid, kThreads, 0, s>>>(make_stored<3, double>(d, d.Ke64), dinv, dinv32);
     else
-      k_diag<3><<<grid, kThreads, 0, s>>>(make_fine<3, double>(d, d.scale64), dinv, dinv32);
+      ::tobk::note_launch(), k_diag<3><<<grid, kThreads, 0, s>>>(make_fine<3, double>(d, d.scale64), dinv, dinv32);
   }
 }
 
 // ---- first Jacobi sweep from zero --------------------------------------------------------------
 template <typename T>
 __global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ z, T omega,
-                          int64_t n, int64_t stride) {
+                          int64_t n, int64_t stride, const double* __restrict__ act) {
+  if (rhs_done(act)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t off = (int64_t)blockIdx.y * stride;
@@ -221,11 +223,11 @@ __global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T
 
 void launch_jacobi0(const double* b, const double* dinv, double* z, double omega, int64_t n, int nr,
                     int64_t stride, cudaStream_t s) {
-  k_jacobi0<double><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride);
+  ::tobk::note_launch(), k_jacobi0<double><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride, active_rhs());
 }
 void launch_jacobi0_32(const float* b, const float* dinv, float* z, float omega, int64_t n, int nr, int64_t stride,
                        cudaStream_t s) {
-  k_jacobi0<float><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride);
+  ::tobk::note_launch(), k_jacobi0<float><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride, active_rhs());
 }
 
 // ---- transfers ----------------------------------------------------------------------------------
@@ -233,7 +235,8 @@ void launch_jacobi0_32(const float* b, const float* dinv, float* z, float omega,
 // coupled with weight 1 when f = 2C and 1/2 when |f - 2C| = 1.
 template <int DIM, typename T>
 __global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c, const T* __restrict__ rf,
-                           T* __restrict__ bc, int64_t sf, int64_t sc) {
+                           T* __restrict__ bc, int64_t sf, int64_t sc, const double* __restrict__ act) {
+  if (rhs_done(act)) return;
   const int64_t cn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int I, J, K;
   if (!node_coords(gc, cn, I, J, K)) return;
@@ -270,7 +273,8 @@ __global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c
 
 template <int DIM, typename T>
 __global__ void k_prolong_add(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_f, const T* __restrict__ zc,
-                              T* __restrict__ zf, int64_t sf, int64_t sc) {
+                              T* __restrict__ zf, int64_t sf, int64_t sc, const double* __restrict__ act) {
+  if (rhs_done(act)) return;
   const int64_t fn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
   if (!node_coords(gf, fn, i, j, k)) return;
@@ -314,18 +318,18 @@ static void restrict_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_c
                           int64_t sf, int64_t sc, cudaStream_t s) {
   dim3 grid(blocks_for(gc.nnode), nr);
   if (gf.dim == 2)
-    k_restrict<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc);
+    ::tobk::note_launch(), k_restrict<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs());
   else
-    k_restrict<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc);
+    ::tobk::note_launch(), k_restrict<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs());
 }
 template <typename T>
 static void prolong_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const T* zc, T* zf, int nr,
                          int64_t sf, int64_t sc, cudaStream_t s) {
   dim3 grid(blocks_for(gf.nnode), nr);
   if (gf.dim == 2)
-    k_prolong_add<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc);
+    ::tobk::note_launch(), k_prolong_add<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc, active_rhs());
   else
-    k_prolong_add<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc);
+    ::tobk::note_launch(), k_prolong_add<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc, active_rhs());
 }
 
 void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc, int nr,
@@ -348,7 +352,8 @@ void launch_prolong_add32(const Grid& gf, const Grid& gc, const uint8_t* fixed_f
 // ---- coarsest level: dense inverse --------------------------------------------------------------
 template <typename T>
 __global__ void k_dense_gemv(const double* __restrict__ A, const T* __restrict__ b, T* __restrict__ z, int64_t n,
-                             int64_t stride) {
+                             int64_t stride, const double* __restrict__ act) {
+  if (rhs_done(act)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -364,11 +369,11 @@ __global__ void k_dense_gemv(const double* __restrict__ A, const T* __restrict__
 
 void launch_dense_gemv(const double* Ainv, const double* b, double* z, int64_t n, int nr, int64_t stride,
                        cudaStream_t s) {
-  k_dense_gemv<double><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride);
+  ::tobk::note_launch(), k_dense_gemv<double><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride, active_rhs());
 }
 void launch_dense_gemv32(const double* Ainv, const float* b, float* z, int64_t n, int nr, int64_t stride,
                          cudaStream_t s) {
-  k_dense_gemv<float><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride);
+  ::tobk::note_launch(), k_dense_gemv<float><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride, active_rhs());
 }
 
 template <int DIM, class Op>
@@ -425,14 +430,14 @@ void launch_dense_assemble(const LevelOpDesc& d, double* A, cudaStream_t s) {
   const unsigned grid = blocks_for(d.g.nnode, 128);
   if (d.stored) {
     if (d.g.dim == 2)
-      k_dense_assemble<2><<<grid, 128, 0, s>>>(make_stored<2, double>(d, d.Ke64), A);
+      ::tobk::note_launch(), k_dense_assemble<2><<<grid, 128, 0, s>>>(make_stored<2, double>(d, d.Ke64), A);
     else
-      k_dense_assemble<3><<<grid, 128, 0, s>>>(make_stored<3, double>(d, d.Ke64), A);
+      ::tobk::note_launch(), k_dense_assemble<3><<<grid, 128, 0, s>>>(make_stored<3, double>(d, d.Ke64), A);
   } else {
     if (d.g.dim == 2)
-      k_dense_assemble<2><<<grid, 128, 0, s>>>(FineOpGlobal<2>{d.g, d.scale64, d.fixed, d.T0dev}, A);
+      ::tobk::note_launch(), k_dense_assemble<2><<<grid, 128, 0, s>>>(FineOpGlobal<2>{d.g, d.scale64, d.fixed, d.T0dev}, A);
     else
-      k_dense_assemble<3><<<grid, 128, 0, s>>>(FineOpGlobal<3>{d.g, d.scale64, d.fixed, d.T0dev}, A);
+      ::tobk::note_launch(), k_dense_assemble<3><<<grid, 128, 0, s>>>(FineOpGlobal<3>{d.g, d.scale64, d.fixed, d.T0dev}, A);
   }
 }
 
@@ -459,7 +464,7 @@ double* launch_dense_invert(double* A, double* work, int64_t n, cudaStream_t s) 
   double* src = A;
   double* dst = work;
   for (int64_t k = 0; k < n; ++k) {
-    k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k);
+    ::tobk::note_launch(), k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k);
     std::swap(src, dst);
   }
   return src;
@@ -527,9 +532,9 @@ template <int SRC>
 static void galerkin_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* src,
                           const double* T0, const double* W, double* Kc, cudaStream_t s) {
   if (gf.dim == 2)
-    k_galerkin<2, SRC><<<(unsigned)gc.m, 64, 0, s>>>(gf, gc, fixed_f, src, T0, W, Kc);
+    ::tobk::note_launch(), k_galerkin<2, SRC><<<(unsigned)gc.m, 64, 0, s>>>(gf, gc, fixed_f, src, T0, W, Kc);
   else
-    k_galerkin<3, SRC><<<(unsigned)gc.m, 576, 0, s>>>(gf, gc, fixed_f, src, T0, W, Kc);
+    ::tobk::note_launch(), k_galerkin<3, SRC><<<(unsigned)gc.m, 576, 0, s>>>(gf, gc, fixed_f, src, T0, W, Kc);
 }
 
 void launch_galerkin_fine_K(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* scale,
@@ -652,9 +657,9 @@ __global__ void k_stress_gs(Grid g, const double* __restrict__ u, const double* 
 void launch_stress_gs_dev(const Grid& g, const double* u, const double* Es, const double* dN, const double* D,
                           double wdet, double* Gs0, double* Gs, cudaStream_t s) {
   if (g.dim == 2)
-    k_stress_gs<2><<<blocks_for(g.m, 128), 128, 0, s>>>(g, u, Es, dN, D, wdet, Gs0, Gs);
+    ::tobk::note_launch(), k_stress_gs<2><<<blocks_for(g.m, 128), 128, 0, s>>>(g, u, Es, dN, D, wdet, Gs0, Gs);
   else
-    k_stress_gs<3><<<blocks_for(g.m, 128), 128, 0, s>>>(g, u, Es, dN, D, wdet, Gs0, Gs);
+    ::tobk::note_launch(), k_stress_gs<3><<<blocks_for(g.m, 128), 128, 0, s>>>(g, u, Es, dN, D, wdet, Gs0, Gs);
 }
 
 // ================================================================================================
@@ -677,7 +682,7 @@ __global__ void k_simp(const double* __restrict__ x, int64_t m, double penal, do
 
 void launch_simp(const double* x, int64_t m, double penal, double E0, double Emin, double* Ek, double* Es,
                  double* dEk, double* dEs, float* Ek32, cudaStream_t s) {
-  k_simp<<<blocks_for(m), kThreads, 0, s>>>(x, m, penal, E0, Emin, Ek, Es, dEk, dEs, Ek32);
+  ::tobk::note_launch(), k_simp<<<blocks_for(m), kThreads, 0, s>>>(x, m, penal, E0, Emin, Ek, Es, dEk, dEs, Ek32);
 }
 
 __global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
@@ -689,10 +694,10 @@ __global__ void k_f32_to_f64(const float* a, double* b, int64_t n) {
   if (i < n) b[i] = (double)a[i];
 }
 void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
-  k_f64_to_f32<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
+  ::tobk::note_launch(), k_f64_to_f32<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
 }
 void launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
-  k_f32_to_f64<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
+  ::tobk::note_launch(), k_f32_to_f64<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
 }
 
 __global__ void k_mask_copy(const double* __restrict__ src, const uint8_t* __restrict__ fixed, double* __restrict__ dst,
@@ -704,7 +709,7 @@ __global__ void k_mask_copy(const double* __restrict__ src, const uint8_t* __res
 }
 void launch_mask_copy(const double* src, const uint8_t* fixed, double* dst, int64_t n, int nr, int64_t stride,
                       cudaStream_t s) {
-  k_mask_copy<<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(src, fixed, dst, n, stride);
+  ::tobk::note_launch(), k_mask_copy<<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(src, fixed, dst, n, stride);
 }
 
 // ================================================================================================
@@ -914,7 +919,7 @@ template <int DIM, class Op>
 static void cg_init_impl(const Op& op, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
                          int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = cg_partial_stride(op.g.nnode);
-  k_cg_init<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, use_x0 ? 1 : 0, rtol,
+  ::tobk::note_launch(), k_cg_init<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, use_x0 ? 1 : 0, rtol,
                                                                             stride, sc, partial, counters, ps);
 }
 
@@ -937,14 +942,14 @@ void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q
                     int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = 4 * kVecBlocks;
   const unsigned g = (unsigned)std::min<int64_t>(kVecBlocks, (n + kThreads - 1) / kThreads);
-  k_cg_dots<<<dim3(g, nr), kThreads, 0, s>>>(n, z, r, q, p, flexible ? 1 : 0, stride, sc, partial, counters + kMaxRhs, ps);
+  ::tobk::note_launch(), k_cg_dots<<<dim3(g, nr), kThreads, 0, s>>>(n, z, r, q, p, flexible ? 1 : 0, stride, sc, partial, counters + kMaxRhs, ps);
 }
 
 template <int DIM, class Op>
 static void cg_dir_impl(const Op& op, const double* z, const double* p_old, double* p_new, double* q, int nr,
                         int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = cg_partial_stride(op.g.nnode);
-  k_cg_direction<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, z, p_old, p_new, q, stride, sc,
+  ::tobk::note_launch(), k_cg_direction<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, z, p_old, p_new, q, stride, sc,
                                                                                  partial, counters + 2 * kMaxRhs, ps);
 }
 
@@ -967,14 +972,14 @@ void launch_cg_update(int64_t n, double* x, double* r, const double* p, const do
                       double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = 4 * kVecBlocks;
   const unsigned g = (unsigned)std::min<int64_t>(kVecBlocks, (n + kThreads - 1) / kThreads);
-  k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial, counters + 3 * kMaxRhs, ps);
+  ::tobk::note_launch(), k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial, counters + 3 * kMaxRhs, ps);
 }
 
 template <int DIM, class Op>
 static void true_res_impl(const Op& op, const double* b, const double* x, double* r, int nr, int64_t stride,
                           double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = cg_partial_stride(op.g.nnode);
-  k_true_residual<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, stride, sc, partial,
+  ::tobk::note_launch(), k_true_residual<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, stride, sc, partial,
                                                                                   counters + 4 * kMaxRhs, ps);
 }
 
@@ -1043,8 +1048,8 @@ void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, in
     cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     configured = true;
   }
-  k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, partial);
-  k_gram_final<<<blocks_for((int64_t)na * nb), kThreads, 0, s>>>(partial, chunks, na * nb, C);
+  ::tobk::note_launch(), k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, partial);
+  ::tobk::note_launch(), k_gram_final<<<blocks_for((int64_t)na * nb), kThreads, 0, s>>>(partial, chunks, na * nb, C);
 }
 
 // Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j]; one thread per row index, up to 32 outputs per
@@ -1077,7 +1082,7 @@ __global__ void k_combine(const double* __restrict__ X, int nx, const double* __
 void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta, double* Y,
                     int64_t n, int64_t stride, cudaStream_t s) {
   dim3 grid(blocks_for(n), (ny + 31) / 32);
-  k_combine<<<grid, kThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n, stride);
+  ::tobk::note_launch(), k_combine<<<grid, kThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n, stride);
 }
 
 }  // namespace tobk

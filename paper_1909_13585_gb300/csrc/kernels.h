@@ -10,6 +10,11 @@
 
 namespace tobk {
 
+// Per-RHS scalar state ([nr][kScStride]) of the CG driver running on this host thread, or null.
+// While set, the V-cycle kernels skip right-hand sides that have converged.
+const double* active_rhs();
+void set_active_rhs(const double* sc);
+
 // Which element operator a level uses.
 struct LevelOpDesc {
   Grid g;

@@ -120,11 +120,11 @@ static void finalize_modes(tobk_handle* h, const double* A, const double* lam_de
   const int chunks = 64;
   double* pv = h->gram_partial;
   long long* pi = (long long*)(h->gram_partial + (size_t)q * chunks);
-  k_argmax_partial<<<dim3(chunks, q), 256, 0, st>>>(A, n, n, pv, pi);
+  ::tobk::note_launch(), k_argmax_partial<<<dim3(chunks, q), 256, 0, st>>>(A, n, n, pv, pi);
   int* perm = (int*)(h->dscal + 640);
   double* scale = h->dscal + 704;
-  k_order_modes<<<1, 32, 0, st>>>(A, n, pv, pi, chunks, lam_dev, num_dev, q, perm, scale, lam_out_dev);
-  k_permute_scale<<<dim3(nblk(n), q), 256, 0, st>>>(A, perm, scale, out, n, n);
+  ::tobk::note_launch(), k_order_modes<<<1, 32, 0, st>>>(A, n, pv, pi, chunks, lam_dev, num_dev, q, perm, scale, lam_out_dev);
+  ::tobk::note_launch(), k_permute_scale<<<dim3(nblk(n), q), 256, 0, st>>>(A, perm, scale, out, n, n);
 }
 
 int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
@@ -179,7 +179,7 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     apply_G_level(h, 0, Phi, GP, q, n);
     launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
     launch_coldots(Phi, GP, q, n, n, den, h->gram_partial, st);
-    k_rq<<<1, 64, 0, st>>>(num, den, q, lraw);
+    ::tobk::note_launch(), k_rq<<<1, 64, 0, st>>>(num, den, q, lraw);
     finalize_modes(h, Phi, lraw, num, h->modes, h->lam);
     ei.iterations += si.iterations;
   }
@@ -401,11 +401,11 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
     const double* phi = h->modes + (size_t)i * n;
     double* b = h->adj_rhs + (size_t)i * n;
     if (g.dim == 2) {
-      k_adjoint_gp<2><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
-      k_adjoint_gather<2><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
+      ::tobk::note_launch(), k_adjoint_gp<2><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
+      ::tobk::note_launch(), k_adjoint_gather<2><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
     } else {
-      k_adjoint_gp<3><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
-      k_adjoint_gather<3><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
+      ::tobk::note_launch(), k_adjoint_gp<3><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
+      ::tobk::note_launch(), k_adjoint_gather<3><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
     }
   }
   // adjoint systems K z_i = b_i: one multi-RHS mgPCG solve
@@ -418,10 +418,10 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
   double* pGp = h->dscal + 960;
   launch_coldots(h->modes, GP, q, n, n, pGp, h->gram_partial, st);
   if (g.dim == 2)
-    k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk,
+    ::tobk::note_launch(), k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk,
                                                        h->dEs, h->lam, pGp, h->dlam, h->dJ);
   else
-    k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk, h->dEs,
+    ::tobk::note_launch(), k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk, h->dEs,
                                                      h->lam, pGp, h->dlam, h->dJ);
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (dlam_out) cudaMemcpyAsync(dlam_out, h->dlam, sizeof(double) * q * g.m, kind, st);

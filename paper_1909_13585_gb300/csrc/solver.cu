@@ -12,6 +12,19 @@
 
 namespace tobk {
 
+std::atomic<long long> g_launch_count{0};
+
+static thread_local const double* t_active_rhs = nullptr;
+const double* active_rhs() { return t_active_rhs; }
+void set_active_rhs(const double* sc) { t_active_rhs = sc; }
+
+namespace {
+struct ActiveRhsScope {
+  explicit ActiveRhsScope(const double* sc) { set_active_rhs(sc); }
+  ~ActiveRhsScope() { set_active_rhs(nullptr); }
+};
+}  // namespace
+
 // ================================================================================================
 // element tables (Gauss-Legendre 2-point rule per axis; exact for Q4/H8 on unit elements)
 // ================================================================================================
@@ -294,6 +307,12 @@ void destroy_handle(tobk_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  for (auto& p : h->prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
+  for (auto& kv : h->cg_graphs) cudaGraphExecDestroy(kv.second.exec);
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->cg.host_sc) cudaFreeHost(h->cg.host_sc);
   if (h->hscal) cudaFreeHost(h->hscal);
@@ -353,10 +372,10 @@ int set_fixed(tobk_handle* h, const uint8_t* fixed, bool on_device) {
   const int64_t n = h->lv[0].g.n;
   int rc = copy_in(h, h->lv[0].fixed, fixed, n, on_device);
   if (rc) return rc;
-  k_normalize_fixed<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->lv[0].fixed, n);
+  ::tobk::note_launch(), k_normalize_fixed<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->lv[0].fixed, n);
   for (int j = 1; j < h->L; ++j) {
     const Grid& gc = h->lv[j].g;
-    k_coarsen_fixed<<<(unsigned)((gc.nnode + 255) / 256), 256, 0, h->stream>>>(h->lv[j - 1].g, gc, h->lv[j - 1].fixed,
+    ::tobk::note_launch(), k_coarsen_fixed<<<(unsigned)((gc.nnode + 255) / 256), 256, 0, h->stream>>>(h->lv[j - 1].g, gc, h->lv[j - 1].fixed,
                                                                                 h->lv[j].fixed);
   }
   h->have_fixed = true;
@@ -417,28 +436,84 @@ int setup_hierarchy(tobk_handle* h) {
 // ================================================================================================
 // V-cycle (multigrid preconditioner)
 // ================================================================================================
+// ================================================================================================
+// kernel-class timing (CUDA events around selected launches while profiling is enabled)
+// ================================================================================================
+void prof_begin(tobk_handle* h, int kc, double units) {
+  if (!h->prof_on) return;
+  h->prof_units[kc] += units;
+  cudaEvent_t a, b;
+  if (h->prof_pool.size() >= 2) {
+    a = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    b = h->prof_pool.back();
+    h->prof_pool.pop_back();
+  } else {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  cudaEventRecord(a, h->stream);
+  h->prof_pending.push_back({kc, a, b});
+}
+
+void prof_end(tobk_handle* h) {
+  if (!h->prof_on || h->prof_pending.empty()) return;
+  cudaEventRecord(h->prof_pending.back().b, h->stream);
+  if (h->prof_pending.size() > 4096) prof_flush(h);
+}
+
+void prof_flush(tobk_handle* h) {
+  if (h->prof_pending.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& p : h->prof_pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    h->prof_ms[p.kc] += ms;
+    h->prof_cnt[p.kc] += 1;
+    h->prof_pool.push_back(p.a);
+    h->prof_pool.push_back(p.b);
+  }
+  h->prof_pending.clear();
+}
+
 static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* z, double* t) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[j];
   const int64_t n = L.g.n;
   const double om = h->desc.omega;
+  const int ks = j == 0 ? TOBK_KC_FINE_SMOOTH : TOBK_KC_COARSE;
+  const int kr = j == 0 ? TOBK_KC_FINE_RESIDUAL : TOBK_KC_COARSE;
   if (j == h->L - 1) {
+    prof_begin(h, TOBK_KC_COARSEST, (double)nr * n);
     launch_dense_gemv(h->Ainv, b, z, n, nr, n, s);
+    prof_end(h);
     return z;
   }
   const LevelOpDesc op = level_op(h, j);
+  prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
   launch_jacobi0(b, L.dinv, z, om, n, nr, n, s);
+  prof_end(h);
   for (int it = 1; it < h->desc.nu_pre; ++it) {
+    prof_begin(h, ks, (double)nr * n);
     launch_apply(op, APPLY_JAC, z, b, L.dinv, t, om, nr, n, s);
+    prof_end(h);
     std::swap(z, t);
   }
+  prof_begin(h, kr, (double)nr * n);
   launch_apply(op, APPLY_RES, z, b, nullptr, L.r, 0.0, nr, n, s);
+  prof_end(h);
   Level& C = h->lv[j + 1];
+  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
   launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s);
+  prof_end(h);
   double* zc = vcycle64(h, j + 1, nr, C.b, C.z, C.t);
+  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
   launch_prolong_add(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
+  prof_end(h);
   for (int it = 0; it < h->desc.nu_post; ++it) {
+    prof_begin(h, ks, (double)nr * n);
     launch_apply(op, APPLY_JAC, z, b, L.dinv, t, om, nr, n, s);
+    prof_end(h);
     std::swap(z, t);
   }
   return z;
@@ -449,23 +524,39 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
   Level& L = h->lv[j];
   const int64_t n = L.g.n;
   const float om = (float)h->desc.omega;
+  const int ks = j == 0 ? TOBK_KC_FINE_SMOOTH : TOBK_KC_COARSE;
+  const int kr = j == 0 ? TOBK_KC_FINE_RESIDUAL : TOBK_KC_COARSE;
   if (j == h->L - 1) {
+    prof_begin(h, TOBK_KC_COARSEST, (double)nr * n);
     launch_dense_gemv32(h->Ainv, b, z, n, nr, n, s);
+    prof_end(h);
     return z;
   }
   const LevelOpDesc op = level_op(h, j);
+  prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
   launch_jacobi0_32(b, L.dinv32, z, om, n, nr, n, s);
+  prof_end(h);
   for (int it = 1; it < h->desc.nu_pre; ++it) {
+    prof_begin(h, ks, (double)nr * n);
     launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, om, nr, n, s);
+    prof_end(h);
     std::swap(z, t);
   }
+  prof_begin(h, kr, (double)nr * n);
   launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, 0.0f, nr, n, s);
+  prof_end(h);
   Level& C = h->lv[j + 1];
+  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
   launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s);
+  prof_end(h);
   float* zc = vcycle32(h, j + 1, nr, C.b32, C.z32, C.t32);
+  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
   launch_prolong_add32(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
+  prof_end(h);
   for (int it = 0; it < h->desc.nu_post; ++it) {
+    prof_begin(h, ks, (double)nr * n);
     launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, om, nr, n, s);
+    prof_end(h);
     std::swap(z, t);
   }
   return z;
@@ -485,6 +576,62 @@ static double* precondition(tobk_handle* h, int s, int nr, const double* r, doub
 // ================================================================================================
 // multi-RHS preconditioned CG
 // ================================================================================================
+// Two CG iterations (the two direction buffers swap roles twice, so the launch sequence and every
+// pointer in it are the same each time): V-cycle, dot products + beta, direction + q = K p + alpha,
+// x/r update + convergence test.  The iterate lives in the handle's buffer w.x.
+static void enqueue_cg_pair(tobk_handle* h, int s, int nr, int precision) {
+  cudaStream_t st = h->stream;
+  const LevelOpDesc op = level_op(h, s);
+  const int64_t n = op.g.n;
+  CGWork& w = h->cg;
+  const bool flexible = precision != TOBK_FP64;
+  for (int k = 0; k < 2; ++k) {
+    double* p_old = k == 0 ? w.p0 : w.p1;
+    double* p_new = k == 0 ? w.p1 : w.p0;
+    double* z = precondition(h, s, nr, w.r, w.z, w.zt, precision);
+    prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
+    launch_cg_dots(n, z, w.r, w.q, p_old, flexible, nr, n, w.sc, w.partial, w.counters, st);
+    prof_end(h);
+    prof_begin(h, s == 0 ? TOBK_KC_FINE_CG_MATVEC : TOBK_KC_COARSE, (double)nr * n);
+    launch_cg_direction(op, z, p_old, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
+    prof_end(h);
+    prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
+    launch_cg_update(n, w.x, w.r, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
+    prof_end(h);
+  }
+}
+
+// Runs one iteration pair: replayed from a CUDA graph captured on first use for this (level, RHS
+// count, precision), or launched directly while profiling or on the legacy default stream.
+static int run_cg_pair(tobk_handle* h, int s, int nr, int precision) {
+  if (h->prof_on || h->stream == nullptr || !h->use_graphs) {
+    enqueue_cg_pair(h, s, nr, precision);
+    return TOBK_OK;
+  }
+  const uint64_t key = (uint64_t)s | ((uint64_t)nr << 8) | ((uint64_t)precision << 16);
+  auto it = h->cg_graphs.find(key);
+  if (it == h->cg_graphs.end()) {
+    cudaGraph_t g = nullptr;
+    const long long c0 = g_launch_count.load();
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return check_cuda(h, "graph capture");
+    enqueue_cg_pair(h, s, nr, precision);
+    if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess) return check_cuda(h, "graph capture");
+    const long long kernels = g_launch_count.load() - c0;
+    g_launch_count.fetch_sub(kernels);
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return check_cuda(h, "graph instantiate");
+    }
+    cudaGraphDestroy(g);
+    it = h->cg_graphs.emplace(key, tobk_handle::CGGraph{ex, kernels}).first;
+  }
+  cudaGraphLaunch(it->second.exec, h->stream);
+  g_launch_count.fetch_add(it->second.kernels);
+  return TOBK_OK;
+}
+
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
               int precision, tobk_solve_info* info) {
   if (nr < 1 || nr > h->rmax) return fail(h, TOBK_E_ARG, "bad RHS count");
@@ -496,47 +643,39 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
   const LevelOpDesc op = level_op(h, s);
   const int64_t n = op.g.n;
   CGWork& w = h->cg;
-  double* p_old = w.p0;
-  double* p_new = w.p1;
-  cudaMemsetAsync(p_old, 0, sizeof(double) * nr * n, st);
-  cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  const bool flexible = precision != TOBK_FP64;
-  int total_it = 0;
+  ActiveRhsScope active_scope(w.sc);
+  if (use_x0) cudaMemcpyAsync(w.x, X, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, st);
+  int pairs = 0;
   int rc = TOBK_OK;
   double worst = 0.0;
+  int iters = 0;
   bool all_conv = true;
   for (int attempt = 0; attempt < 4; ++attempt) {
-    launch_cg_init(op, B, X, w.r, use_x0 || attempt > 0, rtol, nr, n, w.sc, w.partial, w.counters, st);
-    if (attempt > 0) {
-      cudaMemsetAsync(p_old, 0, sizeof(double) * nr * n, st);
-      cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+    launch_cg_init(op, B, w.x, w.r, use_x0 || attempt > 0, rtol, nr, n, w.sc, w.partial, w.counters, st);
+    cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
+    cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+    while (2 * pairs < max_iter) {
+      rc = run_cg_pair(h, s, nr, precision);
+      if (rc) break;
+      ++pairs;
+      cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      bool any = false;
+      for (int r = 0; r < nr; ++r) any |= w.host_sc[r * kScStride + SC_ACTIVE] != 0.0;
+      if (!any) break;
     }
-    const int check_every = 2;
-    for (int it = 0; it < max_iter; ++it) {
-      double* z = precondition(h, s, nr, w.r, w.z, w.zt, precision);
-      launch_cg_dots(n, z, w.r, w.q, p_old, flexible, nr, n, w.sc, w.partial, w.counters, st);
-      launch_cg_direction(op, z, p_old, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
-      launch_cg_update(n, X, w.r, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
-      std::swap(p_old, p_new);
-      ++total_it;
-      if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
-        cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
-        bool any = false;
-        for (int r = 0; r < nr; ++r) any |= w.host_sc[r * kScStride + SC_ACTIVE] != 0.0;
-        if (!any) break;
-      }
-    }
-    cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
+    if (rc) break;
     int status = 0;
-    for (int r = 0; r < nr; ++r) status = std::max(status, (int)w.host_sc[r * kScStride + SC_STATUS]);
+    for (int r = 0; r < nr; ++r) {
+      status = std::max(status, (int)w.host_sc[r * kScStride + SC_STATUS]);
+      iters = std::max(iters, (int)w.host_sc[r * kScStride + SC_ITERS]);
+    }
     // true residual recomputed at exit
-    launch_true_residual(op, B, X, w.zt, nr, n, w.sc, w.partial, w.counters, st);
+    launch_true_residual(op, B, w.x, w.zt, nr, n, w.sc, w.partial, w.counters, st);
     cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     rc = check_cuda(h, "pcg_solve");
@@ -556,9 +695,10 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
       rc = fail(h, TOBK_E_NONFINITE, "non-finite value in CG");
       break;
     }
-    if (all_conv || total_it >= max_iter) break;
-    // the recursive residual met the target but the true one did not: restart from X
+    if (all_conv || 2 * pairs >= max_iter) break;
+    // the recursive residual met the target but the true one did not: restart from the iterate
   }
+  cudaMemcpyAsync(X, w.x, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, st);
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -566,12 +706,12 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (info) {
-    info->iterations = total_it;
+    info->iterations = iters;
     info->converged = all_conv ? 1 : 0;
     info->num_rhs = nr;
     info->rel_residual = worst;
     info->time_ms = ms;
-    info->status_detail = 0;
+    info->status_detail = 2 * pairs;
   }
   if (rc == TOBK_OK && !all_conv) rc = fail(h, TOBK_E_NOT_CONVERGED, "CG iteration limit reached");
   return rc;

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -116,6 +117,12 @@ struct CGWork {
   double* host_sc;     // pinned host copy of sc
 };
 
+}  // namespace tobk
+
+namespace tobk {
+// Number of kernels this library has launched (all handles); read through tobk_launch_count().
+extern std::atomic<long long> g_launch_count;
+inline void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace tobk
 
 // The opaque handle of the C-ABI.
