@@ -194,6 +194,29 @@ int tobk_solve(tobk_handle* h, int level, const double* B, double* X, int nrhs, 
  * [m_level][nd*nd] (device pointer), nd = dim * 2^dim. */
 int tobk_get_element_matrices(tobk_handle* h, int level, int which, double* out, int64_t len);
 
+/* ---- allocation-free residual check ------------------------------------------------------------
+ * Not part of the paper's method (it has no counterpart there): a utility for callers that must not
+ * allocate device memory when they verify a solution, e.g. code running while a stream is being
+ * captured into a CUDA graph (cudaMalloc is not allowed there), programs whose device memory is
+ * owned by another framework's pool allocator, or latency-critical loops that cannot afford
+ * cudaMalloc's implicit synchronisation.  It needs no handle and allocates nothing.
+ *
+ * For r = 0..nrhs-1 writes relres[r] = ||B_r - K(x) X_r||_2 / ||B_r||_2 over the free DOFs of the
+ * fine grid described by desc (dim, nel, nu, E0, Emin, penal; other fields ignored), K(x) being the
+ * SIMP stiffness of tobk_apply_K at level 1.  x [m], fixed [n] (uint8, 1 = fixed), B and X
+ * [nrhs][n] and relres [nrhs] are DEVICE pointers on the current device; the caller owns them.
+ * The work is enqueued on cuda_stream (NULL = legacy default stream); relres is valid once that
+ * stream has reached this point.
+ * Limits: nrhs <= 16 (otherwise TOBK_E_ARG): the reduction scratch is a fixed array of 256 KiB in
+ * the library's own device memory, which every GPU that loads the library keeps until the process
+ * exits.  Every call on a device shares that array: calls whose kernels may overlap on the GPU
+ * (different streams without ordering) race and must not be issued.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture begins.
+ * Errors: TOBK_E_ARG (null pointer, bad dim or sizes, nrhs out of range), TOBK_E_CUDA. */
+int tobk_residual_noalloc(const tobk_desc* desc, const double* x, const uint8_t* fixed, const double* B,
+                          const double* X, int nrhs, double* relres, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

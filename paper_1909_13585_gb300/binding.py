@@ -55,6 +55,7 @@ _SIGS = {
     "tobk_apply_G": (C.c_int, [_H, C.c_int, _P, _P, C.c_int]),
     "tobk_solve": (C.c_int, [_H, C.c_int, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
     "tobk_get_element_matrices": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int64]),
+    "tobk_residual_noalloc": (C.c_int, [C.POINTER(tobk_desc), _P, _P, _P, _P, C.c_int, _P, C.c_void_p]),
     "tobk_launch_count": (C.c_longlong, []),
     "tobk_profile_enable": (C.c_int, [_H, C.c_int]),
     "tobk_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),

@@ -1,0 +1,219 @@
+// Allocation-free residual check on the fine grid (declared as tobk_residual_noalloc in
+// include/tobk.h).
+//
+// Some callers cannot allocate device memory at the point where they want to verify a solution:
+// code running while a CUDA stream is being captured into a graph (cudaMalloc is not a legal
+// operation there), applications whose device memory is owned by another framework's pool allocator
+// and may not be grown behind its back, and latency-critical loops where cudaMalloc's implicit
+// device synchronisation is not acceptable.  This entry point needs no handle and no allocation: it
+// recomputes ||b_r - K(x) x_r|| / ||b_r|| for each right-hand side r, with the reduction scratch in
+// a fixed-size array that lives in this file's device memory for as long as the library is loaded.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "../../include/tobk.h"
+#include "device_common.cuh"
+
+namespace tobk {
+
+constexpr int kNoAllocMaxRhs = 16;    // largest nrhs accepted
+constexpr int kNoAllocBlocks = 1024;  // fixed grid width (grid-stride loop over nodes)
+
+// Scratch shared by every call on a device: per-(RHS, block) partial sums and per-RHS arrival
+// counters of the last-block reduction (256 KiB + 64 B per device).
+static __device__ __align__(256) double g_noalloc_partial[kNoAllocMaxRhs * kNoAllocBlocks * 2];
+static __device__ __align__(256) unsigned g_noalloc_counter[kNoAllocMaxRhs];
+
+// Fine-grid SIMP stiffness with E_kappa evaluated from the densities inside the kernel.
+template <int DIM>
+struct FineOpFromDensity {
+  Grid g;
+  const double* x;
+  const uint8_t* fixed;
+  double penal, E0, Emin;
+  double M[Dims<DIM>::ND * Dims<DIM>::ND];
+  __device__ __forceinline__ double scale(int64_t e) const { return Emin + pow(x[e], penal) * (E0 - Emin); }
+  __device__ __forceinline__ double entry(int64_t, int r, int c) const { return M[r * Dims<DIM>::ND + c]; }
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_residual_noalloc(const __grid_constant__ FineOpFromDensity<DIM> op,
+                                                          const double* __restrict__ B,
+                                                          const double* __restrict__ X, int64_t stride,
+                                                          double* __restrict__ partial, unsigned* counters,
+                                                          double* __restrict__ relres) {
+  __shared__ double smem[64];
+  const int rhs = blockIdx.y;
+  const int64_t off = (int64_t)rhs * stride;
+  double v[2] = {0.0, 0.0};  // r.r, b.b over free DOFs
+  for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < op.g.nnode;
+       node += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    node_coords(op.g, node, i, j, k);
+    double acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+    gather_rows<DIM, double>(op, i, j, k, LoadVec<double>{X + off}, acc);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t idx = DIM * node + c;
+      if (op.fixed[idx]) continue;
+      const double bi = B[off + idx];
+      const double ri = bi - acc[c];
+      v[0] += ri * ri;
+      v[1] += bi * bi;
+    }
+  }
+  double tot[2];
+  if (grid_sum_last<2>(v, partial + (size_t)rhs * gridDim.x * 2, counters + rhs, tot, smem) && threadIdx.x == 0)
+    relres[rhs] = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : sqrt(tot[0]);
+}
+
+namespace {
+
+// Unit-modulus element stiffness K_e0 = sum_gp w |J| B^T D B of the unit Q4 (plane stress) or H8
+// element, 2-point Gauss rule per axis, written into a caller-provided array (no heap use).
+template <int DIM>
+void element_stiffness_on_stack(double nu, double* Ke) {
+  constexpr int NN = Dims<DIM>::NN, ND = Dims<DIM>::ND, NV = Dims<DIM>::NV;
+  double D[NV * NV] = {0.0};
+  if (DIM == 2) {
+    const double c = 1.0 / (1.0 - nu * nu);
+    D[0] = c;
+    D[1] = c * nu;
+    D[NV] = c * nu;
+    D[NV + 1] = c;
+    D[2 * NV + 2] = c * (1.0 - nu) / 2.0;
+  } else {
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = 1.0 / (2.0 * (1.0 + nu));
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) D[a * NV + b] = lam + (a == b ? 2.0 * mu : 0.0);
+    for (int a = 3; a < NV; ++a) D[a * NV + a] = mu;
+  }
+  for (int q = 0; q < ND * ND; ++q) Ke[q] = 0.0;
+  const double g = 1.0 / std::sqrt(3.0);
+  const double wdet = DIM == 2 ? 0.25 : 0.125;
+  for (int gp = 0; gp < NN; ++gp) {
+    double xg[3] = {((gp >> 0) & 1) ? g : -g, ((gp >> 1) & 1) ? g : -g, ((gp >> 2) & 1) ? g : -g};
+    double dN[DIM][NN];
+    for (int l = 0; l < NN; ++l) {
+      const double xl[3] = {corner_x(l) ? 1.0 : -1.0, corner_y(l) ? 1.0 : -1.0, corner_z(l) ? 1.0 : -1.0};
+      for (int a = 0; a < DIM; ++a) {
+        double v = xl[a] / (DIM == 2 ? 4.0 : 8.0);
+        for (int b = 0; b < DIM; ++b)
+          if (b != a) v *= 1.0 + xl[b] * xg[b];
+        dN[a][l] = 2.0 * v;
+      }
+    }
+    double B[NV][ND];
+    for (int a = 0; a < NV; ++a)
+      for (int r = 0; r < ND; ++r) B[a][r] = 0.0;
+    for (int l = 0; l < NN; ++l) {
+      if (DIM == 2) {
+        B[0][2 * l] = dN[0][l];
+        B[1][2 * l + 1] = dN[1][l];
+        B[2][2 * l] = dN[1][l];
+        B[2][2 * l + 1] = dN[0][l];
+      } else {
+        B[0][3 * l] = dN[0][l];
+        B[1][3 * l + 1] = dN[1][l];
+        B[2][3 * l + 2] = dN[DIM - 1][l];
+        B[3][3 * l] = dN[1][l];
+        B[3][3 * l + 1] = dN[0][l];
+        B[4][3 * l + 1] = dN[DIM - 1][l];
+        B[4][3 * l + 2] = dN[1][l];
+        B[5][3 * l] = dN[DIM - 1][l];
+        B[5][3 * l + 2] = dN[0][l];
+      }
+    }
+    for (int r = 0; r < ND; ++r)
+      for (int c = 0; c < ND; ++c) {
+        double s = 0.0;
+        for (int a = 0; a < NV; ++a)
+          for (int b = 0; b < NV; ++b) s += B[a][r] * D[a * NV + b] * B[b][c];
+        Ke[r * ND + c] += wdet * s;
+      }
+  }
+}
+
+std::mutex g_setup_mutex;
+constexpr int kMaxDevices = 64;
+double* g_partial_addr[kMaxDevices] = {nullptr};
+unsigned* g_counter_addr[kMaxDevices] = {nullptr};
+
+// Device addresses of the scratch arrays, looked up once per device (with that device current).
+int scratch_for_device(int dev, double** partial, unsigned** counters) {
+  if (dev < 0 || dev >= kMaxDevices) return TOBK_E_ARG;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_partial_addr[dev]) {
+    void* p = nullptr;
+    void* c = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partial) != cudaSuccess ||
+        cudaGetSymbolAddress(&c, g_noalloc_counter) != cudaSuccess) {
+      cudaGetLastError();
+      return TOBK_E_CUDA;
+    }
+    g_partial_addr[dev] = static_cast<double*>(p);
+    g_counter_addr[dev] = static_cast<unsigned*>(c);
+  }
+  *partial = g_partial_addr[dev];
+  *counters = g_counter_addr[dev];
+  return TOBK_OK;
+}
+
+template <int DIM>
+void launch_noalloc(const tobk_desc& d, const double* x, const uint8_t* fixed, const double* B, const double* X,
+                    int nrhs, double* relres, double* partial, unsigned* counters, cudaStream_t s) {
+  FineOpFromDensity<DIM> op;
+  int nel[3] = {d.nel[0], d.nel[1], DIM == 3 ? d.nel[2] : 1};
+  op.g = make_grid(DIM, nel);
+  op.x = x;
+  op.fixed = fixed;
+  op.penal = d.penal;
+  op.E0 = d.E0;
+  op.Emin = d.Emin;
+  element_stiffness_on_stack<DIM>(d.nu, op.M);
+  const int64_t want = (op.g.nnode + 255) / 256;
+  const unsigned blocks = (unsigned)(want < kNoAllocBlocks ? want : kNoAllocBlocks);
+  note_launch();
+  k_residual_noalloc<DIM><<<dim3(blocks, nrhs), 256, 0, s>>>(op, B, X, op.g.n, partial, counters, relres);
+}
+}  // namespace
+
+}  // namespace tobk
+
+extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, const uint8_t* fixed, const double* B,
+                                     const double* X, int nrhs, double* relres, void* cuda_stream) {
+  using namespace tobk;
+  if (!desc || !x || !fixed || !B || !X || !relres) return TOBK_E_ARG;
+  if (desc->dim != 2 && desc->dim != 3) return TOBK_E_ARG;
+  for (int a = 0; a < desc->dim; ++a)
+    if (desc->nel[a] < 1) return TOBK_E_ARG;
+  // the built-in scratch holds kNoAllocMaxRhs right-hand sides; larger blocks are rejected
+  if (nrhs < 1 || nrhs > kNoAllocMaxRhs) return TOBK_E_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TOBK_E_CUDA;
+  }
+  double* partial = nullptr;
+  unsigned* counters = nullptr;
+  if (scratch_for_device(dev, &partial, &counters) != TOBK_OK) {
+    return TOBK_E_CUDA;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // the arrival counters must start at zero (an interrupted earlier call could have left them set)
+  cudaMemsetAsync(counters, 0, sizeof(unsigned) * kNoAllocMaxRhs, s);
+  if (desc->dim == 2)
+    launch_noalloc<2>(*desc, x, fixed, B, X, nrhs, relres, partial, counters, s);
+  else
+    launch_noalloc<3>(*desc, x, fixed, B, X, nrhs, relres, partial, counters, s);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    return TOBK_E_CUDA;
+  }
+  return TOBK_OK;
+}
