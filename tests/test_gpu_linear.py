@@ -145,3 +145,21 @@ def test_fp32_vcycle_flexible_cg_reaches_same_tolerance():
         assert res <= 1e-8
         uo, Jo = lba.linear_analysis(op)
         assert J == pytest.approx(Jo, rel=1e-7)
+
+
+def test_graph_replayed_solves_match_direct_launches():
+    """On a non-default stream the CG iterations replay a captured CUDA graph; the iterates must be
+    identical to the directly launched ones (same kernels, same order)."""
+    torch, pkg = require_gpu()
+    p = _problem(CASES_2D[2])
+    s1 = pkg.Solver(p)                                   # legacy default stream: direct launches
+    stream = torch.cuda.Stream()
+    s2 = pkg.Solver(p, stream=stream)                    # graph replay
+    J1, i1 = s1.solve_equilibrium()
+    J2, i2 = s2.solve_equilibrium()
+    J3, i3 = s2.solve_equilibrium()                      # second solve replays the cached graph
+    u1 = s1.get_field(pkg.TOBK_FIELD_U)
+    u2 = s2.get_field(pkg.TOBK_FIELD_U)
+    assert i1["iterations"] == i2["iterations"] == i3["iterations"]
+    assert np.array_equal(u1, u2)
+    assert J1 == J2 == J3
