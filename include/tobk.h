@@ -170,7 +170,9 @@ typedef enum {
   TOBK_KC_TRANSFER = 4,        /* restriction and prolongation */
   TOBK_KC_COARSEST = 5,        /* dense coarsest-level solve */
   TOBK_KC_VECTOR = 6,          /* CG dot products and vector updates, first Jacobi sweep */
-  TOBK_KC_COUNT = 7
+  TOBK_KC_EIGEN_DENSE = 7,     /* eigensolver: dense Rayleigh-Ritz and block Cholesky kernels */
+  TOBK_KC_EIGEN_BLOCK = 8,     /* eigensolver: block orthogonalisation and Ritz-vector kernels */
+  TOBK_KC_COUNT = 9
 } tobk_kernel_class;
 
 /* Enables (1) or disables (0) kernel-class timing on h; enabling resets the counters. */

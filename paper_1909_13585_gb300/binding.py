@@ -63,7 +63,7 @@ _SIGS = {
 }
 
 KERNEL_CLASSES = ("fine_smooth", "fine_residual", "fine_cg_matvec", "coarse", "transfer", "coarsest",
-                  "vector")
+                  "vector", "eigen_dense", "eigen_block")
 
 
 def launch_count():

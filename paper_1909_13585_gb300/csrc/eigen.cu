@@ -4,17 +4,21 @@
 // With mu = 1/lambda the pencil reads -G phi = mu K phi: the q lowest positive lambda are the q
 // largest positive mu of the operator T = K^{-1}(-G), which is self-adjoint in the K inner product.
 // The paper solves this problem with Krylov-Schur to a residual of 1e-8 (Appendix A).  Here a
-// block Krylov/Davidson iteration with explicit Rayleigh-Ritz is used: the basis V is kept
-// K-orthonormal, each outer step appends T applied to the unconverged Ritz vectors (one multi-RHS
-// mgPCG solve on the sub-hierarchy below the level), and the projected pencil (V^T(-G)V, V^T K V)
-// is solved densely in a single thread block.  Convergence: ||(K + lambda G) x|| / ||K x|| <= tol.
+// block generalised-Davidson iteration with explicit Rayleigh-Ritz is used: the basis V is kept
+// K-orthonormal, each outer step appends the multigrid-preconditioned residuals
+// M(-G x_i - theta_i K x_i) of the unconverged Ritz pairs (one V-cycle for all of them, on the
+// sub-hierarchy below the level), and the projected problem V^T(-G)V is solved densely in a single
+// thread block.  Convergence: ||(K + lambda G) x|| / ||K x|| <= tol for the q wanted pairs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "handle.h"
+#include "small_dense.cuh"
 
 namespace tobk {
 
@@ -97,196 +101,6 @@ __global__ void k_small_cholinv(const double* M, int k, double* Rinv, double* in
   if (t == 0) info[0] = bad ? 1.0 : 0.0;
 }
 
-// Dense Rayleigh-Ritz of the projected pencil: H y = theta B y, B SPD, size m <= 64.
-// Output: theta descending, Y (ld = ldy) with Y^T B Y = I.  One thread block, FP64.
-constexpr int kRRMax = 64;
-
-__global__ void __launch_bounds__(512) k_small_rr(const double* H, const double* B, int m, int ld, double* theta,
-                                                  double* Y, int ldy, double* info, int max_sweeps) {
-  extern __shared__ double sm[];
-  double* L = sm;                   // [m*m]  Cholesky factor of B (lower)
-  double* Cm = sm + m * m;          // [m*m]  L^{-1} H L^{-T}, then rotated
-  double* Vv = sm + 2 * m * m;      // [m*m]  accumulated rotations
-  double* rc = sm + 3 * m * m;      // [kRRMax] cosines
-  double* rs = rc + kRRMax;         // [kRRMax] sines
-  double* red = rs + kRRMax;        // [64] reduction scratch
-  __shared__ int s_bad;
-  __shared__ double s_off, s_tot;
-  const int t = threadIdx.x, nt = blockDim.x;
-  if (t == 0) s_bad = 0;
-  for (int q = t; q < m * m; q += nt) {
-    const int i = q / m, j = q % m;
-    L[q] = B[(size_t)i * ld + j];
-    Cm[q] = H[(size_t)i * ld + j];
-    Vv[q] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (t == 0) {
-      double d = L[j * m + j];
-      for (int p = 0; p < j; ++p) d -= L[j * m + p] * L[j * m + p];
-      if (!(d > 0.0)) {
-        s_bad = 1;
-        d = 1e-300;
-      }
-      L[j * m + j] = sqrt(d);
-    }
-    __syncthreads();
-    for (int i = j + 1 + t; i < m; i += nt) {
-      double s = L[i * m + j];
-      for (int p = 0; p < j; ++p) s -= L[i * m + p] * L[j * m + p];
-      L[i * m + j] = s / L[j * m + j];
-    }
-    __syncthreads();
-  }
-  // Cm <- L^{-1} Cm (columns)
-  for (int c = t; c < m; c += nt) {
-    for (int i = 0; i < m; ++i) {
-      double s = Cm[i * m + c];
-      for (int p = 0; p < i; ++p) s -= L[i * m + p] * Cm[p * m + c];
-      Cm[i * m + c] = s / L[i * m + i];
-    }
-  }
-  __syncthreads();
-  // Cm <- Cm L^{-T} (rows)
-  for (int r = t; r < m; r += nt) {
-    for (int i = 0; i < m; ++i) {
-      double s = Cm[r * m + i];
-      for (int p = 0; p < i; ++p) s -= Cm[r * m + p] * L[i * m + p];
-      Cm[r * m + i] = s / L[i * m + i];
-    }
-  }
-  __syncthreads();
-  for (int q = t; q < m * m; q += nt) {
-    const int i = q / m, j = q % m;
-    if (i < j) {
-      const double a = 0.5 * (Cm[i * m + j] + Cm[j * m + i]);
-      Cm[i * m + j] = a;
-      Cm[j * m + i] = a;
-    }
-  }
-  __syncthreads();
-  // parallel cyclic Jacobi with a round-robin pairing (mp players, mp even)
-  const int mp = (m + 1) & ~1;
-  int sweeps = 0;
-  for (; sweeps < max_sweeps; ++sweeps) {
-    double off = 0.0, tot = 0.0;
-    for (int q = t; q < m * m; q += nt) {
-      const double v = Cm[q] * Cm[q];
-      tot += v;
-      if (q / m != q % m) off += v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((t & 31) == 0) {
-      red[(t >> 5) * 2] = off;
-      red[(t >> 5) * 2 + 1] = tot;
-    }
-    __syncthreads();
-    if (t == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < (nt + 31) / 32; ++w) {
-        a += red[2 * w];
-        b += red[2 * w + 1];
-      }
-      s_off = a;
-      s_tot = b;
-    }
-    __syncthreads();
-    if (!(s_off > 1e-30 * s_tot)) break;
-    for (int round = 0; round < mp - 1; ++round) {
-      for (int pr = t; pr < mp / 2; pr += nt) {
-        int p, q;
-        if (pr == 0) {
-          p = mp - 1;
-          q = round;
-        } else {
-          p = (round + pr) % (mp - 1);
-          q = (round - pr + (mp - 1)) % (mp - 1);
-        }
-        double c = 1.0, s = 0.0;
-        if (p < m && q < m) {
-          const double apq = Cm[p * m + q];
-          if (apq != 0.0) {
-            const double tau = (Cm[q * m + q] - Cm[p * m + p]) / (2.0 * apq);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
-            s = tt * c;
-          }
-        }
-        rc[pr] = c;
-        rs[pr] = s;
-      }
-      __syncthreads();
-      // rows p, q
-      for (int w = t; w < (mp / 2) * m; w += nt) {
-        const int pr = w / m, k = w % m;
-        int p, q;
-        if (pr == 0) {
-          p = mp - 1;
-          q = round;
-        } else {
-          p = (round + pr) % (mp - 1);
-          q = (round - pr + (mp - 1)) % (mp - 1);
-        }
-        if (p >= m || q >= m) continue;
-        const double c = rc[pr], s = rs[pr];
-        const double xp = Cm[p * m + k], xq = Cm[q * m + k];
-        Cm[p * m + k] = c * xp - s * xq;
-        Cm[q * m + k] = s * xp + c * xq;
-      }
-      __syncthreads();
-      // columns p, q (and the eigenvector accumulation)
-      for (int w = t; w < (mp / 2) * m; w += nt) {
-        const int pr = w / m, k = w % m;
-        int p, q;
-        if (pr == 0) {
-          p = mp - 1;
-          q = round;
-        } else {
-          p = (round + pr) % (mp - 1);
-          q = (round - pr + (mp - 1)) % (mp - 1);
-        }
-        if (p >= m || q >= m) continue;
-        const double c = rc[pr], s = rs[pr];
-        const double xp = Cm[k * m + p], xq = Cm[k * m + q];
-        Cm[k * m + p] = c * xp - s * xq;
-        Cm[k * m + q] = s * xp + c * xq;
-        const double vp = Vv[k * m + p], vq = Vv[k * m + q];
-        Vv[k * m + p] = c * vp - s * vq;
-        Vv[k * m + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-  }
-  // back-transform Y = L^{-T} V (columns)
-  for (int c = t; c < m; c += nt) {
-    for (int i = m - 1; i >= 0; --i) {
-      double s = Vv[i * m + c];
-      for (int p = i + 1; p < m; ++p) s -= L[p * m + i] * Vv[p * m + c];
-      Vv[i * m + c] = s / L[i * m + i];
-    }
-  }
-  __syncthreads();
-  // sort descending by theta (selection by rank; ties broken by index)
-  for (int c = t; c < m; c += nt) {
-    const double tc = Cm[c * m + c];
-    int rank = 0;
-    for (int o = 0; o < m; ++o) {
-      const double to = Cm[o * m + o];
-      if (to > tc || (to == tc && o < c)) ++rank;
-    }
-    theta[rank] = tc;
-    for (int i = 0; i < m; ++i) Y[(size_t)i * ldy + rank] = Vv[i * m + c];
-  }
-  if (t == 0) {
-    info[0] = s_bad ? 1.0 : 0.0;
-    info[1] = (double)sweeps;
-  }
-}
-
 // Column-wise dot products out[i] = sum_k A_i[k] B_i[k] (two stage, deterministic).
 constexpr int kColChunk = 2048;
 __global__ void k_coldots_partial(const double* A, const double* B, int64_t n, int64_t stride, double* partial) {
@@ -331,12 +145,15 @@ __global__ void k_eig_residual_vec(const double* KX, const double* GX, const dou
   R[(int64_t)i * stride + k] = KX[(int64_t)i * stride + k] + lam * GX[(int64_t)i * stride + k];
 }
 
-// W_c = -GX_{sel[c]}
-__global__ void k_gather_neg(const double* GX, const int* sel, int nsel, double* W, int64_t n, int64_t stride) {
+// W_c = -GX_{s} - theta_s KX_{s}, s = sel[c]: the residual of the pencil -G x = mu K x at the Ritz
+// pair (theta_s, x_s)
+__global__ void k_gather_residual(const double* GX, const double* KX, const double* theta, const int* sel,
+                                  double* W, int64_t n, int64_t stride) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int c = blockIdx.y;
-  W[(int64_t)c * stride + k] = -GX[(int64_t)sel[c] * stride + k];
+  const int s = sel[c];
+  W[(int64_t)c * stride + k] = -GX[(int64_t)s * stride + k] - theta[s] * KX[(int64_t)s * stride + k];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -365,12 +182,18 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   double* Cs = h->Cs;
   double* M = h->Cs + (size_t)mmax * nb;  // nb x nb block Gram
   double* Rinv = M + (size_t)nb * nb;
-  const size_t rr_smem = sizeof(double) * (3 * (size_t)kRRMax * kRRMax + 2 * kRRMax + 64);
+  const size_t rr_smem = small_rr_smem_bytes();
+  const size_t tri_smem = small_eig_tridiag_smem_bytes();
   static bool rr_configured = false;
   if (!rr_configured) {
     cudaFuncSetAttribute(k_small_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem);
+    cudaFuncSetAttribute(k_small_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem);
+    cudaFuncSetAttribute(k_tri_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_reduce_smem_bytes());
+    cudaFuncSetAttribute(k_tri_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_finish_smem_bytes());
     rr_configured = true;
   }
+  const int keep_max = std::min(2 * nb, mmax - nb);
+  const bool use_jacobi = std::getenv("TOBK_EIG_JACOBI") != nullptr;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -380,21 +203,33 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   int nadd = nb, m = 0, it = 0, inner_total = 0;
   bool converged = false;
   double worst = INFINITY;
-  std::vector<double> hth(mmax), hres(q), hkx(q);
+  std::vector<double> hth(mmax), hth_prev(mmax, 0.0), hres(q), hkx(q);
+  // The dense Rayleigh-Ritz runs its Jacobi sweeps in FP32 until the wanted Ritz values have
+  // settled to ~1e-6 (their error is quadratic in the residual), then in FP64 for the final digits.
+  bool fp64_mode = std::getenv("TOBK_EIG_FP32_RR") == nullptr;
+  const bool trace = std::getenv("TOBK_EIG_TRACE") != nullptr;
   int rc = TOBK_OK;
   for (it = 0; it < h->desc.eig_max_iter; ++it) {
     // ---- K-orthogonalise the new block against the basis (classical Gram-Schmidt, twice)
+    prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
     for (int pass = 0; pass < 2 && m > 0; ++pass) {
       launch_gram(h->KV, m, W, nadd, n, sd, Cs, h->gram_partial, st);
       launch_combine(h->V, m, Cs, nadd, nadd, -1.0, 1.0, W, n, sd, st);
     }
+    prof_end(h);
     // ---- K-orthonormalise within the block (Cholesky QR, twice)
     for (int pass = 0; pass < 2; ++pass) {
       apply_K_level(h, j, W, KW, nadd, sd);
+      prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
       launch_gram(W, nadd, KW, nadd, n, sd, M, h->gram_partial, st);
+      prof_end(h);
+      prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)nadd);
       ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, nadd, Rinv, sinfo);
+      prof_end(h);
+      prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
       launch_combine(W, nadd, Rinv, nadd, nadd, 1.0, 0.0, Tb, n, sd, st);
       cudaMemcpyAsync(W, Tb, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
+      prof_end(h);
     }
     apply_K_level(h, j, W, KW, nadd, sd);
     apply_G_level(h, j, W, GW, nadd, sd);
@@ -403,25 +238,52 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     cudaMemcpyAsync(h->KV + (size_t)m * n, KW, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(h->GV + (size_t)m * n, GW, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
     const int mn = m + nadd;
+    prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)mn * n);
     launch_gram(h->V, mn, GW, nadd, n, sd, Cs, h->gram_partial, st);
     ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, -1.0, h->Hs, mmax);
-    launch_gram(h->V, mn, KW, nadd, n, sd, Cs, h->gram_partial, st);
-    ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, 1.0, h->Bs, mmax);
+    prof_end(h);
     m = mn;
-    // ---- Rayleigh-Ritz
-    ::tobk::note_launch(), k_small_rr<<<1, 512, rr_smem, st>>>(h->Hs, h->Bs, m, mmax, theta, h->Ys, mmax, sinfo + 2, 40);
+    // ---- Rayleigh-Ritz (the basis is K-orthonormal, so V^T K V = I): the leading eigenpairs of
+    // the projected matrix in FP64 (Householder + bisection + inverse iteration); the Jacobi
+    // variant (FP32 sweeps, FP64 refinement near convergence and before restarts) is kept as an
+    // alternative.
+    const bool full = !use_jacobi || fp64_mode || (m + nb > mmax);
+    prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)m);
+    if (use_jacobi) {
+      ::tobk::note_launch(), k_small_rr<<<1, 512, rr_smem, st>>>(h->Hs, m, mmax, theta, h->Ys, mmax, sinfo + 2,
+                                                                 full ? 1 : 0);
+    } else {
+      const int nvec = std::min(m, keep_max);
+      ::tobk::note_launch(), k_tri_reduce<<<1, 256, tri_reduce_smem_bytes(), st>>>(h->Hs, m, mmax, h->tri, mmax);
+      ::tobk::note_launch(), k_tri_eigvec<<<nvec, 64, 0, st>>>(h->tri, mmax, m);
+      ::tobk::note_launch(), k_tri_finish<<<1, 256, tri_finish_smem_bytes(), st>>>(h->tri, mmax, m, nvec, theta,
+                                                                                   h->Ys, mmax);
+    }
+    prof_end(h);
     const int kk = std::min(nb, m);
+    prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)m * n);
     launch_combine(h->V, m, h->Ys, mmax, kk, 1.0, 0.0, X, n, sd, st);
     launch_combine(h->KV, m, h->Ys, mmax, kk, 1.0, 0.0, KX, n, sd, st);
     launch_combine(h->GV, m, h->Ys, mmax, kk, 1.0, 0.0, GX, n, sd, st);
     ::tobk::note_launch(), k_eig_residual_vec<<<dim3(nblk(n), q), 256, 0, st>>>(KX, GX, theta, Tb, n, sd);
     launch_coldots(Tb, Tb, q, n, sd, resn, h->gram_partial, st);
     launch_coldots(KX, KX, q, n, sd, kxn, h->gram_partial, st);
+    prof_end(h);
     cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double) * 512, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     rc = check_cuda(h, "eigen_solve");
     if (rc) break;
     for (int i = 0; i < kk; ++i) hth[i] = h->hscal[i];
+    if (!fp64_mode && it > 0) {
+      double change = 0.0;
+      for (int i = 0; i < q && i < kk; ++i)
+        change = std::max(change, std::fabs(hth[i] - hth_prev[i]) / std::max(std::fabs(hth[i]), 1e-300));
+      if (change < 1e-6) fp64_mode = true;
+    }
+    for (int i = 0; i < kk; ++i) hth_prev[i] = hth[i];
+    if (trace)
+      std::fprintf(stderr, "[tobk eig] level %d it %d m %d nadd %d full %d theta0 %.9e thetaq %.9e sweeps %g/%g\n", j, it,
+                   m, nadd, full ? 1 : 0, hth[0], hth[std::min(q, kk) - 1], h->hscal[386], h->hscal[387]);
     worst = 0.0;
     std::vector<int> sel;
     for (int i = 0; i < kk; ++i) {
@@ -433,33 +295,34 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       }
       if (!ok) sel.push_back(i);
     }
-    converged = true;
+    if (trace) std::fprintf(stderr, "[tobk eig]   worst residual %.3e, unconverged %d\n", worst, (int)sel.size());
+    converged = full;
     for (int i = 0; i < q; ++i) {
       const double res = std::sqrt(h->hscal[128 + i] / std::max(h->hscal[256 + i], 1e-300));
       if (!(hth[i] > 0.0 && res <= tol)) converged = false;
     }
     if (converged) break;
-    // ---- expansion block W = T X_sel = K^{-1} (-G X_sel)
+    // ---- expansion block (generalised Davidson): W = M r_s, r_s = -G x_s - theta_s K x_s for the
+    // selected Ritz pairs, M = one multigrid V-cycle for K on this level and below
     nadd = (int)sel.size();
     cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st);
-    ::tobk::note_launch(), k_gather_neg<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, dsel, nadd, Tb, n, sd);
-    tobk_solve_info si{};
-    int src = pcg_solve(h, j, Tb, W, nadd, 1e-10, h->desc.max_iter, false, TOBK_FP64, &si);
-    inner_total += si.iterations;
-    if (src && src != TOBK_E_NOT_CONVERGED) {
-      rc = src;
-      break;
-    }
-    // ---- thick restart: keep the kk Ritz vectors
+    ::tobk::note_launch(), k_gather_residual<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, KX, theta, dsel, Tb, n, sd);
+    apply_vcycle(h, j, nadd, Tb, W);
+    ++inner_total;
+    // ---- thick restart: keep the kk Ritz vectors (FP64-accurate, hence K-orthonormal)
     if (m + nadd > mmax) {
-      cudaMemcpyAsync(h->V, X, sizeof(double) * kk * n, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(h->KV, KX, sizeof(double) * kk * n, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(h->GV, GX, sizeof(double) * kk * n, cudaMemcpyDeviceToDevice, st);
-      launch_gram(h->V, kk, h->GV, kk, n, sd, Cs, h->gram_partial, st);
-      ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)kk * kk), 256, 0, st>>>(Cs, kk, kk, 0, -1.0, h->Hs, mmax);
-      launch_gram(h->V, kk, h->KV, kk, n, sd, Cs, h->gram_partial, st);
-      ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)kk * kk), 256, 0, st>>>(Cs, kk, kk, 0, 1.0, h->Bs, mmax);
-      m = kk;
+      // keep the leading min(2 nb, mmax - nb) Ritz vectors (and their K and G images)
+      const int keep = std::min(std::min(2 * nb, mmax - nb), m);
+      double* tmp = h->EW + (size_t)4 * nb * n;
+      double* bases[3] = {h->V, h->KV, h->GV};
+      for (double* bsp : bases) {
+        launch_combine(bsp, m, h->Ys, mmax, keep, 1.0, 0.0, tmp, n, sd, st);
+        cudaMemcpyAsync(bsp, tmp, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st);
+      }
+      launch_gram(h->V, keep, h->GV, keep, n, sd, Cs, h->gram_partial, st);
+      ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)keep * keep), 256, 0, st>>>(Cs, keep, keep, 0, -1.0, h->Hs,
+                                                                                       mmax);
+      m = keep;
     }
   }
   if (rc == TOBK_OK) {

@@ -53,6 +53,7 @@ struct tobk_handle {
   double *V = nullptr, *KV = nullptr, *GV = nullptr, *EW = nullptr, *EKW = nullptr, *EGW = nullptr;
   double *Hs = nullptr, *Bs = nullptr, *Ys = nullptr, *Cs = nullptr, *gram_partial = nullptr;
   double* small_host = nullptr;  // pinned
+  double* tri = nullptr;         // scratch of the split small eigensolver (reflectors, T, vectors)
   // small scalars
   double* dscal = nullptr;       // device scratch scalars [256]
   double* hscal = nullptr;       // pinned host scratch [256]
@@ -105,6 +106,9 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
 // G_j v at level j (fine: matrix-free from Gs; coarse: Galerkin Ge)
 void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
 void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
+// out = M r: one multigrid V-cycle for K on level j and below (nr RHS, stride n_j); r must not be
+// one of level j's own work vectors
+void apply_vcycle(tobk_handle* h, int j, int nr, const double* r, double* out);
 void prof_begin(tobk_handle* h, int kc, double units);
 void prof_end(tobk_handle* h);
 void prof_flush(tobk_handle* h);

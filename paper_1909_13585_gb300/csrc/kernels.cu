@@ -114,8 +114,16 @@ void apply_dim32(const LevelOpDesc& d, int mode, const float* v, const float* b,
     apply_dispatch<DIM>(make_fine<DIM, float>(d, d.scale32), mode, v, b, dinv, y, omega, nr, stride, s);
 }
 
+template <typename T>
+void launch_apply_stencil(const Grid& g, const T* S, const uint8_t* fixed, int mode, const T* v, const T* b,
+                          const T* dinv, T* y, T omega, int nr, int64_t stride, cudaStream_t s);
+
 void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double* b, const double* dinv,
                   double* y, double omega, int nr, int64_t stride, cudaStream_t s) {
+  if (op.S64) {
+    launch_apply_stencil<double>(op.g, op.S64, op.fixed, mode, v, b, dinv, y, omega, nr, stride, s);
+    return;
+  }
   if (op.g.dim == 2)
     apply_dim<2>(op, mode, v, b, dinv, y, omega, nr, stride, s);
   else
@@ -124,6 +132,10 @@ void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double
 
 void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
                     float* y, float omega, int nr, int64_t stride, cudaStream_t s) {
+  if (op.S32) {
+    launch_apply_stencil<float>(op.g, op.S32, op.fixed, mode, v, b, dinv, y, omega, nr, stride, s);
+    return;
+  }
   if (op.g.dim == 2)
     apply_dim32<2>(op, mode, v, b, dinv, y, omega, nr, stride, s);
   else

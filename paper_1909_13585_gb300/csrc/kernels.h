@@ -28,7 +28,16 @@ struct LevelOpDesc {
   const double* Ke64;
   const float* Ke32;
   bool stored;
+  // coarse: the same operator assembled per node as a 3^d-point stencil of d x d blocks
+  // ([node][neighbour][d][d]); when set, smoother and residual launches use it
+  const double* S64 = nullptr;
+  const float* S32 = nullptr;
 };
+
+// Assembles the per-node stencil of a stored-element-matrix level (rows/columns of fixed DOFs
+// zeroed); also writes the float copy when S32 != nullptr.
+void launch_stencil_assemble(const Grid& g, const double* Ke, const uint8_t* fixed, double* S, float* S32,
+                             cudaStream_t s);
 
 enum ApplyMode { APPLY_KV = 0, APPLY_RES = 1, APPLY_JAC = 2 };
 

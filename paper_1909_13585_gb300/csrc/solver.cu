@@ -152,8 +152,11 @@ static void layout(tobk_handle* h, Arena& a) {
     const int64_t n = L.g.n, m = L.g.m;
     L.fixed = a.take<uint8_t>(n);
     if (j > 0) {
+      const int ne = (h->dim == 2 ? 9 : 27) * h->dim * h->dim;
       L.Ke = a.take<double>(m * nd * nd);
       if (mixed) L.Ke32 = a.take<float>(m * nd * nd);
+      L.S = a.take<double>((size_t)ne * L.g.nnode);
+      if (mixed) L.S32 = a.take<float>((size_t)ne * L.g.nnode);
     }
     if (j > 0 && j <= h->eig) L.Ge = a.take<double>(m * nd * nd);
     L.dinv = a.take<double>(n);
@@ -215,13 +218,15 @@ static void layout(tobk_handle* h, Arena& a) {
   h->V = a.take<double>((size_t)mm * ne);
   h->KV = a.take<double>((size_t)mm * ne);
   h->GV = a.take<double>((size_t)mm * ne);
-  h->EW = a.take<double>((size_t)4 * nb * ne);   // X, KX, GX, W blocks
+  h->EW = a.take<double>((size_t)(4 * nb + mm) * ne);   // X, KX, GX, W blocks + restart scratch
   h->EKW = a.take<double>((size_t)2 * nb * ne);
   h->EGW = a.take<double>((size_t)nb * ne);
   h->Hs = a.take<double>((size_t)mm * mm);
   h->Bs = a.take<double>((size_t)mm * mm);
   h->Ys = a.take<double>((size_t)mm * mm);
   h->Cs = a.take<double>((size_t)mm * mm);
+  // small eigensolver scratch: reflectors [mm*mm], d, e, beta [mm each], 48 eigenvalues, 48 vectors
+  h->tri = a.take<double>((size_t)mm * mm + 3 * (size_t)mm + 48 + 48 * (size_t)mm);
   const int64_t gp_rows = std::max<int64_t>(gram_partial_blocks(ne), gram_partial_blocks(nf));
   h->gram_partial = a.take<double>((size_t)gp_rows * mm * std::max(mm, nb));
   h->dscal = a.take<double>(1024);
@@ -250,7 +255,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
   h->eig = d->eig_level - 1;
   h->q = d->num_modes;
   h->eig_nb = h->q + 4;
-  h->eig_mmax = std::min(4 * h->eig_nb, 64);
+  h->eig_mmax = 64;
   h->rmax = std::max({d->max_rhs, h->eig_nb, h->q + 1, 1});
   if (h->rmax > kMaxRhs || h->eig_mmax < 2 * h->eig_nb) {
     delete h;
@@ -400,6 +405,8 @@ LevelOpDesc level_op(tobk_handle* h, int j) {
     d.stored = true;
     d.Ke64 = h->lv[j].Ke;
     d.Ke32 = h->lv[j].Ke32;
+    d.S64 = h->lv[j].S;
+    d.S32 = h->lv[j].S32;
   }
   return d;
 }
@@ -423,6 +430,7 @@ int setup_hierarchy(tobk_handle* h) {
       launch_galerkin_stored(Lf.g, Lc.g, Lf.fixed, Lf.Ke, h->d_W, Lc.Ke, s);
     if (mixed) launch_f64_to_f32(Lc.Ke, Lc.Ke32, Lc.g.m * nd2, s);
     launch_diag(level_op(h, j), Lc.dinv, mixed ? Lc.dinv32 : nullptr, s);
+    launch_stencil_assemble(Lc.g, Lc.Ke, Lc.fixed, Lc.S, mixed ? Lc.S32 : nullptr, s);
   }
   const int jc = h->L - 1;
   launch_dense_assemble(level_op(h, jc), h->Adense, s);
@@ -571,6 +579,12 @@ static double* precondition(tobk_handle* h, int s, int nr, const double* r, doub
   float* z32 = vcycle32(h, s, nr, L.b32, L.z32, L.t32);
   launch_f32_to_f64(z32, z, (int64_t)nr * n, h->stream);
   return z;
+}
+
+void apply_vcycle(tobk_handle* h, int j, int nr, const double* r, double* out) {
+  Level& L = h->lv[j];
+  double* z = precondition(h, j, nr, r, L.z, L.t, h->desc.precision);
+  cudaMemcpyAsync(out, z, sizeof(double) * nr * L.g.n, cudaMemcpyDeviceToDevice, h->stream);
 }
 
 // ================================================================================================

@@ -101,6 +101,8 @@ struct Level {
   double* Ke = nullptr;       // [m][nd*nd]
   float* Ke32 = nullptr;      // FP32 copy for the mixed-precision V-cycle
   double* Ge = nullptr;       // [m][nd*nd] Galerkin G (only down to the eigen level)
+  double* S = nullptr;        // assembled nodal stencil of K (levels >= 2), see stencil.cu
+  float* S32 = nullptr;
   double* dinv = nullptr;     // [n] inverse diagonal (0 at fixed DOFs)
   float* dinv32 = nullptr;
   // V-cycle work vectors, capacity rmax RHS: b, z, t (ping-pong), r
