@@ -53,13 +53,53 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision / 3D form measurements")
     ap.add_argument("--profile-run", action="store_true",
                     help="one untimed step only (for an external profiler's launch list)")
     return ap.parse_args()
 
 
-def rhs_per_step(p):
-    return 1 + (2 * p.num_modes if p.eig_level > 1 else p.num_modes)
+def rhs_per_step(p, fused=False):
+    """Fine-grid right-hand sides solved per step: the load, the q fine-mode systems of the
+    multilevel path (none for the exact path) and the q adjoint systems (+1 when the load is
+    re-solved in the same block)."""
+    return 1 + (p.num_modes if p.eig_level > 1 else 0) + p.num_modes + (1 if fused else 0)
+
+
+def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush):
+    """The same step on another workload / precision, device-timed per step with an L2 flush."""
+    p = synthetic.config(name)
+    stream = torch.cuda.Stream(device=dev)
+    s = pkg.Solver(p, stream=stream, precision=precision, fuse_load_adjoint=1 if fused else 0)
+    x_d = torch.from_numpy(p.x).to(dev)
+    q, m = p.num_modes, p.num_elements
+    dlam_d = torch.zeros((q, m), dtype=torch.float64, device=dev)
+    dJ_d = torch.zeros(m, dtype=torch.float64, device=dev)
+    info = {}
+
+    def step():
+        s.set_densities(x_d)
+        _, i1 = s.solve_equilibrium()
+        _, i2 = s.compute_buckling()
+        _, _, i3 = s.compute_sensitivities(dlam_d, dJ_d)
+        info.update(la_iters=i1["iterations"], buckling_iters=i2["iterations"], adjoint_iters=i3["iterations"])
+
+    for _ in range(warmup):
+        step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    units = p.num_dofs * rhs_per_step(p, fused)
+    s.close()
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "dofs": p.num_dofs,
+            "rhs_per_step": rhs_per_step(p, fused), "precision": "fp64" if precision == 0 else "fp32_vcycle",
+            "fused_load_adjoint": bool(fused), "steps": steps, "warmup": warmup, **info}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -356,6 +396,14 @@ def ours(args):
         e2e = {"value": world * units * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 8 * m + 8 * n + n, "d2h_bytes_per_step": 8 * q + 8 * q * m + 8 * m + 8}
 
+    forms = {}
+    if not args.no_forms:
+        fs, fw = min(args.steps, 3), max(3, min(args.warmup, 3))
+        forms["column480x160_fp32_vcycle"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP32_VCYCLE, False,
+                                                          fs, fw, dev, flush)
+        forms["cantilever96x48x48_fp32_vcycle_fused"] = measure_form(pkg, torch, "cantilever96x48x48",
+                                                                     pkg.TOBK_FP32_VCYCLE, True, fs, fw, dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times = run_oracle(args.workload, 1)
@@ -373,6 +421,7 @@ def ours(args):
             "wall_s_timed_region": t_wall,
             "phases_ms": {k: statistics.median(v) for k, v in phases.items()},
             "kernel_classes": prof,
+            "forms": forms,
         }
         print(json.dumps(line))
     if world > 1:

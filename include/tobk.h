@@ -94,7 +94,17 @@ typedef struct {
   double eig_tol;    /* eigenpair residual ||(K + lam G) phi|| / ||K phi|| target (1e-8, Appendix A) */
   int eig_max_iter;  /* outer iterations of the block eigensolver */
   int max_rhs;       /* largest multi-RHS block the caller will pass to tobk_solve (>= 1) */
+  int eig_inner_iters; /* eigensolver preconditioner: 0 = one V-cycle, k > 0 = k mgPCG iterations */
+  int fuse_load_adjoint; /* 1: tobk_compute_sensitivities solves K [u, Z] = [f, B] as one (q+1)-RHS
+                            block (the load re-solved beside the q adjoint systems, u replaced by the
+                            new solution); 0: only the q adjoint systems */
+  int smoother;      /* tobk_smoother: damped Jacobi (weight omega) or Chebyshev (degree nu_pre /
+                        nu_post in D^{-1} K over [lambda_max / cheb_ratio, lambda_max], lambda_max
+                        measured per level and design by power iteration); nu_pre, nu_post <= 8 */
+  double cheb_ratio; /* lambda_max / lambda_min of the Chebyshev interval (e.g. 10) */
 } tobk_desc;
+
+typedef enum { TOBK_SMOOTHER_JACOBI = 0, TOBK_SMOOTHER_CHEBYSHEV = 1 } tobk_smoother;
 
 typedef struct {
   int iterations;        /* CG iterations (max over RHS) or eigensolver outer iterations */

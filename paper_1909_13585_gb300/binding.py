@@ -24,7 +24,8 @@ class tobk_desc(C.Structure):
                 ("eig_level", C.c_int), ("num_modes", C.c_int), ("precision", C.c_int),
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("omega", C.c_double),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("eig_tol", C.c_double),
-                ("eig_max_iter", C.c_int), ("max_rhs", C.c_int)]
+                ("eig_max_iter", C.c_int), ("max_rhs", C.c_int), ("eig_inner_iters", C.c_int),
+                ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double)]
 
 
 class tobk_solve_info(C.Structure):

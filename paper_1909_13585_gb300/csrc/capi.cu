@@ -39,6 +39,10 @@ int tobk_default_desc(tobk_desc* d) {
   d->eig_tol = 1e-8;
   d->eig_max_iter = 200;
   d->max_rhs = 10;
+  d->eig_inner_iters = 2;
+  d->fuse_load_adjoint = 0;
+  d->smoother = TOBK_SMOOTHER_CHEBYSHEV;
+  d->cheb_ratio = 10.0;
   return TOBK_OK;
 }
 

@@ -307,8 +307,20 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     nadd = (int)sel.size();
     cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st);
     ::tobk::note_launch(), k_gather_residual<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, KX, theta, dsel, Tb, n, sd);
-    apply_vcycle(h, j, nadd, Tb, W);
-    ++inner_total;
+    if (h->desc.eig_inner_iters <= 0) {
+      apply_vcycle(h, j, nadd, Tb, W);
+      ++inner_total;
+    } else {
+      // a few mgPCG iterations on K w = r (a better approximation of K^{-1} r than one V-cycle;
+      // the iteration limit is the point, so "not converged" is the expected status)
+      tobk_solve_info si{};
+      const int src = pcg_solve(h, j, Tb, W, nadd, 1e-300, h->desc.eig_inner_iters, false, h->desc.precision, &si);
+      if (src && src != TOBK_E_NOT_CONVERGED) {
+        rc = src;
+        break;
+      }
+      inner_total += si.status_detail;
+    }
     // ---- thick restart: keep the kk Ritz vectors (FP64-accurate, hence K-orthonormal)
     if (m + nadd > mmax) {
       // keep the leading min(2 nb, mmax - nb) Ritz vectors (and their K and G images)

@@ -43,6 +43,8 @@ struct tobk_handle {
   // buckling / sensitivity outputs
   double* modes = nullptr;   // [q][n] fine-grid modes (K-normalised)
   double* lam = nullptr;     // [q] device
+  double* adj_blockB = nullptr;  // [q+1][n]: f, then the adjoint right-hand sides
+  double* adj_blockX = nullptr;  // [q+1][n]: u of the fused solve, then the adjoint solutions
   double* adj = nullptr;     // [q][n] adjoint solutions
   double* adj_rhs = nullptr; // [q][n]
   double* dlam = nullptr;    // [q][m]
@@ -93,6 +95,8 @@ int set_densities(tobk_handle* h, const double* x, bool on_device);
 int set_load(tobk_handle* h, const double* f, bool on_device);
 int set_fixed(tobk_handle* h, const uint8_t* fixed, bool on_device);
 int setup_hierarchy(tobk_handle* h);
+// lambda_max(D^{-1} K) per level and the smoother coefficients (called by setup_hierarchy)
+void setup_smoothers(tobk_handle* h);
 LevelOpDesc level_op(tobk_handle* h, int j);
 // Multi-RHS MGCG solve at level s (0-based): K_s X = B, nr RHS (device, [nr][n_s]).
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,

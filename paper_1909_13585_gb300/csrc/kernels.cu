@@ -53,7 +53,7 @@ StoredOp<DIM, T> make_stored(const LevelOpDesc& d, const T* Ke) {
 // ================================================================================================
 template <int DIM, class Op, typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_apply(const __grid_constant__ Op op, const T* __restrict__ v, const T* __restrict__ b,
-                                                     const T* __restrict__ dinv, T* __restrict__ y, T omega,
+                                                     const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
                                                      int64_t stride, const double* __restrict__ act) {
   if (rhs_done(act)) return;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,68 +78,83 @@ __global__ void __launch_bounds__(kThreads) k_apply(const __grid_constant__ Op o
     } else if (MODE == APPLY_RES) {
       out = b[idx] - acc[c];
     } else {
-      out = v[idx] + omega * dinv[idx] * (b[idx] - acc[c]);
+      const T r = dinv[idx] * (b[idx] - acc[c]);
+      const T dn = (sm.d_in ? sm.coef[0] * sm.d_in[off + idx] : T(0)) + sm.coef[1] * r;
+      if (sm.d_out) sm.d_out[off + idx] = dn;
+      out = v[idx] + dn;
     }
     y[idx] = out;
   }
 }
 
 template <int DIM, class Op, typename T>
-void apply_dispatch(const Op& op, int mode, const T* v, const T* b, const T* dinv, T* y, T omega, int nr,
+void apply_dispatch(const Op& op, int mode, const T* v, const T* b, const T* dinv, T* y, SmoothArgs<T> sm, int nr,
                     int64_t stride, cudaStream_t s) {
   dim3 grid(blocks_for(op.g.nnode), nr);
   if (mode == APPLY_KV)
-    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_KV><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride, active_rhs());
+    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_KV><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, sm, stride, active_rhs());
   else if (mode == APPLY_RES)
-    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_RES><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride, active_rhs());
+    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_RES><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, sm, stride, active_rhs());
   else
-    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_JAC><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, omega, stride, active_rhs());
+    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_JAC><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, sm, stride, active_rhs());
 }
 
 template <int DIM>
 void apply_dim(const LevelOpDesc& d, int mode, const double* v, const double* b, const double* dinv, double* y,
-               double omega, int nr, int64_t stride, cudaStream_t s) {
+               SmoothArgs<double> sm, int nr, int64_t stride, cudaStream_t s) {
   if (d.stored)
-    apply_dispatch<DIM>(make_stored<DIM, double>(d, d.Ke64), mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dispatch<DIM>(make_stored<DIM, double>(d, d.Ke64), mode, v, b, dinv, y, sm, nr, stride, s);
   else
-    apply_dispatch<DIM>(make_fine<DIM, double>(d, d.scale64), mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dispatch<DIM>(make_fine<DIM, double>(d, d.scale64), mode, v, b, dinv, y, sm, nr, stride, s);
 }
 
 template <int DIM>
 void apply_dim32(const LevelOpDesc& d, int mode, const float* v, const float* b, const float* dinv, float* y,
-                 float omega, int nr, int64_t stride, cudaStream_t s) {
+                 SmoothArgs<float> sm, int nr, int64_t stride, cudaStream_t s) {
   if (d.stored)
-    apply_dispatch<DIM>(make_stored<DIM, float>(d, d.Ke32), mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dispatch<DIM>(make_stored<DIM, float>(d, d.Ke32), mode, v, b, dinv, y, sm, nr, stride, s);
   else
-    apply_dispatch<DIM>(make_fine<DIM, float>(d, d.scale32), mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dispatch<DIM>(make_fine<DIM, float>(d, d.scale32), mode, v, b, dinv, y, sm, nr, stride, s);
 }
 
 template <typename T>
 void launch_apply_stencil(const Grid& g, const T* S, const uint8_t* fixed, int mode, const T* v, const T* b,
-                          const T* dinv, T* y, T omega, int nr, int64_t stride, cudaStream_t s);
+                          const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s);
+
+template <typename T>
+void launch_fine_q4(const Grid& g, const T* Ek, const uint8_t* fixed, const double* Ke0, int mode, const T* v,
+                    const T* b, const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s);
 
 void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double* b, const double* dinv,
-                  double* y, double omega, int nr, int64_t stride, cudaStream_t s) {
+                  double* y, SmoothArgs<double> sm, int nr, int64_t stride, cudaStream_t s) {
   if (op.S64) {
-    launch_apply_stencil<double>(op.g, op.S64, op.fixed, mode, v, b, dinv, y, omega, nr, stride, s);
+    launch_apply_stencil<double>(op.g, op.S64, op.fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+    return;
+  }
+  if (!op.stored && op.g.dim == 2) {
+    launch_fine_q4<double>(op.g, op.scale64, op.fixed, op.T0, mode, v, b, dinv, y, sm, nr, stride, s);
     return;
   }
   if (op.g.dim == 2)
-    apply_dim<2>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dim<2>(op, mode, v, b, dinv, y, sm, nr, stride, s);
   else
-    apply_dim<3>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dim<3>(op, mode, v, b, dinv, y, sm, nr, stride, s);
 }
 
 void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
-                    float* y, float omega, int nr, int64_t stride, cudaStream_t s) {
+                    float* y, SmoothArgs<float> sm, int nr, int64_t stride, cudaStream_t s) {
   if (op.S32) {
-    launch_apply_stencil<float>(op.g, op.S32, op.fixed, mode, v, b, dinv, y, omega, nr, stride, s);
+    launch_apply_stencil<float>(op.g, op.S32, op.fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+    return;
+  }
+  if (!op.stored && op.g.dim == 2) {
+    launch_fine_q4<float>(op.g, op.scale32, op.fixed, op.T0, mode, v, b, dinv, y, sm, nr, stride, s);
     return;
   }
   if (op.g.dim == 2)
-    apply_dim32<2>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dim32<2>(op, mode, v, b, dinv, y, sm, nr, stride, s);
   else
-    apply_dim32<3>(op, mode, v, b, dinv, y, omega, nr, stride, s);
+    apply_dim32<3>(op, mode, v, b, dinv, y, sm, nr, stride, s);
 }
 
 // ---- stress stiffness operator (fine level) -----------------------------------------------------
@@ -224,22 +239,24 @@ void launch_diag(const LevelOpDesc& d, double* dinv, float* dinv32, cudaStream_t
 
 // ---- first Jacobi sweep from zero --------------------------------------------------------------
 template <typename T>
-__global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ z, T omega,
+__global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ z, SmoothArgs<T> sm,
                           int64_t n, int64_t stride, const double* __restrict__ act) {
   if (rhs_done(act)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t off = (int64_t)blockIdx.y * stride;
-  z[off + i] = omega * dinv[i] * b[off + i];
+  const T zi = sm.coef[1] * dinv[i] * b[off + i];
+  z[off + i] = zi;
+  if (sm.d_out) sm.d_out[off + i] = zi;
 }
 
-void launch_jacobi0(const double* b, const double* dinv, double* z, double omega, int64_t n, int nr,
+void launch_jacobi0(const double* b, const double* dinv, double* z, SmoothArgs<double> sm, int64_t n, int nr,
                     int64_t stride, cudaStream_t s) {
-  ::tobk::note_launch(), k_jacobi0<double><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride, active_rhs());
+  ::tobk::note_launch(), k_jacobi0<double><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, sm, n, stride, active_rhs());
 }
-void launch_jacobi0_32(const float* b, const float* dinv, float* z, float omega, int64_t n, int nr, int64_t stride,
+void launch_jacobi0_32(const float* b, const float* dinv, float* z, SmoothArgs<float> sm, int64_t n, int nr, int64_t stride,
                        cudaStream_t s) {
-  ::tobk::note_launch(), k_jacobi0<float><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, omega, n, stride, active_rhs());
+  ::tobk::note_launch(), k_jacobi0<float><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, sm, n, stride, active_rhs());
 }
 
 // ---- transfers ----------------------------------------------------------------------------------
@@ -455,28 +472,35 @@ void launch_dense_assemble(const LevelOpDesc& d, double* A, cudaStream_t s) {
 
 // One Gauss-Jordan elimination step on an SPD matrix (no pivoting): after steps k = 0..n-1 the
 // buffer holds the inverse.
-__global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int64_t n, int64_t k) {
+// rcp[k & 1] holds 1 / A[k][k] on entry; the thread that produces the next pivot B[k+1][k+1] stores
+// its reciprocal in rcp[(k + 1) & 1], so each step performs a single FP64 division.
+__global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, int64_t n, int64_t k,
+                          double* __restrict__ rcp) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;
   const int64_t i = idx / n, j = idx % n;
-  const double p = A[k * n + k];
+  const double rp = rcp[k & 1];
   double v;
   if (i == k && j == k)
-    v = 1.0 / p;
+    v = rp;
   else if (i == k)
-    v = A[k * n + j] / p;
+    v = A[k * n + j] * rp;
   else if (j == k)
-    v = -A[i * n + k] / p;
+    v = -A[i * n + k] * rp;
   else
-    v = A[i * n + j] - A[i * n + k] * A[k * n + j] / p;
+    v = A[i * n + j] - A[i * n + k] * (A[k * n + j] * rp);
   B[idx] = v;
+  if (i == k + 1 && j == k + 1) rcp[(k + 1) & 1] = 1.0 / v;
 }
 
-double* launch_dense_invert(double* A, double* work, int64_t n, cudaStream_t s) {
+__global__ void k_first_pivot(const double* A, double* rcp) { rcp[0] = 1.0 / A[0]; }
+
+double* launch_dense_invert(double* A, double* work, int64_t n, double* rcp2, cudaStream_t s) {
   double* src = A;
   double* dst = work;
+  ::tobk::note_launch(), k_first_pivot<<<1, 1, 0, s>>>(A, rcp2);
   for (int64_t k = 0; k < n; ++k) {
-    ::tobk::note_launch(), k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k);
+    ::tobk::note_launch(), k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k, rcp2);
     std::swap(src, dst);
   }
   return src;
@@ -1066,24 +1090,27 @@ void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, in
 
 // Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j]; one thread per row index, up to 32 outputs per
 // pass over blockIdx.y tiles of columns.
+// Each thread owns one row index k and kCombineJ consecutive output columns, so that the grid has
+// enough blocks to cover the SMs even for the short vectors of the coarse eigen level.
+constexpr int kCombineJ = 4;
 __global__ void k_combine(const double* __restrict__ X, int nx, const double* __restrict__ C, int ldc, int ny,
                           double alpha, double beta, double* __restrict__ Y, int64_t n, int64_t stride) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = blockIdx.y * 32;
-  const int nj = min(32, ny - j0);
+  const int j0 = blockIdx.y * kCombineJ;
+  const int nj = min(kCombineJ, ny - j0);
   if (k >= n) return;
-  double acc[32];
+  double acc[kCombineJ];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kCombineJ; ++j) acc[j] = 0.0;
   for (int i = 0; i < nx; ++i) {
-    const double xi = X[(int64_t)i * stride + k];
+    const double xi = __ldg(X + (int64_t)i * stride + k);
     const double* ci = C + (size_t)i * ldc + j0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < nj) acc[j] += xi * ci[j];
+    for (int j = 0; j < kCombineJ; ++j)
+      if (j < nj) acc[j] += xi * __ldg(ci + j);
   }
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
+  for (int j = 0; j < kCombineJ; ++j) {
     if (j < nj) {
       double* y = Y + (int64_t)(j0 + j) * stride + k;
       *y = (beta == 0.0 ? 0.0 : beta * *y) + alpha * acc[j];
@@ -1093,7 +1120,7 @@ __global__ void k_combine(const double* __restrict__ X, int nx, const double* __
 
 void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta, double* Y,
                     int64_t n, int64_t stride, cudaStream_t s) {
-  dim3 grid(blocks_for(n), (ny + 31) / 32);
+  dim3 grid(blocks_for(n), (ny + kCombineJ - 1) / kCombineJ);
   ::tobk::note_launch(), k_combine<<<grid, kThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n, stride);
 }
 

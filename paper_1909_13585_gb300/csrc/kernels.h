@@ -41,20 +41,31 @@ void launch_stencil_assemble(const Grid& g, const double* Ke, const uint8_t* fix
 
 enum ApplyMode { APPLY_KV = 0, APPLY_RES = 1, APPLY_JAC = 2 };
 
+// One smoothing step (APPLY_JAC): r = dinv (b - K v); dn = coef[0] d_in + coef[1] r; y = v + dn;
+// d_out = dn.  d_in == nullptr means a zero previous increment; coef is a device pointer (so that
+// captured graphs stay valid when the coefficients change).  Damped Jacobi: coef = (0, omega);
+// Chebyshev: the per-step recurrence coefficients.
+template <typename T>
+struct SmoothArgs {
+  const T* coef = nullptr;
+  const T* d_in = nullptr;
+  T* d_out = nullptr;
+};
+
 // y = K v | y = b - K v | y = v + omega dinv (b - K v), for nr RHS (double or float vectors).
 void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double* b, const double* dinv,
-                  double* y, double omega, int nr, int64_t stride, cudaStream_t s);
+                  double* y, SmoothArgs<double> sm, int nr, int64_t stride, cudaStream_t s);
 void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
-                    float* y, float omega, int nr, int64_t stride, cudaStream_t s);
+                    float* y, SmoothArgs<float> sm, int nr, int64_t stride, cudaStream_t s);
 // y = G v with G_e = Gs_e (x) I (Gs includes E_sigma), fine level.
 void launch_apply_kron(const Grid& g, const uint8_t* fixed, const double* Gs, const double* v, double* y,
                        int nr, int64_t stride, cudaStream_t s);
 // dinv = 1/diag(K) (0 at fixed DOFs); also a float copy when dinv32 != nullptr.
 void launch_diag(const LevelOpDesc& op, double* dinv, float* dinv32, cudaStream_t s);
 // z = omega dinv b (first damped-Jacobi sweep from a zero guess)
-void launch_jacobi0(const double* b, const double* dinv, double* z, double omega, int64_t n, int nr,
+void launch_jacobi0(const double* b, const double* dinv, double* z, SmoothArgs<double> sm, int64_t n, int nr,
                     int64_t stride, cudaStream_t s);
-void launch_jacobi0_32(const float* b, const float* dinv, float* z, float omega, int64_t n, int nr,
+void launch_jacobi0_32(const float* b, const float* dinv, float* z, SmoothArgs<float> sm, int64_t n, int nr,
                        int64_t stride, cudaStream_t s);
 // coarse b = P^T r_fine (masked); fine z += P z_coarse (masked)
 void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc,
@@ -74,7 +85,7 @@ void launch_dense_gemv32(const double* Ainv, const float* b, float* z, int64_t n
 // Gauss-Jordan inversion (SPD, no pivoting) ping-ponging between A and work.
 void launch_dense_assemble(const LevelOpDesc& op, double* A, cudaStream_t s);
 // returns the buffer holding the inverse (A or work)
-double* launch_dense_invert(double* A, double* work, int64_t n, cudaStream_t s);
+double* launch_dense_invert(double* A, double* work, int64_t n, double* rcp2, cudaStream_t s);
 
 // Galerkin coarse element matrices.  child source: fine K (scale * table), fine G (Es * Gs0 (x) I),
 // or stored matrices of the previous level.  Rows/cols of fixed fine DOFs are masked.

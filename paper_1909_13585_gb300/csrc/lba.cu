@@ -408,10 +408,20 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
       ::tobk::note_launch(), k_adjoint_gather<3><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
     }
   }
-  // adjoint systems K z_i = b_i: one multi-RHS mgPCG solve
+  // adjoint systems K z_i = b_i: one multi-RHS mgPCG solve (optionally with the load as an extra
+  // column, K [u, Z] = [f, B], the new u replacing the stored one)
   tobk_solve_info si{};
-  int rc = pcg_solve(h, 0, h->adj_rhs, h->adj, q, h->desc.rtol, h->desc.max_iter, false, h->desc.precision, &si);
-  if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+  int rc;
+  if (h->desc.fuse_load_adjoint) {
+    launch_mask_copy(h->f, h->lv[0].fixed, h->adj_blockB, n, 1, n, st);
+    rc = pcg_solve(h, 0, h->adj_blockB, h->adj_blockX, q + 1, h->desc.rtol, h->desc.max_iter, false,
+                   h->desc.precision, &si);
+    if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+    cudaMemcpyAsync(h->u, h->adj_blockX, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  } else {
+    rc = pcg_solve(h, 0, h->adj_rhs, h->adj, q, h->desc.rtol, h->desc.max_iter, false, h->desc.precision, &si);
+    if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+  }
   // phi_i^T G phi_i
   double* GP = h->lv[0].z;
   apply_G_level(h, 0, h->modes, GP, q, n);

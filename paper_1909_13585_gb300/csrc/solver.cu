@@ -161,6 +161,17 @@ static void layout(tobk_handle* h, Arena& a) {
     if (j > 0 && j <= h->eig) L.Ge = a.take<double>(m * nd * nd);
     L.dinv = a.take<double>(n);
     if (mixed) L.dinv32 = a.take<float>(n);
+    L.coef = a.take<double>(2 * kMaxSmoothSteps + 1);
+    if (mixed) L.coef32 = a.take<float>(2 * kMaxSmoothSteps);
+    if (h->desc.smoother == TOBK_SMOOTHER_CHEBYSHEV && j + 1 < h->L) {
+      if (mixed) {
+        L.dA32 = a.take<float>(rm * n);
+        L.dB32 = a.take<float>(rm * n);
+      } else {
+        L.dA = a.take<double>(rm * n);
+        L.dB = a.take<double>(rm * n);
+      }
+    }
     L.b = a.take<double>(rm * n);
     L.z = a.take<double>(rm * n);
     L.t = a.take<double>(rm * n);
@@ -207,8 +218,12 @@ static void layout(tobk_handle* h, Arena& a) {
   const int q = h->q;
   h->modes = a.take<double>((size_t)q * nf);
   h->lam = a.take<double>(q);
-  h->adj = a.take<double>((size_t)q * nf);
-  h->adj_rhs = a.take<double>((size_t)q * nf);
+  // [load | q adjoint right-hand sides] and [u | q adjoint solutions], so that the fused solve
+  // K [u, Z] = [f, B] is one contiguous (q+1)-RHS block
+  h->adj_blockB = a.take<double>((size_t)(q + 1) * nf);
+  h->adj_blockX = a.take<double>((size_t)(q + 1) * nf);
+  h->adj_rhs = h->adj_blockB + nf;
+  h->adj = h->adj_blockX + nf;
   h->dlam = a.take<double>((size_t)q * g.m);
   h->dJ = a.take<double>(g.m);
   h->esens = a.take<double>((size_t)g.m * h->tab.ngp * h->tab.nv);
@@ -240,6 +255,9 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
   if (d->eig_level < 1 || d->eig_level > d->mg_levels) return TOBK_E_ARG;
   if (d->num_modes < 1 || d->num_modes > 24) return TOBK_E_ARG;
   if (d->nu_pre < 1 || d->nu_post < 0 || !(d->omega > 0.0) || !(d->rtol > 0.0) || d->max_iter < 1) return TOBK_E_ARG;
+  if (d->nu_pre > kMaxSmoothSteps || d->nu_post > kMaxSmoothSteps) return TOBK_E_ARG;
+  if (d->smoother != TOBK_SMOOTHER_JACOBI && d->smoother != TOBK_SMOOTHER_CHEBYSHEV) return TOBK_E_ARG;
+  if (d->smoother == TOBK_SMOOTHER_CHEBYSHEV && !(d->cheb_ratio > 1.0)) return TOBK_E_ARG;
   if (!(d->nu > -1.0 && d->nu < 0.5) || !(d->E0 > 0.0) || !(d->Emin > 0.0) || !(d->penal >= 1.0)) return TOBK_E_ARG;
   if (d->precision != TOBK_FP64 && d->precision != TOBK_FP32_VCYCLE) return TOBK_E_ARG;
   for (int a = 0; a < d->dim; ++a) {
@@ -434,7 +452,8 @@ int setup_hierarchy(tobk_handle* h) {
   }
   const int jc = h->L - 1;
   launch_dense_assemble(level_op(h, jc), h->Adense, s);
-  h->Ainv = launch_dense_invert(h->Adense, h->Awork, h->lv[jc].g.n, s);
+  h->Ainv = launch_dense_invert(h->Adense, h->Awork, h->lv[jc].g.n, h->dscal + 1000, s);
+  setup_smoothers(h);
   int rc = check_cuda(h, "setup_hierarchy");
   if (rc) return rc;
   h->setup_done = true;
@@ -488,7 +507,6 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
   cudaStream_t s = h->stream;
   Level& L = h->lv[j];
   const int64_t n = L.g.n;
-  const double om = h->desc.omega;
   const int ks = j == 0 ? TOBK_KC_FINE_SMOOTH : TOBK_KC_COARSE;
   const int kr = j == 0 ? TOBK_KC_FINE_RESIDUAL : TOBK_KC_COARSE;
   if (j == h->L - 1) {
@@ -498,17 +516,21 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
     return z;
   }
   const LevelOpDesc op = level_op(h, j);
+  // smoothing steps: Chebyshev keeps its increment in dA/dB; damped Jacobi needs none
+  double* dA = L.dA;
+  double* dB = L.dB;
   prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
-  launch_jacobi0(b, L.dinv, z, om, n, nr, n, s);
+  launch_jacobi0(b, L.dinv, z, SmoothArgs<double>{L.coef, nullptr, dA}, n, nr, n, s);
   prof_end(h);
   for (int it = 1; it < h->desc.nu_pre; ++it) {
     prof_begin(h, ks, (double)nr * n);
-    launch_apply(op, APPLY_JAC, z, b, L.dinv, t, om, nr, n, s);
+    launch_apply(op, APPLY_JAC, z, b, L.dinv, t, SmoothArgs<double>{L.coef + 2 * it, dA, dB}, nr, n, s);
     prof_end(h);
     std::swap(z, t);
+    std::swap(dA, dB);
   }
   prof_begin(h, kr, (double)nr * n);
-  launch_apply(op, APPLY_RES, z, b, nullptr, L.r, 0.0, nr, n, s);
+  launch_apply(op, APPLY_RES, z, b, nullptr, L.r, SmoothArgs<double>{}, nr, n, s);
   prof_end(h);
   Level& C = h->lv[j + 1];
   prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
@@ -520,9 +542,11 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
   prof_end(h);
   for (int it = 0; it < h->desc.nu_post; ++it) {
     prof_begin(h, ks, (double)nr * n);
-    launch_apply(op, APPLY_JAC, z, b, L.dinv, t, om, nr, n, s);
+    launch_apply(op, APPLY_JAC, z, b, L.dinv, t, SmoothArgs<double>{L.coef + 2 * it, it == 0 ? nullptr : dA, dB},
+                 nr, n, s);
     prof_end(h);
     std::swap(z, t);
+    std::swap(dA, dB);
   }
   return z;
 }
@@ -531,7 +555,6 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
   cudaStream_t s = h->stream;
   Level& L = h->lv[j];
   const int64_t n = L.g.n;
-  const float om = (float)h->desc.omega;
   const int ks = j == 0 ? TOBK_KC_FINE_SMOOTH : TOBK_KC_COARSE;
   const int kr = j == 0 ? TOBK_KC_FINE_RESIDUAL : TOBK_KC_COARSE;
   if (j == h->L - 1) {
@@ -541,17 +564,20 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
     return z;
   }
   const LevelOpDesc op = level_op(h, j);
+  float* dA = L.dA32;
+  float* dB = L.dB32;
   prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
-  launch_jacobi0_32(b, L.dinv32, z, om, n, nr, n, s);
+  launch_jacobi0_32(b, L.dinv32, z, SmoothArgs<float>{L.coef32, nullptr, dA}, n, nr, n, s);
   prof_end(h);
   for (int it = 1; it < h->desc.nu_pre; ++it) {
     prof_begin(h, ks, (double)nr * n);
-    launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, om, nr, n, s);
+    launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, SmoothArgs<float>{L.coef32 + 2 * it, dA, dB}, nr, n, s);
     prof_end(h);
     std::swap(z, t);
+    std::swap(dA, dB);
   }
   prof_begin(h, kr, (double)nr * n);
-  launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, 0.0f, nr, n, s);
+  launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, SmoothArgs<float>{}, nr, n, s);
   prof_end(h);
   Level& C = h->lv[j + 1];
   prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
@@ -563,9 +589,11 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
   prof_end(h);
   for (int it = 0; it < h->desc.nu_post; ++it) {
     prof_begin(h, ks, (double)nr * n);
-    launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, om, nr, n, s);
+    launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t,
+                   SmoothArgs<float>{L.coef32 + 2 * it, it == 0 ? nullptr : dA, dB}, nr, n, s);
     prof_end(h);
     std::swap(z, t);
+    std::swap(dA, dB);
   }
   return z;
 }
@@ -732,7 +760,7 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
 }
 
 void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride) {
-  launch_apply(level_op(h, j), APPLY_KV, v, nullptr, nullptr, y, 0.0, nr, stride, h->stream);
+  launch_apply(level_op(h, j), APPLY_KV, v, nullptr, nullptr, y, SmoothArgs<double>{}, nr, stride, h->stream);
 }
 
 void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride) {
@@ -744,7 +772,7 @@ void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, in
     d.fixed = h->lv[j].fixed;
     d.stored = true;
     d.Ke64 = h->lv[j].Ge;
-    launch_apply(d, APPLY_KV, v, nullptr, nullptr, y, 0.0, nr, stride, h->stream);
+    launch_apply(d, APPLY_KV, v, nullptr, nullptr, y, SmoothArgs<double>{}, nr, stride, h->stream);
   }
 }
 

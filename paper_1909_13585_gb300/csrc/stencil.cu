@@ -65,7 +65,7 @@ void launch_stencil_assemble(const Grid& g, const double* Ke, const uint8_t* fix
 template <int DIM, typename T, int MODE, int R>
 __global__ void __launch_bounds__(256) k_apply_stencil(Grid g, const T* __restrict__ S, const uint8_t* __restrict__ fixed,
                                                        const T* __restrict__ v, const T* __restrict__ b,
-                                                       const T* __restrict__ dinv, T* __restrict__ y, T omega,
+                                                       const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
                                                        int nr, int64_t stride, const double* __restrict__ act) {
   constexpr int NB = StencilDims<DIM>::NB;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,7 +121,12 @@ __global__ void __launch_bounds__(256) k_apply_stencil(Grid g, const T* __restri
       else if (MODE == APPLY_RES)
         out = b[off + idx] - acc[r][c];
       else
-        out = v[off + idx] + omega * dinv[idx] * (b[off + idx] - acc[r][c]);
+      {
+        const T rr = dinv[idx] * (b[off + idx] - acc[r][c]);
+        const T dn = (sm.d_in ? sm.coef[0] * sm.d_in[off + idx] : T(0)) + sm.coef[1] * rr;
+        if (sm.d_out) sm.d_out[off + idx] = dn;
+        out = v[off + idx] + dn;
+      }
       y[off + idx] = out;
     }
   }
@@ -129,31 +134,32 @@ __global__ void __launch_bounds__(256) k_apply_stencil(Grid g, const T* __restri
 
 template <int DIM, typename T, int R>
 static void stencil_dispatch(const Grid& g, const T* S, const uint8_t* fixed, int mode, const T* v, const T* b,
-                             const T* dinv, T* y, T omega, int nr, int64_t stride, cudaStream_t s) {
+                             const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
   dim3 grid((unsigned)((g.nnode + 255) / 256), (unsigned)((nr + R - 1) / R));
   const double* act = active_rhs();
   note_launch();
   if (mode == APPLY_KV)
-    k_apply_stencil<DIM, T, APPLY_KV, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, omega, nr, stride, act);
+    k_apply_stencil<DIM, T, APPLY_KV, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
   else if (mode == APPLY_RES)
-    k_apply_stencil<DIM, T, APPLY_RES, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, omega, nr, stride, act);
+    k_apply_stencil<DIM, T, APPLY_RES, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
   else
-    k_apply_stencil<DIM, T, APPLY_JAC, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, omega, nr, stride, act);
+    k_apply_stencil<DIM, T, APPLY_JAC, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
 }
 
 template <typename T>
 void launch_apply_stencil(const Grid& g, const T* S, const uint8_t* fixed, int mode, const T* v, const T* b,
-                          const T* dinv, T* y, T omega, int nr, int64_t stride, cudaStream_t s) {
+                          const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
   if (g.dim == 2)
-    stencil_dispatch<2, T, 4>(g, S, fixed, mode, v, b, dinv, y, omega, nr, stride, s);
+    stencil_dispatch<2, T, 4>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
   else
-    stencil_dispatch<3, T, 2>(g, S, fixed, mode, v, b, dinv, y, omega, nr, stride, s);
+    stencil_dispatch<3, T, 2>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
 }
 
 template void launch_apply_stencil<double>(const Grid&, const double*, const uint8_t*, int, const double*,
-                                           const double*, const double*, double*, double, int, int64_t,
+                                           const double*, const double*, double*, SmoothArgs<double>, int, int64_t,
                                            cudaStream_t);
 template void launch_apply_stencil<float>(const Grid&, const float*, const uint8_t*, int, const float*, const float*,
-                                          const float*, float*, float, int, int64_t, cudaStream_t);
+                                          const float*, float*, SmoothArgs<float>, int, int64_t,
+                                          cudaStream_t);
 
 }  // namespace tobk

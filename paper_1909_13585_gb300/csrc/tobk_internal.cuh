@@ -23,6 +23,7 @@ constexpr int kMaxLevels = 12;
 constexpr int kMaxRhs = 64;      // RHS per multi-RHS solve (per-kernel reduction counters)
 constexpr int kNumCounterSets = 6;
 constexpr int kScStride = 16;  // doubles of per-RHS scalar state in the CG driver
+constexpr int kMaxSmoothSteps = 8;  // smoothing steps per pre-/post-smoothing phase
 
 // per-RHS CG scalar slots
 enum ScSlot {
@@ -105,6 +106,12 @@ struct Level {
   float* S32 = nullptr;
   double* dinv = nullptr;     // [n] inverse diagonal (0 at fixed DOFs)
   float* dinv32 = nullptr;
+  // smoother: per-step coefficients [2 * kMaxSmoothSteps] (+ lambda_max estimate at the end) and
+  // the Chebyshev increment vectors (ping-pong, [rmax][n])
+  double* coef = nullptr;
+  float* coef32 = nullptr;
+  double *dA = nullptr, *dB = nullptr;
+  float *dA32 = nullptr, *dB32 = nullptr;
   // V-cycle work vectors, capacity rmax RHS: b, z, t (ping-pong), r
   double *b = nullptr, *z = nullptr, *t = nullptr, *r = nullptr;
   float *b32 = nullptr, *z32 = nullptr, *t32 = nullptr, *r32 = nullptr;

@@ -201,8 +201,8 @@ def config(name: str) -> Problem:
                         fine-grid eigenproblem, 6 modes.
     column480x160       2D Q4, 480 x 160, seed 1, radius 4, volfrac 0.5, 5 MG levels, eigenproblem
                         on level 3 (120 x 40), 12 modes.
-    cantilever96x48x48  3D H8, 96 x 48 x 48, seed 2, radius 3, volfrac 0.3, 4 MG levels, eigenproblem
-                        on level 3 (24 x 12 x 12), 12 modes.
+    cantilever96x48x48  3D H8, 96 x 48 x 48, seed 2, radius 3, volfrac 0.3, 5 MG levels (coarsest
+                        6 x 3 x 3), eigenproblem on level 3 (24 x 12 x 12), 12 modes.
     cantilever128x64x64 3D H8, 128 x 64 x 64, seed 3, radius 3, volfrac 0.3, 5 MG levels.
     """
     if name == "column60x20":
@@ -212,7 +212,7 @@ def config(name: str) -> Problem:
         return column_2d(480, 160, seed=1, radius=4, volfrac=0.5, name=name, mg_levels=5,
                          eig_level=3, num_modes=12)
     if name == "cantilever96x48x48":
-        return cantilever_3d(96, 48, 48, seed=2, radius=3, volfrac=0.3, name=name, mg_levels=4,
+        return cantilever_3d(96, 48, 48, seed=2, radius=3, volfrac=0.3, name=name, mg_levels=5,
                              eig_level=3, num_modes=12)
     if name == "cantilever128x64x64":
         return cantilever_3d(128, 64, 64, seed=3, radius=3, volfrac=0.3, name=name, mg_levels=5,

@@ -130,3 +130,33 @@ def test_sensitivities_exact_path_against_oracle_pairs():
     for i in range(p.num_modes):
         if g[i] > 1e-4:
             assert rel_err(dlam[i], dlam_o[i]) < 1e-5, i
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_vcycle_and_fused_load_adjoint_pipeline(dim):
+    """The mixed-precision form (FP32 V-cycle inside FP64 flexible CG) with the load re-solved in the
+    adjoint block: same tolerances against the FP64 oracle."""
+    torch, pkg = require_gpu()
+    if dim == 2:
+        p = synthetic.column_2d(96, 32, seed=27, radius=3, mg_levels=4, eig_level=3, num_modes=6)
+    else:
+        p = synthetic.cantilever_3d(16, 8, 8, seed=26, radius=2, volfrac=0.3, mg_levels=3, eig_level=2,
+                                    num_modes=4)
+    s = pkg.Solver(p, precision=pkg.TOBK_FP32_VCYCLE, fuse_load_adjoint=1)
+    J, info = s.solve_equilibrium()
+    lam, _ = s.compute_buckling()
+    Phi = s.get_field(pkg.TOBK_FIELD_MODES).reshape(p.num_modes, -1).T
+    dlam, dJ, _ = s.compute_sensitivities()
+    u = s.get_field(pkg.TOBK_FIELD_U)
+    op = lba.Problem(p)
+    res = np.linalg.norm(p.f[op.free] - op.Kf @ u[op.free]) / np.linalg.norm(p.f[op.free])
+    assert res <= 1e-8
+    uo, Jo = lba.linear_analysis(op)
+    assert J == pytest.approx(Jo, rel=1e-7)
+    ml = lba.multilevel_lba(op, uo, p.num_modes, p.eig_level)
+    if np.all(_gaps(ml["lam_coarse"]) > 1e-4):
+        assert np.allclose(lam, ml["lam"], rtol=1e-6), (lam, ml["lam"])
+    dlam_o, dJ_o, _ = sensitivity.sensitivities(op, u, lam, Phi)
+    assert rel_err(dJ, dJ_o) < 1e-6
+    for i in range(p.num_modes):
+        assert rel_err(dlam[i], dlam_o[i]) < 1e-5, i
