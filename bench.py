@@ -102,6 +102,63 @@ def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush):
             "fused_load_adjoint": bool(fused), "steps": steps, "warmup": warmup, **info}
 
 
+def batch_rhs(pkg, torch, problems, nadj, dev, stream):
+    """Right-hand sides of the batch: per design the load and nadj adjoint right-hand sides of a
+    preceding buckling analysis of the same design (multilevel, eigenproblem on the second-coarsest
+    level), packed [design][1 + nadj][n_d] on the device."""
+    blocks = []
+    for p in problems:
+        q = synthetic.column_2d(p.nel[1], p.nel[0], seed=p.meta["seed"], radius=p.meta["radius"],
+                                volfrac=p.meta["volfrac"], mg_levels=p.mg_levels,
+                                eig_level=max(2, p.mg_levels - 1), num_modes=nadj, x=p.x)
+        s = pkg.Solver(q, stream=stream, precision=pkg.TOBK_FP32_VCYCLE)
+        s.solve_equilibrium()
+        s.compute_buckling()
+        s.compute_sensitivities()
+        B = np.zeros((1 + nadj, p.num_dofs))
+        B[0] = p.f
+        B[1:] = s.get_field(pkg.TOBK_FIELD_ADJOINT_RHS).reshape(nadj, p.num_dofs)
+        blocks.append(B.reshape(-1))
+        s.close()
+    return torch.from_numpy(np.concatenate(blocks)).to(dev)
+
+
+def measure_batch(pkg, torch, steps, warmup, dev, flush, count=64, nadj=6):
+    """Batched form: `count` uneven 2D designs, each with the load and `nadj` adjoint RHS, solved
+    together (grouped launches, captured graphs, autotuned tiles, FP32 V-cycle, FP64 outer CG).
+    One step = set every design's densities (hierarchy set-up) + the batched solve."""
+    problems = synthetic.batch_configs(count)
+    stream = torch.cuda.Stream(device=dev)
+    B = batch_rhs(pkg, torch, problems, nadj, dev, stream)
+    bt = pkg.Batch(problems, 1 + nadj, stream=stream)
+    x = torch.from_numpy(np.concatenate([p.x for p in problems])).to(dev)
+    fixed = torch.from_numpy(np.concatenate([p.fixed for p in problems]).astype(np.uint8)).to(dev)
+    X = torch.zeros_like(B)
+    bt.set_designs(x, fixed)
+    variants = bt.autotune()
+    infos = None
+    for _ in range(warmup):
+        bt.set_designs(x, fixed)
+        infos, _ = bt.solve(B, X)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        evs[k][0].record(stream)
+        bt.set_designs(x, fixed)
+        infos, _ = bt.solve(B, X)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    dofs = int(sum(p.num_dofs for p in problems))
+    units = dofs * (1 + nadj)
+    bt.close()
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "designs": count, "dofs_total": dofs,
+            "rhs_per_design": 1 + nadj, "precision": "fp32_vcycle", "autotuned_variants": list(variants),
+            "iterations_max": max(i["iterations"] for i in infos),
+            "rel_residual_max": max(i["rel_residual"] for i in infos), "steps": steps, "warmup": warmup}
+
+
 # ------------------------------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ------------------------------------------------------------------------------------------------
@@ -403,6 +460,7 @@ def ours(args):
                                                           fs, fw, dev, flush)
         forms["cantilever96x48x48_fp32_vcycle_fused"] = measure_form(pkg, torch, "cantilever96x48x48",
                                                                      pkg.TOBK_FP32_VCYCLE, True, fs, fw, dev, flush)
+        forms["batch64_column2d_fp32_vcycle"] = measure_batch(pkg, torch, fs, fw, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

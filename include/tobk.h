@@ -206,6 +206,40 @@ int tobk_solve(tobk_handle* h, int level, const double* B, double* X, int nrhs, 
  * [m_level][nd*nd] (device pointer), nd = dim * 2^dim. */
 int tobk_get_element_matrices(tobk_handle* h, int level, int which, double* out, int64_t len);
 
+/* ---- many designs solved together ------------------------------------------------------------
+ * A batch holds nd independent 2D designs (each its own grid, densities, Dirichlet set and multigrid
+ * hierarchy) that share one CUDA stream and are solved together: K_d X_d = B_d with nrhs right-hand
+ * sides per design (e.g. the load and the q adjoint systems of eq. AdjointSystem), by flexible CG in
+ * FP64 preconditioned with an FP32 V-cycle (the TOBK_FP32_VCYCLE form of the mgPCG of Appendix A).
+ * Every phase of the iteration is one launch over all designs (grouped work lists, persistent-style
+ * grid stride), two CG iterations are replayed from a captured CUDA graph, and the smoother tile
+ * shapes are chosen by tobk_batch_autotune.
+ *
+ * Packed layouts: design d owns elements [elem_off[d], elem_off[d+1]) of the packed densities and
+ * DOFs [dof_off[d], dof_off[d+1]) of the packed Dirichlet mask; the packed right-hand sides and
+ * solutions put design d's block [nrhs][n_d] at offset nrhs * dof_off[d].
+ * Limits: dim = 2; 2 <= mg_levels <= 8; all designs share nu, nu_pre, nu_post and the smoother;
+ * rtol and max_iter of descs[0] apply to every design; 1 <= nrhs <= 64.  Errors as for the
+ * single-design calls; tobk_batch_last_error() gives the message. */
+typedef struct tobk_batch tobk_batch;
+int tobk_batch_create(const tobk_desc* descs, int ndesigns, int nrhs, void* cuda_stream, tobk_batch** out);
+void tobk_batch_destroy(tobk_batch* b);
+const char* tobk_batch_last_error(const tobk_batch* b);
+/* dof_offsets, elem_offsets: [ndesigns + 1] (either may be NULL). */
+int tobk_batch_layout(const tobk_batch* b, int64_t* dof_offsets, int64_t* elem_offsets);
+/* Packed densities x and Dirichlet masks (host or device); builds every design's hierarchy. */
+int tobk_batch_set_designs(tobk_batch* b, const double* x, const uint8_t* fixed, int on_device);
+/* Solves every design's K_d X_d = B_d to rtol (B, X packed, host or device).  infos: [ndesigns]
+ * (may be NULL), per design: CG iterations (max over its RHS), converged, the worst true relative
+ * residual at exit, the device time of the whole batch call. */
+int tobk_batch_solve(tobk_batch* b, const double* B, double* X, int on_device, tobk_solve_info* infos);
+/* Times the candidate variants of the grouped smoother kernels on the current designs and keeps
+ * the fastest: fine FP32 smoother node tiles 0: 32x8, 1: 32x4, 2: 64x4, 3: 16x16; coarse stencil
+ * kernel 0/1/2: 1/2/4 right-hand sides per thread.  Outputs the choices (either may be NULL). */
+int tobk_batch_autotune(tobk_batch* b, int* fine_variant, int* coarse_variant);
+/* Sets the variants explicitly (same numbering). */
+int tobk_batch_set_variants(tobk_batch* b, int fine_variant, int coarse_variant);
+
 /* ---- allocation-free residual check ------------------------------------------------------------
  * Not part of the paper's method (it has no counterpart there): a utility for callers that must not
  * allocate device memory when they verify a solution, e.g. code running while a stream is being

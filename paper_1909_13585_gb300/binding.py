@@ -57,6 +57,14 @@ _SIGS = {
     "tobk_solve": (C.c_int, [_H, C.c_int, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
     "tobk_get_element_matrices": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int64]),
     "tobk_residual_noalloc": (C.c_int, [C.POINTER(tobk_desc), _P, _P, _P, _P, C.c_int, _P, C.c_void_p]),
+    "tobk_batch_create": (C.c_int, [C.POINTER(tobk_desc), C.c_int, C.c_int, C.c_void_p, C.POINTER(_H)]),
+    "tobk_batch_destroy": (None, [_H]),
+    "tobk_batch_last_error": (C.c_char_p, [_H]),
+    "tobk_batch_layout": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "tobk_batch_set_designs": (C.c_int, [_H, _P, _P, C.c_int]),
+    "tobk_batch_solve": (C.c_int, [_H, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
+    "tobk_batch_autotune": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "tobk_batch_set_variants": (C.c_int, [_H, C.c_int, C.c_int]),
     "tobk_launch_count": (C.c_longlong, []),
     "tobk_profile_enable": (C.c_int, [_H, C.c_int]),
     "tobk_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
@@ -257,3 +265,81 @@ class Solver:
     def element_matrices(self, level, which, out):
         self._check(self.lib.tobk_get_element_matrices(self.h, level, which, out.data_ptr(), out.numel()))
         return out
+
+
+def problem_desc(lib, problem, **overrides):
+    """A tobk_desc for a problem object (synthetic.Problem-like), defaults from tobk_default_desc."""
+    d = tobk_desc()
+    lib.tobk_default_desc(C.byref(d))
+    d.dim = problem.dim
+    d.nel[0], d.nel[1] = problem.nel[0], problem.nel[1]
+    d.nel[2] = problem.nel[2] if problem.dim == 3 else 1
+    d.nu, d.E0, d.Emin, d.penal = problem.nu, problem.E0, problem.Emin, problem.penal
+    d.mg_levels, d.eig_level, d.num_modes = problem.mg_levels, problem.eig_level, problem.num_modes
+    for k, v in overrides.items():
+        setattr(d, k, v)
+    return d
+
+
+class Batch:
+    """Owner of a tobk_batch: many independent 2D designs solved together (tobk_batch_* calls).
+    Packed arrays follow `layout()`; arrays may be numpy (host) or torch tensors (host or device)."""
+
+    def __init__(self, problems, nrhs, *, stream=None, **overrides):
+        self.lib = load()
+        n = len(problems)
+        descs = (tobk_desc * n)()
+        for i, p in enumerate(problems):
+            descs[i] = problem_desc(self.lib, p, **overrides)
+        h = _H()
+        s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = self.lib.tobk_batch_create(descs, n, nrhs, C.c_void_p(s), C.byref(h))
+        if rc != TOBK_OK:
+            raise TobkError(rc, "tobk_batch_create failed")
+        self.h = h
+        self.nd = n
+        self.nrhs = nrhs
+        dof = (C.c_int64 * (n + 1))()
+        elem = (C.c_int64 * (n + 1))()
+        self.lib.tobk_batch_layout(self.h, dof, elem)
+        self.dof_offsets = np.array(dof[:], dtype=np.int64)
+        self.elem_offsets = np.array(elem[:], dtype=np.int64)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tobk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != TOBK_OK and rc not in allow:
+            raise TobkError(rc, self.lib.tobk_batch_last_error(self.h).decode())
+        return rc
+
+    def set_designs(self, x, fixed):
+        px, dx = _ptr(x)
+        pf, df = _ptr(fixed)
+        assert dx == df
+        self._check(self.lib.tobk_batch_set_designs(self.h, px, pf, dx))
+
+    def solve(self, B, X, allow_not_converged=False):
+        pb, db = _ptr(B)
+        px, dx = _ptr(X)
+        assert db == dx
+        infos = (tobk_solve_info * self.nd)()
+        rc = self._check(self.lib.tobk_batch_solve(self.h, pb, px, db, infos),
+                         (TOBK_E_NOT_CONVERGED,) if allow_not_converged else ())
+        return [i.as_dict() for i in infos], rc
+
+    def autotune(self):
+        f, c = C.c_int(), C.c_int()
+        self._check(self.lib.tobk_batch_autotune(self.h, C.byref(f), C.byref(c)))
+        return f.value, c.value
+
+    def set_variants(self, fine, coarse):
+        self._check(self.lib.tobk_batch_set_variants(self.h, fine, coarse))

@@ -191,18 +191,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* >= 32
 }
 
 // Writes this block's partials, and returns true in the block that arrives last; that block then
-// holds the grid totals in tot[] (valid in thread 0).  partial: [gridDim.x][NV] for this slot.
+// holds the grid totals in tot[] (valid in thread 0).  partial: [nblocks][NV] for this slot; bid is
+// this block's index among the nblocks blocks that reduce into the slot.
 template <int NV>
-__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partial, unsigned* counter,
-                                              double (&tot)[NV], double* smem) {
+__device__ __forceinline__ bool grid_sum_last_idx(double (&v)[NV], double* partial, unsigned* counter,
+                                                  double (&tot)[NV], double* smem, unsigned bid, unsigned nblocks) {
   block_sum<NV>(v, smem);
   __shared__ bool s_last;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) partial[(size_t)blockIdx.x * NV + q] = v[q];
+    for (int q = 0; q < NV; ++q) partial[(size_t)bid * NV + q] = v[q];
     __threadfence();
     const unsigned ticket = atomicAdd(counter, 1u);
-    s_last = (ticket == gridDim.x - 1);
+    s_last = (ticket == nblocks - 1);
   }
   __syncthreads();
   if (!s_last) return false;
@@ -210,7 +211,7 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partial, 
   double w[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) w[q] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+  for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) w[q] += __ldcg(partial + (size_t)b * NV + q);
   }
@@ -221,6 +222,12 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partial, 
     *counter = 0u;
   }
   return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partial, unsigned* counter,
+                                              double (&tot)[NV], double* smem) {
+  return grid_sum_last_idx<NV>(v, partial, counter, tot, smem, blockIdx.x, gridDim.x);
 }
 
 }  // namespace tobk

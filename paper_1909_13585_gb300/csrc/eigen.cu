@@ -42,11 +42,14 @@ __global__ void k_random_block(double* X, int64_t n, int64_t stride, const uint8
   X[(int64_t)c * stride + i] = fixed[i] ? 0.0 : u;
 }
 
-// H[i][col0 + j] = H[col0 + j][i] = sign * C[i][j]  for i < rows, j < cols
+// H[i][col0 + j] = H[col0 + j][i] = sign * C[i][j]  for i < rows, j < cols.  Inside the square block
+// i >= col0 both C[i][j] and C[col0 + j][i - col0] name the same pair; the one with i <= col0 + j is
+// used, so that H is exactly symmetric and every entry has a single writer.
 __global__ void k_scatter_sym(const double* C, int rows, int cols, int col0, double sign, double* H, int ld) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * cols) return;
   const int i = t / cols, j = t % cols;
+  if (i >= col0 && i > col0 + j) return;
   const double v = sign * C[t];
   H[(size_t)i * ld + col0 + j] = v;
   H[(size_t)(col0 + j) * ld + i] = v;
@@ -182,18 +185,14 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   double* Cs = h->Cs;
   double* M = h->Cs + (size_t)mmax * nb;  // nb x nb block Gram
   double* Rinv = M + (size_t)nb * nb;
-  const size_t rr_smem = small_rr_smem_bytes();
-  const size_t tri_smem = small_eig_tridiag_smem_bytes();
   static bool rr_configured = false;
   if (!rr_configured) {
-    cudaFuncSetAttribute(k_small_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem);
-    cudaFuncSetAttribute(k_small_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem);
-    cudaFuncSetAttribute(k_tri_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_reduce_smem_bytes());
-    cudaFuncSetAttribute(k_tri_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_finish_smem_bytes());
+    cudaFuncSetAttribute(k_rr_eig32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_eig32_smem_bytes());
+    cudaFuncSetAttribute(k_rr_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)rr_finish_smem_bytes(kRRMax, kRRMax));
     rr_configured = true;
   }
   const int keep_max = std::min(2 * nb, mmax - nb);
-  const bool use_jacobi = std::getenv("TOBK_EIG_JACOBI") != nullptr;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -203,10 +202,16 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   int nadd = nb, m = 0, it = 0, inner_total = 0;
   bool converged = false;
   double worst = INFINITY;
-  std::vector<double> hth(mmax), hth_prev(mmax, 0.0), hres(q), hkx(q);
-  // The dense Rayleigh-Ritz runs its Jacobi sweeps in FP32 until the wanted Ritz values have
-  // settled to ~1e-6 (their error is quadratic in the residual), then in FP64 for the final digits.
-  bool fp64_mode = std::getenv("TOBK_EIG_FP32_RR") == nullptr;
+  std::vector<double> hth(mmax);
+  // Rayleigh-Ritz scratch: FP32-stage eigenvectors, refined eigenvectors, S, R, wanted columns
+  double* rrX0 = h->tri;
+  double* rrX1 = rrX0 + (size_t)mmax * mmax;
+  double* rrS = rrX1 + (size_t)mmax * mmax;
+  double* rrR = rrS + (size_t)mmax * mmax;
+  double* rrXw = rrR + (size_t)mmax * mmax;
+  double* rrLam = rrXw + (size_t)mmax * mmax;
+  double* rrDelta = rrLam + mmax;
+  int rr_prev = 0;  // size of the previous projected problem whose eigenvectors are in rrX1 (0: none)
   const bool trace = std::getenv("TOBK_EIG_TRACE") != nullptr;
   int rc = TOBK_OK;
   for (it = 0; it < h->desc.eig_max_iter; ++it) {
@@ -244,22 +249,20 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     prof_end(h);
     m = mn;
     // ---- Rayleigh-Ritz (the basis is K-orthonormal, so V^T K V = I): the leading eigenpairs of
-    // the projected matrix in FP64 (Householder + bisection + inverse iteration); the Jacobi
-    // variant (FP32 sweeps, FP64 refinement near convergence and before restarts) is kept as an
-    // alternative.
-    const bool full = !use_jacobi || fp64_mode || (m + nb > mmax);
+    // the projected matrix, FP32 decomposition + two FP64 refinement steps (small_dense.cuh)
+    const int nvec = std::min(m, keep_max);
     prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)m);
-    if (use_jacobi) {
-      ::tobk::note_launch(), k_small_rr<<<1, 512, rr_smem, st>>>(h->Hs, m, mmax, theta, h->Ys, mmax, sinfo + 2,
-                                                                 full ? 1 : 0);
-    } else {
-      const int nvec = std::min(m, keep_max);
-      ::tobk::note_launch(), k_tri_reduce<<<1, 256, tri_reduce_smem_bytes(), st>>>(h->Hs, m, mmax, h->tri, mmax);
-      ::tobk::note_launch(), k_tri_eigvec<<<nvec, 64, 0, st>>>(h->tri, mmax, m);
-      ::tobk::note_launch(), k_tri_finish<<<1, 256, tri_finish_smem_bytes(), st>>>(h->tri, mmax, m, nvec, theta,
-                                                                                   h->Ys, mmax);
-    }
+    // warm start from the previous refined eigenvectors while the basis only grew since then
+    ::tobk::note_launch(), k_rr_eig32<<<1, 1024, rr_eig32_smem_bytes(), st>>>(h->Hs, m, mmax, rrX1, rr_prev, rrX0,
+                                                                              sinfo + 2);
+    ::tobk::note_launch(), k_rr_oa_products<<<m, 64, 0, st>>>(h->Hs, mmax, rrX0, m, rrS, rrR);
+    ::tobk::note_launch(), k_rr_oa_update<<<m, 64, 0, st>>>(rrX0, rrS, rrR, m, rrX1, m, nullptr, rrDelta, 1);
+    ::tobk::note_launch(), k_rr_oa_products<<<m, 64, 0, st>>>(h->Hs, mmax, rrX1, m, rrS, rrR);
+    ::tobk::note_launch(), k_rr_oa_update<<<nvec, 64, 0, st>>>(rrX1, rrS, rrR, m, rrXw, mmax, rrLam, rrDelta, 0);
+    ::tobk::note_launch(), k_rr_finish<<<1, 256, rr_finish_smem_bytes(m, nvec), st>>>(
+        h->Hs, mmax, m, nvec, rrXw, mmax, rrLam, rrDelta, theta, h->Ys, mmax);
     prof_end(h);
+    rr_prev = m;
     const int kk = std::min(nb, m);
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)m * n);
     launch_combine(h->V, m, h->Ys, mmax, kk, 1.0, 0.0, X, n, sd, st);
@@ -274,16 +277,9 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     rc = check_cuda(h, "eigen_solve");
     if (rc) break;
     for (int i = 0; i < kk; ++i) hth[i] = h->hscal[i];
-    if (!fp64_mode && it > 0) {
-      double change = 0.0;
-      for (int i = 0; i < q && i < kk; ++i)
-        change = std::max(change, std::fabs(hth[i] - hth_prev[i]) / std::max(std::fabs(hth[i]), 1e-300));
-      if (change < 1e-6) fp64_mode = true;
-    }
-    for (int i = 0; i < kk; ++i) hth_prev[i] = hth[i];
     if (trace)
-      std::fprintf(stderr, "[tobk eig] level %d it %d m %d nadd %d full %d theta0 %.9e thetaq %.9e sweeps %g/%g\n", j, it,
-                   m, nadd, full ? 1 : 0, hth[0], hth[std::min(q, kk) - 1], h->hscal[386], h->hscal[387]);
+      std::fprintf(stderr, "[tobk eig] level %d it %d m %d nadd %d theta0 %.9e thetaq %.9e fp32 sweeps %g\n", j, it, m,
+                   nadd, hth[0], hth[std::min(q, kk) - 1], h->hscal[386]);
     worst = 0.0;
     std::vector<int> sel;
     for (int i = 0; i < kk; ++i) {
@@ -296,7 +292,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       if (!ok) sel.push_back(i);
     }
     if (trace) std::fprintf(stderr, "[tobk eig]   worst residual %.3e, unconverged %d\n", worst, (int)sel.size());
-    converged = full;
+    converged = true;
     for (int i = 0; i < q; ++i) {
       const double res = std::sqrt(h->hscal[128 + i] / std::max(h->hscal[256 + i], 1e-300));
       if (!(hth[i] > 0.0 && res <= tol)) converged = false;
@@ -335,6 +331,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)keep * keep), 256, 0, st>>>(Cs, keep, keep, 0, -1.0, h->Hs,
                                                                                        mmax);
       m = keep;
+      rr_prev = 0;  // the basis was replaced by Ritz vectors: its projected matrix is diagonal
     }
   }
   if (rc == TOBK_OK) {

@@ -67,6 +67,7 @@ struct tobk_handle {
   };
   std::map<uint64_t, CGGraph> cg_graphs;
   bool use_graphs = true;
+  bool solve_only = false;
 
   // kernel-class timing
   struct ProfPending {
@@ -89,7 +90,9 @@ struct tobk_handle {
 
 namespace tobk {
 
-int create_handle(const tobk_desc* desc, void* stream, tobk_handle** out);
+// solve_only: allocate the multigrid hierarchy and CG work space only (no buckling / sensitivity
+// storage); such a handle serves tobk_solve-style solves, e.g. as one design of a batch.
+int create_handle(const tobk_desc* desc, void* stream, tobk_handle** out, bool solve_only = false);
 void destroy_handle(tobk_handle* h);
 int set_densities(tobk_handle* h, const double* x, bool on_device);
 int set_load(tobk_handle* h, const double* f, bool on_device);

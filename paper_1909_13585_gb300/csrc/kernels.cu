@@ -946,15 +946,15 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(const __grid_constan
   }
 }
 
-int64_t cg_partial_stride(int64_t nnode) {
-  const int64_t a = (nnode + kThreads - 1) / kThreads;
-  return 4 * std::max<int64_t>(a, kVecBlocks);
+int64_t cg_partial_stride(const Grid& g) {
+  const int64_t a = (g.nnode + kThreads - 1) / kThreads;
+  return 4 * std::max<int64_t>(std::max<int64_t>(a, kVecBlocks), g.dim == 2 ? fine_q4_tiles(g) : 0);
 }
 
 template <int DIM, class Op>
 static void cg_init_impl(const Op& op, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
                          int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
-  const int64_t ps = cg_partial_stride(op.g.nnode);
+  const int64_t ps = cg_partial_stride(op.g);
   ::tobk::note_launch(), k_cg_init<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, use_x0 ? 1 : 0, rtol,
                                                                             stride, sc, partial, counters, ps);
 }
@@ -984,13 +984,18 @@ void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q
 template <int DIM, class Op>
 static void cg_dir_impl(const Op& op, const double* z, const double* p_old, double* p_new, double* q, int nr,
                         int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
-  const int64_t ps = cg_partial_stride(op.g.nnode);
+  const int64_t ps = cg_partial_stride(op.g);
   ::tobk::note_launch(), k_cg_direction<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, z, p_old, p_new, q, stride, sc,
                                                                                  partial, counters + 2 * kMaxRhs, ps);
 }
 
 void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_old, double* p_new, double* q,
                          int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  if (d.g.dim == 2 && !d.stored) {
+    launch_fine_q4_cg_direction(d.g, d.scale64, d.fixed, d.T0, z, p_old, p_new, q, nr, stride, sc, partial,
+                                counters + 2 * kMaxRhs, cg_partial_stride(d.g), s);
+    return;
+  }
   if (d.g.dim == 2) {
     if (d.stored)
       cg_dir_impl<2>(make_stored<2, double>(d, d.Ke64), z, p_old, p_new, q, nr, stride, sc, partial, counters, s);
@@ -1014,7 +1019,7 @@ void launch_cg_update(int64_t n, double* x, double* r, const double* p, const do
 template <int DIM, class Op>
 static void true_res_impl(const Op& op, const double* b, const double* x, double* r, int nr, int64_t stride,
                           double* sc, double* partial, unsigned* counters, cudaStream_t s) {
-  const int64_t ps = cg_partial_stride(op.g.nnode);
+  const int64_t ps = cg_partial_stride(op.g);
   ::tobk::note_launch(), k_true_residual<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, stride, sc, partial,
                                                                                   counters + 4 * kMaxRhs, ps);
 }

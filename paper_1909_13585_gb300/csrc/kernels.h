@@ -100,7 +100,15 @@ void launch_galerkin_stored(const Grid& gf, const Grid& gc, const uint8_t* fixed
 // dN [ngp][dim][nn] and D [nv][nv] are device tables.
 void launch_stress_gs_dev(const Grid& g, const double* u, const double* Es, const double* dN, const double* D,
                           double wdet, double* Gs0, double* Gs, cudaStream_t s);
-int64_t cg_partial_stride(int64_t nnode);
+int64_t cg_partial_stride(const Grid& g);
+// Thread blocks of the factored fine Q4 kernels for one RHS (tiles of 32 x 8 nodes).
+int64_t fine_q4_tiles(const Grid& g);
+// CG direction on the fine Q4 level in factored form: p_new = z + beta p_old, q = K p_new,
+// sc[SC_PQ] = p_new . q, sc[SC_ALPHA] (same contract as launch_cg_direction).
+void launch_fine_q4_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, const double* Ke0,
+                                 const double* z, const double* p_old, double* p_new, double* q, int nr,
+                                 int64_t stride, double* sc, double* partial, unsigned* counters, int64_t pstride,
+                                 cudaStream_t s);
 
 // SIMP moduli (paper Sec. 2): Ek = Emin + x^p (E0 - Emin), Es = x^p E0, derivatives.
 void launch_simp(const double* x, int64_t m, double penal, double E0, double Emin, double* Ek, double* Es,

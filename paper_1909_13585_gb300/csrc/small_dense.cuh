@@ -1,677 +1,391 @@
-// Dense Rayleigh-Ritz of the projected buckling pencil in one thread block (included by eigen.cu).
+// Dense Rayleigh-Ritz of the projected buckling pencil (included by eigen.cu).
 //
 // The eigensolver keeps its basis K-orthonormal, so the projected problem is the standard
-// symmetric eigenproblem H y = theta y with H = V^T (-G) V (size m <= 64).  GB300 executes FP64 at
-// 1/64 of its FP32 rate, so the cyclic Jacobi sweeps run in FP32 first (to ~1e-6 relative
-// off-diagonal mass); when full accuracy is requested, the FP32 eigenvectors are refined in FP64:
-// C = V^T H V (nearly diagonal), followed by FP64 Jacobi sweeps, which converge quadratically from
-// there.  Eigenpairs are returned sorted by descending theta.
+// symmetric eigenproblem H y = theta y with H = V^T (-G) V (size m <= kRRMax).  A dense eigensolver
+// is a long chain of dependent steps confined to one SM, and GB300 executes FP64 at 1/64 of its
+// FP32 rate (2 FP64 FMA per clock per SM), so the O(m^3) work of the decomposition is done in FP32
+// and FP64 accuracy is recovered by a refinement made only of matrix products, spread over one
+// thread block per column:
+//   1. k_rr_eig32 (one block): all m eigenvectors of H by cyclic Jacobi sweeps in FP32.
+//   2. two refinement steps in FP64 (Ogita & Aishima, "Iterative refinement for symmetric
+//      eigenvalue decomposition", Japan J. Indust. Appl. Math. 35 (2018)): with X the current
+//      eigenvector matrix, R = I - X^T X, S = X^T H X, lambda_i = s_ii / (1 - r_ii),
+//      E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for i != j, E_ii = r_ii / 2, and
+//      X <- X + X E; each step squares the error.  Pairs closer than the step's error bound delta
+//      get E_ij = r_ij / 2, which refines their common subspace but not its split.
+//   3. k_rr_finish (one block): the wanted columns sorted by lambda; every cluster of wanted
+//      eigenvalues closer than delta is split by FP64 Jacobi rotations of its small block of
+//      X^T H X.
+// Eigenpairs are returned sorted by descending theta.
 #pragma once
 #include <cuda_runtime.h>
 
 namespace tobk {
 
-constexpr int kRRMax = 64;
+constexpr int kRRMax = 64;  // largest projected problem (the FP32 stage pads to it)
 
-// Round-robin pairing of mp (even) indices: round r, pair slot k -> (p, q).
-__device__ __forceinline__ void rr_pair(int mp, int round, int k, int& p, int& q) {
-  if (k == 0) {
-    p = mp - 1;
-    q = round;
-  } else {
-    p = (round + k) % (mp - 1);
-    q = (round - k + (mp - 1)) % (mp - 1);
-  }
-}
-
-// One cyclic Jacobi sweep (all pairs once, m/2 disjoint rotations per round) on C (m x m, row-major)
-// with the rotations accumulated into V.  rc/rs: per-pair cosines and sines (T precision).
-template <typename T>
-__device__ void jacobi_sweep(T* C, T* V, int m, T* rc, T* rs) {
-  const int t = threadIdx.x, nt = blockDim.x;
-  const int mp = (m + 1) & ~1;
-  for (int round = 0; round < mp - 1; ++round) {
-    for (int k = t; k < mp / 2; k += nt) {
-      int p, q;
-      rr_pair(mp, round, k, p, q);
-      T c = T(1), s = T(0);
-      if (p < m && q < m) {
-        const T apq = C[p * m + q];
-        if (apq != T(0)) {
-          const T tau = (C[q * m + q] - C[p * m + p]) / (T(2) * apq);
-          const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-          c = T(1) / sqrt(T(1) + tt * tt);
-          s = tt * c;
-        }
-      }
-      rc[k] = c;
-      rs[k] = s;
-    }
-    __syncthreads();
-    for (int w = t; w < (mp / 2) * m; w += nt) {  // rows p, q
-      const int k = w / m, col = w % m;
-      int p, q;
-      rr_pair(mp, round, k, p, q);
-      if (p >= m || q >= m || rs[k] == T(0)) continue;
-      const T c = rc[k], s = rs[k];
-      const T xp = C[p * m + col], xq = C[q * m + col];
-      C[p * m + col] = c * xp - s * xq;
-      C[q * m + col] = s * xp + c * xq;
-    }
-    __syncthreads();
-    for (int w = t; w < (mp / 2) * m; w += nt) {  // columns p, q and the accumulated rotations
-      const int k = w / m, row = w % m;
-      int p, q;
-      rr_pair(mp, round, k, p, q);
-      if (p >= m || q >= m || rs[k] == T(0)) continue;
-      const T c = rc[k], s = rs[k];
-      const T xp = C[row * m + p], xq = C[row * m + q];
-      C[row * m + p] = c * xp - s * xq;
-      C[row * m + q] = s * xp + c * xq;
-      const T vp = V[row * m + p], vq = V[row * m + q];
-      V[row * m + p] = c * vp - s * vq;
-      V[row * m + q] = s * vp + c * vq;
-    }
-    __syncthreads();
-  }
-}
-
-// off-diagonal and total squared Frobenius mass of C (result valid in all threads)
-template <typename T>
-__device__ void offdiag_mass(const T* C, int m, double* red, double& off, double& tot) {
-  const int t = threadIdx.x, nt = blockDim.x;
-  double o = 0.0, a = 0.0;
-  for (int q = t; q < m * m; q += nt) {
-    const double v = (double)C[q] * (double)C[q];
-    a += v;
-    if (q / m != q % m) o += v;
-  }
-  for (int s = 16; s > 0; s >>= 1) {
-    o += __shfl_xor_sync(0xffffffffu, o, s);
-    a += __shfl_xor_sync(0xffffffffu, a, s);
-  }
-  __syncthreads();
-  if ((t & 31) == 0) {
-    red[2 * (t >> 5)] = o;
-    red[2 * (t >> 5) + 1] = a;
-  }
-  __syncthreads();
-  o = 0.0;
-  a = 0.0;
-  for (int w = 0; w < (nt + 31) / 32; ++w) {
-    o += red[2 * w];
-    a += red[2 * w + 1];
-  }
-  off = o;
-  tot = a;
-  __syncthreads();
-}
-
-// H: [m][ld] symmetric (only the leading m x m block is read).  full_precision != 0 adds the FP64
-// refinement.  Outputs theta[m] (descending) and Y (column i = eigenvector i, ld = ldy);
-// info[0] = FP32 sweeps, info[1] = FP64 sweeps.
-__global__ void __launch_bounds__(512) k_small_rr(const double* H, int m, int ld, double* theta, double* Y, int ldy,
-                                                  double* info, int full_precision) {
-  extern __shared__ double sm[];
-  double* C64 = sm;                       // [m*m]
-  double* V64 = C64 + m * m;              // [m*m]
-  double* T64 = V64 + m * m;              // [m*m]
-  double* rc64 = T64 + m * m;             // [kRRMax]
-  double* rs64 = rc64 + kRRMax;           // [kRRMax]
-  double* red = rs64 + kRRMax;            // [64]
-  float* C32 = reinterpret_cast<float*>(red + 64);  // [m*m]
-  float* V32 = C32 + m * m;                         // [m*m]
-  float* rc32 = V32 + m * m;                        // [kRRMax]
-  float* rs32 = rc32 + kRRMax;                      // [kRRMax]
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int q = t; q < m * m; q += nt) {
-    const int i = q / m, j = q % m;
-    const double a = 0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]);
-    C64[q] = a;
-    C32[q] = (float)a;
-    V32[q] = (i == j) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  double off, tot;
-  int s32 = 0, s64 = 0;
-  for (; s32 < 30; ++s32) {
-    offdiag_mass(C32, m, red, off, tot);
-    if (!(off > 1e-11 * tot)) break;
-    jacobi_sweep<float>(C32, V32, m, rc32, rs32);
-  }
-  for (int q = t; q < m * m; q += nt) V64[q] = (double)V32[q];
-  __syncthreads();
-  if (full_precision) {
-    // The FP32 rotations leave V64 orthonormal only to ~1e-7: re-orthonormalise its columns in FP64
-    // (classical Gram-Schmidt, column by column; T64 holds the projection coefficients).
-    for (int col = 0; col < m; ++col) {
-      for (int i = t; i < col; i += nt) {
-        double s = 0.0;
-        for (int r = 0; r < m; ++r) s += V64[r * m + i] * V64[r * m + col];
-        T64[i] = s;
-      }
-      __syncthreads();
-      for (int r = t; r < m; r += nt) {
-        double s = V64[r * m + col];
-        for (int i = 0; i < col; ++i) s -= T64[i] * V64[r * m + i];
-        V64[r * m + col] = s;
-      }
-      __syncthreads();
-      if (t < 32) {
-        double s = 0.0;
-        for (int r = t; r < m; r += 32) s += V64[r * m + col] * V64[r * m + col];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (t == 0) T64[m] = 1.0 / sqrt(s);
-      }
-      __syncthreads();
-      for (int r = t; r < m; r += nt) V64[r * m + col] *= T64[m];
-      __syncthreads();
-    }
-    // T = C64 V64, then C64 = V64^T T  (the FP32 basis makes C64 nearly diagonal)
-    for (int q = t; q < m * m; q += nt) {
-      const int i = q / m, j = q % m;
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s += C64[i * m + k] * V64[k * m + j];
-      T64[q] = s;
-    }
-    __syncthreads();
-    for (int q = t; q < m * m; q += nt) {
-      const int i = q / m, j = q % m;
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s += V64[k * m + i] * T64[k * m + j];
-      C64[q] = s;
-    }
-    __syncthreads();
-    for (int q = t; q < m * m; q += nt) {
-      const int i = q / m, j = q % m;
-      if (i < j) {
-        const double a = 0.5 * (C64[i * m + j] + C64[j * m + i]);
-        C64[i * m + j] = a;
-        C64[j * m + i] = a;
-      }
-    }
-    __syncthreads();
-    for (; s64 < 6; ++s64) {
-      offdiag_mass(C64, m, red, off, tot);
-      if (!(off > 1e-30 * tot)) break;
-      jacobi_sweep<double>(C64, V64, m, rc64, rs64);
-    }
-  } else {
-    for (int q = t; q < m * m; q += nt) C64[q] = (double)C32[q];
-    __syncthreads();
-  }
-  // sort descending by theta (rank by comparison; ties by index)
-  for (int c = t; c < m; c += nt) {
-    const double tc = C64[c * m + c];
-    int rank = 0;
-    for (int o = 0; o < m; ++o) {
-      const double to = C64[o * m + o];
-      if (to > tc || (to == tc && o < c)) ++rank;
-    }
-    theta[rank] = tc;
-    for (int i = 0; i < m; ++i) Y[(size_t)i * ldy + rank] = V64[i * m + c];
-  }
-  if (t == 0) {
-    info[0] = (double)s32;
-    info[1] = (double)s64;
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
-// Top-nvec eigenpairs of a small symmetric matrix in FP64 with few block-wide barriers:
-// Householder tridiagonalisation (about 5 barriers per column), then, one thread per wanted
-// eigenvalue, Sturm-sequence bisection and inverse iteration with a partially pivoted tridiagonal
-// solve, re-orthogonalisation inside clusters, and the back-transformation by the reflectors.
-// ------------------------------------------------------------------------------------------------
-constexpr int kTriMaxVec = 48;
-
-__device__ int sturm_count(const double* d, const double* e, int m, double x) {
-  double q = d[0] - x;
-  int cnt = q < 0.0 ? 1 : 0;
-  for (int i = 1; i < m; ++i) {
-    if (q == 0.0) q = 1e-300;
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
-    cnt += q < 0.0 ? 1 : 0;
-  }
-  return cnt;
-}
-
-// In-place solve of (tridiag(e, dd, e)) x = b with partial pivoting; dd, b overwritten; work
-// arrays dl, du, du2 of length m.
-__device__ void tridiag_solve_pivoted(const double* e, double* dd, double* b, double* dl, double* du, double* du2,
-                                      int n, double tiny) {
-  for (int i = 0; i < n - 1; ++i) {
-    dl[i] = e[i];
-    du[i] = e[i];
-  }
-  for (int i = 0; i < n - 1; ++i) {
-    if (fabs(dd[i]) >= fabs(dl[i])) {
-      if (dd[i] == 0.0) dd[i] = tiny;
-      const double f = dl[i] / dd[i];
-      dd[i + 1] -= f * du[i];
-      b[i + 1] -= f * b[i];
-      if (i < n - 2) du2[i] = 0.0;
+// Stage 1.  All m eigenvectors of H [m][ld] (symmetric part) in FP32 by cyclic Jacobi, written in
+// FP64 to X [m][m] (column c = eigenvector of the c-th largest eigenvalue).  The matrix is padded
+// to kRRMax = 64 rows (padding rows are never rotated); one round applies 32 disjoint rotations
+// J_k to C <- J C J^T as independent 2 x 2 blocks (one thread per pair of pairs), so a round costs
+// two barriers.  Warm start: when mprev > 0, Xp [mprev][mprev] (the previous eigenvectors of the
+// leading mprev x mprev block, FP64) starts the accumulated rotation V = diag(Xp, I), so that the
+// old block is already nearly diagonal.  info[0] = sweeps.
+__global__ void __launch_bounds__(1024) k_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev,
+                                                   double* X, double* info) {
+  constexpr int P = kRRMax;  // padded size (even)
+  extern __shared__ float sm32[];
+  float* C = sm32;       // [P*P]
+  float* V = C + P * P;  // [P*P] accumulated rotations, transposed: V[col * P + row]
+  float* T = V + P * P;  // [P*P]
+  __shared__ float cs[P / 2], sn[P / 2];
+  __shared__ int pp[P / 2], qq[P / 2];
+  __shared__ unsigned char pair_tab[(P - 1) * P];  // round-robin pairing: round r, slot k -> (p, q)
+  __shared__ double red[64];
+  __shared__ double hmax_s;
+  __shared__ int done_s;
+  const int t = threadIdx.x;  // blockDim.x == 1024 == (P/2)^2
+  for (int q = t; q < (P - 1) * (P / 2); q += 1024) {
+    const int round = q / (P / 2), k = q % (P / 2);
+    int p, r;
+    if (k == 0) {
+      p = P - 1;
+      r = round;
     } else {
-      const double f = dd[i] / dl[i];
-      dd[i] = dl[i];
-      const double tmp = dd[i + 1];
-      dd[i + 1] = du[i] - f * tmp;
-      if (i < n - 2) {
-        du2[i] = du[i + 1];
-        du[i + 1] = -f * du2[i];
-      }
-      du[i] = tmp;
-      const double tb = b[i];
-      b[i] = b[i + 1];
-      b[i + 1] = tb - f * b[i + 1];
+      p = (round + k) % (P - 1);
+      r = (round - k + (P - 1)) % (P - 1);
     }
+    pair_tab[2 * q] = (unsigned char)p;
+    pair_tab[2 * q + 1] = (unsigned char)r;
   }
-  if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
-  b[n - 1] /= dd[n - 1];
-  if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / dd[n - 2];
-  for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
-}
-
-// H [m][ld] symmetric; returns the nvec (<= kTriMaxVec) largest eigenvalues in theta (descending)
-// and their orthonormal eigenvectors in the first nvec columns of Y (ld = ldy).
-__global__ void __launch_bounds__(256) k_small_eig_tridiag(const double* H, int m, int ld, int nvec, double* theta,
-                                                           double* Y, int ldy, double* info) {
-  extern __shared__ double sm[];
-  double* A = sm;                  // [m*m]; column k below the diagonal stores reflector k
-  double* d = A + m * m;           // [m] diagonal of T
-  double* e = d + m;               // [m] sub-diagonal of T
-  double* beta = e + m;            // [m]
-  double* p = beta + m;            // [m]
-  double* lam = p + m;             // [kTriMaxVec]
-  double* Z = lam + kTriMaxVec;    // [kTriMaxVec][m] eigenvectors of T, then of H
-  double* red = Z + kTriMaxVec * m;  // [64]
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int q = t; q < m * m; q += nt) {
-    const int i = q / m, j = q % m;
-    A[q] = 0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]);
-  }
+  // scale by max |H| so that the FP32 working range holds any problem scaling
+  double mx = 0.0;
+  for (int q = t; q < m * m; q += 1024) mx = fmax(mx, fabs(H[(size_t)(q / m) * ld + q % m]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
   __syncthreads();
-  // ---- Householder tridiagonalisation
-  for (int k = 0; k < m - 2; ++k) {
-    const int s = m - k - 1;
-    double* colk = A + (size_t)(k + 1) * m + k;  // x_i = colk[i * m]
-    if (t < 32) {
-      double sig = 0.0;
-      for (int i = 1 + t; i < s; i += 32) sig += colk[i * m] * colk[i * m];
-      for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
-      if (t == 0) {
-        const double x0 = colk[0];
-        if (sig == 0.0) {
-          beta[k] = 0.0;
-          e[k] = x0;
-          red[0] = 1.0;  // v0 (no scaling of the tail)
-        } else {
-          const double mu = sqrt(x0 * x0 + sig);
-          const double v0 = x0 <= 0.0 ? x0 - mu : -sig / (x0 + mu);
-          beta[k] = 2.0 * v0 * v0 / (sig + v0 * v0);
-          e[k] = mu;
-          red[0] = v0;
-        }
-      }
-    }
-    __syncthreads();
-    const double v0 = red[0], bk = beta[k];
-    for (int i = 1 + t; i < s; i += nt) colk[i * m] /= v0;  // v = x / v0, v_0 = 1 (implicit)
-    __syncthreads();
-    if (bk != 0.0) {
-      double* A22 = A + (size_t)(k + 1) * m + (k + 1);
-      for (int i = t; i < s; i += nt) {
-        double acc = 0.0;
-        for (int j = 0; j < s; ++j) acc += A22[(size_t)i * m + j] * (j == 0 ? 1.0 : colk[j * m]);
-        p[i] = bk * acc;
-      }
-      __syncthreads();
-      if (t < 32) {
-        double kk = 0.0;
-        for (int i = t; i < s; i += 32) kk += p[i] * (i == 0 ? 1.0 : colk[i * m]);
-        for (int o = 16; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
-        if (t == 0) red[1] = 0.5 * bk * kk;
-      }
-      __syncthreads();
-      const double K = red[1];
-      for (int i = t; i < s; i += nt) p[i] -= K * (i == 0 ? 1.0 : colk[i * m]);
-      __syncthreads();
-      for (int q = t; q < s * s; q += nt) {
-        const int i = q / s, j = q % s;
-        const double vi = i == 0 ? 1.0 : colk[i * m], vj = j == 0 ? 1.0 : colk[j * m];
-        A22[(size_t)i * m + j] -= vi * p[j] + p[i] * vj;
-      }
-    }
-    __syncthreads();
-  }
-  for (int i = t; i < m; i += nt) d[i] = A[(size_t)i * m + i];
-  if (t == 0 && m >= 2) e[m - 2] = A[(size_t)(m - 1) * m + (m - 2)];
-  __syncthreads();
-  // ---- eigenvalues (bisection) and eigenvectors (inverse iteration) of T, one thread each
-  double tnorm = 0.0;
-  for (int i = 0; i < m; ++i) {
-    const double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0);
-    tnorm = fmax(tnorm, r);
-  }
-  if (t < nvec) {
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < m; ++i) {
-      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0);
-      lo = fmin(lo, d[i] - r);
-      hi = fmax(hi, d[i] + r);
-    }
-    const int rnk = m - 1 - t;
-    for (int it = 0; it < 200; ++it) {
-      if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
-      const double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, e, m, mid) <= rnk)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    const double l = 0.5 * (lo + hi);
-    lam[t] = l;
-    double dd[kRRMax], dl[kRRMax], du[kRRMax], du2[kRRMax];
-    double* x = Z + (size_t)t * m;
-    for (int i = 0; i < m; ++i) x[i] = 1.0 + 0.1 * (double)((i * 7919 + t * 31) % 13) / 13.0;
-    for (int it = 0; it < 3; ++it) {
-      for (int i = 0; i < m; ++i) dd[i] = d[i] - l;
-      tridiag_solve_pivoted(e, dd, x, dl, du, du2, m, 2.2e-16 * tnorm);
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
-      nrm = 1.0 / sqrt(nrm);
-      for (int i = 0; i < m; ++i) x[i] *= nrm;
-    }
-  }
-  __syncthreads();
-  // ---- re-orthogonalise eigenvectors inside clusters of close eigenvalues (serial, small)
   if (t == 0) {
-    for (int c = 1; c < nvec; ++c) {
-      int c0 = c;
-      while (c0 > 0 && fabs(lam[c0 - 1] - lam[c]) < 1e-6 * tnorm) --c0;
-      if (c0 == c) continue;
-      double* x = Z + (size_t)c * m;
-      for (int jv = c0; jv < c; ++jv) {
-        const double* y = Z + (size_t)jv * m;
-        double dot = 0.0;
-        for (int i = 0; i < m; ++i) dot += y[i] * x[i];
-        for (int i = 0; i < m; ++i) x[i] -= dot * y[i];
-      }
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
-      nrm = 1.0 / sqrt(nrm);
-      for (int i = 0; i < m; ++i) x[i] *= nrm;
-    }
+    double a = 0.0;
+    for (int w = 0; w < 32; ++w) a = fmax(a, red[w]);
+    hmax_s = a > 0.0 ? a : 1.0;
   }
   __syncthreads();
-  // ---- back-transformation y = H_0 H_1 ... H_{m-3} z, one thread per vector
-  if (t < nvec) {
-    double* x = Z + (size_t)t * m;
-    for (int k = m - 3; k >= 0; --k) {
-      const double bk = beta[k];
-      if (bk == 0.0) continue;
-      double dot = x[k + 1];
-      for (int i = k + 2; i < m; ++i) dot += A[(size_t)i * m + k] * x[i];
-      dot *= bk;
-      x[k + 1] -= dot;
-      for (int i = k + 2; i < m; ++i) x[i] -= dot * A[(size_t)i * m + k];
-    }
-    theta[t] = lam[t];
+  const float inv = (float)(1.0 / hmax_s);
+  for (int q = t; q < P * P; q += 1024) {
+    const int i = q >> 6, j = q & (P - 1);
+    float h = 0.f, v = (i == j) ? 1.f : 0.f;
+    if (i < m && j < m) h = inv * (float)(0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]));
+    if (i < mprev && j < mprev) v = (float)Xp[(size_t)i * mprev + j];
+    T[q] = h;
+    V[j * P + i] = v;
   }
   __syncthreads();
-  for (int q = t; q < m * nvec; q += nt) {
-    const int i = q / nvec, c = q % nvec;
-    Y[(size_t)i * ldy + c] = Z[(size_t)c * m + i];
-  }
-  if (t == 0) {
-    info[0] = 0.0;
-    info[1] = 0.0;
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
-// The same method split over several thread blocks, so that the FP64 work of the per-eigenvalue
-// bisection and inverse iteration (the dominant part at GB300's FP64 rate) runs on one SM per
-// eigenvalue.  Scratch layout in global memory (tri, doubles):
-//   [0, m*m)            reflectors (column k below the diagonal), as in k_small_eig_tridiag
-//   d [m], e [m], beta [m], lam [kTriMaxVec], Z [kTriMaxVec][m]
-// ------------------------------------------------------------------------------------------------
-struct TriScratch {
-  double *A, *d, *e, *beta, *lam, *Z;
-  __host__ __device__ static TriScratch at(double* base, int mmax) {
-    TriScratch s;
-    s.A = base;
-    s.d = base + (size_t)mmax * mmax;
-    s.e = s.d + mmax;
-    s.beta = s.e + mmax;
-    s.lam = s.beta + mmax;
-    s.Z = s.lam + kTriMaxVec;
-    return s;
-  }
-  static size_t doubles(int mmax) { return (size_t)mmax * mmax + 3 * (size_t)mmax + kTriMaxVec + (size_t)kTriMaxVec * mmax; }
-};
-
-// Stage 1 (one block): Householder tridiagonalisation of H into the scratch.
-__global__ void __launch_bounds__(256) k_tri_reduce(const double* H, int m, int ld, double* scratch, int mmax) {
-  extern __shared__ double sm[];
-  double* A = sm;           // [m*m]
-  double* p = A + m * m;    // [m]
-  double* beta = p + m;     // [m]
-  double* e = beta + m;     // [m]
-  double* red = e + m;      // [8]
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int q = t; q < m * m; q += nt) {
-    const int i = q / m, j = q % m;
-    A[q] = 0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]);
-  }
-  __syncthreads();
-  for (int k = 0; k < m - 2; ++k) {
-    const int s = m - k - 1;
-    double* colk = A + (size_t)(k + 1) * m + k;
-    if (t < 32) {
-      double sig = 0.0;
-      for (int i = 1 + t; i < s; i += 32) sig += colk[i * m] * colk[i * m];
-      for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
-      if (t == 0) {
-        const double x0 = colk[0];
-        if (sig == 0.0) {
-          beta[k] = 0.0;
-          e[k] = x0;
-          red[0] = 1.0;
-        } else {
-          const double mu = sqrt(x0 * x0 + sig);
-          const double v0 = x0 <= 0.0 ? x0 - mu : -sig / (x0 + mu);
-          beta[k] = 2.0 * v0 * v0 / (sig + v0 * v0);
-          e[k] = mu;
-          red[0] = v0;
-        }
-      }
+  if (mprev > 0) {  // C = V^T T V
+    for (int q = t; q < P * P; q += 1024) {  // C <- T V
+      const int i = q >> 6, j = q & (P - 1);
+      float a = 0.f;
+      for (int k = 0; k < P; ++k) a += T[i * P + k] * V[j * P + k];
+      C[q] = a;
     }
     __syncthreads();
-    const double v0 = red[0], bk = beta[k];
-    for (int i = 1 + t; i < s; i += nt) colk[i * m] /= v0;
-    __syncthreads();
-    if (bk != 0.0) {
-      const double* A22 = A + (size_t)(k + 1) * m + (k + 1);
-      // p = bk A22 v, reading A22 by columns (symmetric) so that neighbouring threads touch
-      // neighbouring words
-      for (int i = t; i < s; i += nt) {
-        double acc = 0.0;
-        for (int j = 0; j < s; ++j) acc += A22[(size_t)j * m + i] * (j == 0 ? 1.0 : colk[j * m]);
-        p[i] = bk * acc;
-      }
-      __syncthreads();
-      if (t < 32) {
-        double kk = 0.0;
-        for (int i = t; i < s; i += 32) kk += p[i] * (i == 0 ? 1.0 : colk[i * m]);
-        for (int o = 16; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
-        if (t == 0) red[1] = 0.5 * bk * kk;
-      }
-      __syncthreads();
-      const double K = red[1];
-      for (int i = t; i < s; i += nt) p[i] -= K * (i == 0 ? 1.0 : colk[i * m]);
-      __syncthreads();
-      double* A22w = A + (size_t)(k + 1) * m + (k + 1);
-      for (int q = t; q < s * s; q += nt) {
-        const int i = q / s, j = q % s;
-        const double vi = i == 0 ? 1.0 : colk[i * m], vj = j == 0 ? 1.0 : colk[j * m];
-        A22w[(size_t)i * m + j] -= vi * p[j] + p[i] * vj;
-      }
+    for (int q = t; q < P * P; q += 1024) {  // T <- V^T C
+      const int i = q >> 6, j = q & (P - 1);
+      float a = 0.f;
+      for (int k = 0; k < P; ++k) a += V[i * P + k] * C[k * P + j];
+      T[q] = a;
     }
     __syncthreads();
   }
-  TriScratch S = TriScratch::at(scratch, mmax);
-  for (int q = t; q < m * m; q += nt) S.A[q] = A[q];
-  for (int i = t; i < m; i += nt) {
-    S.d[i] = A[(size_t)i * m + i];
-    S.beta[i] = i < m - 2 ? beta[i] : 0.0;
-    S.e[i] = i < m - 2 ? e[i] : (i == m - 2 ? A[(size_t)(m - 1) * m + (m - 2)] : 0.0);
-  }
-}
-
-// Stage 2 (one block of 64 threads per wanted eigenvalue c): the c-th largest eigenvalue of T by
-// multisection (64 Sturm counts per round), then its eigenvector by inverse iteration.
-__global__ void __launch_bounds__(64) k_tri_eigvec(double* scratch, int mmax, int m) {
-  const TriScratch S = TriScratch::at(scratch, mmax);
-  __shared__ double d[kRRMax], e[kRRMax];
-  __shared__ double lo_s, hi_s;
-  __shared__ int cnt[64];
-  const int t = threadIdx.x, c = blockIdx.x;
-  for (int i = t; i < m; i += blockDim.x) {
-    d[i] = S.d[i];
-    e[i] = S.e[i];
-  }
+  for (int q = t; q < P * P; q += 1024) C[q] = T[q];
   __syncthreads();
-  double tnorm = 0.0, lo = 1e300, hi = -1e300;
-  for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < m - 1 ? fabs(e[i]) : 0.0);
-    tnorm = fmax(tnorm, fabs(d[i]) + r);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
-  }
-  const int rnk = m - 1 - c;  // rank among the ascending eigenvalues
-  for (int round = 0; round < 40; ++round) {
-    if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
-    const double x = lo + (hi - lo) * (double)(t + 1) / (double)(blockDim.x + 1);
-    cnt[t] = sturm_count(d, e, m, x);
+  int sweeps = 0;
+  for (; sweeps < 30; ++sweeps) {
+    // convergence: off-diagonal mass below 1e-11 of the total (about 3e-6 relative)
+    double o = 0.0, a = 0.0;
+    for (int q = t; q < P * P; q += 1024) {
+      const double v = (double)C[q] * (double)C[q];
+      a += v;
+      if ((q >> 6) != (q & (P - 1))) o += v;
+    }
+    for (int s = 16; s > 0; s >>= 1) {
+      o += __shfl_xor_sync(0xffffffffu, o, s);
+      a += __shfl_xor_sync(0xffffffffu, a, s);
+    }
+    if ((t & 31) == 0) {
+      red[2 * (t >> 5)] = o;
+      red[2 * (t >> 5) + 1] = a;
+    }
     __syncthreads();
     if (t == 0) {
-      // sample points x_1 < ... < x_64; keep the sub-interval whose ends bracket rank rnk
-      double nlo = lo, nhi = hi;
-      for (int k = 0; k < (int)blockDim.x; ++k) {
-        const double xk = lo + (hi - lo) * (double)(k + 1) / (double)(blockDim.x + 1);
-        if (cnt[k] <= rnk)
-          nlo = xk;
-        else {
-          nhi = xk;
-          break;
-        }
+      double oo = 0.0, aa = 0.0;
+      for (int w = 0; w < 32; ++w) {
+        oo += red[2 * w];
+        aa += red[2 * w + 1];
       }
-      lo_s = nlo;
-      hi_s = nhi;
+      done_s = !(oo > 1e-11 * aa);
     }
     __syncthreads();
-    lo = lo_s;
-    hi = hi_s;
-    __syncthreads();
+    if (done_s) break;
+    for (int round = 0; round < P - 1; ++round) {
+      if (t < P / 2) {  // rotation of pair slot t (round-robin pairing of P indices)
+        const int p = pair_tab[2 * (round * (P / 2) + t)], q = pair_tab[2 * (round * (P / 2) + t) + 1];
+        float c = 1.f, s = 0.f;
+        if (p < m && q < m) {
+          const float apq = C[p * P + q];
+          if (apq != 0.f) {
+            const float tau = (C[q * P + q] - C[p * P + p]) / (2.f * apq);
+            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + tt * tt);
+            s = tt * c;
+          }
+        }
+        pp[t] = p;
+        qq[t] = q;
+        cs[t] = c;
+        sn[t] = s;
+      }
+      __syncthreads();
+      {  // block (A, B) of pair slots: rows (p1, q1), columns (p2, q2): B' = J_A B J_B^T
+        const int A = t >> 5, Bs = t & 31;
+        const int p1 = pp[A], q1 = qq[A], p2 = pp[Bs], q2 = qq[Bs];
+        const float c1 = cs[A], s1 = sn[A], c2 = cs[Bs], s2 = sn[Bs];
+        const float b00 = C[p1 * P + p2], b01 = C[p1 * P + q2], b10 = C[q1 * P + p2], b11 = C[q1 * P + q2];
+        // left: rows p1, q1
+        const float l00 = c1 * b00 - s1 * b10, l01 = c1 * b01 - s1 * b11;
+        const float l10 = s1 * b00 + c1 * b10, l11 = s1 * b01 + c1 * b11;
+        // right: columns p2, q2
+        C[p1 * P + p2] = c2 * l00 - s2 * l01;
+        C[p1 * P + q2] = s2 * l00 + c2 * l01;
+        C[q1 * P + p2] = c2 * l10 - s2 * l11;
+        C[q1 * P + q2] = s2 * l10 + c2 * l11;
+        // accumulated rotation V <- V J^T: columns p, q of two pair slots, row t & 63
+        const int row = t & (P - 1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = (t >> 6) + 16 * h;
+          const int p = pp[k], q = qq[k];
+          const float vp = V[p * P + row], vq = V[q * P + row];
+          V[p * P + row] = cs[k] * vp - sn[k] * vq;
+          V[q * P + row] = sn[k] * vp + cs[k] * vq;
+        }
+      }
+      __syncthreads();
+    }
   }
-  if (t != 0) return;
-  const double l = 0.5 * (lo + hi);
-  S.lam[c] = l;
-  double dd[kRRMax], dl[kRRMax], du[kRRMax], du2[kRRMax];
-  double* x = S.Z + (size_t)c * m;
-  for (int i = 0; i < m; ++i) x[i] = 1.0 + 0.1 * (double)((i * 7919 + c * 31) % 13) / 13.0;
-  for (int it = 0; it < 3; ++it) {
-    for (int i = 0; i < m; ++i) dd[i] = d[i] - l;
-    tridiag_solve_pivoted(e, dd, x, dl, du, du2, m, 2.2e-16 * tnorm);
-    double nrm = 0.0;
-    for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
-    nrm = 1.0 / sqrt(nrm);
-    for (int i = 0; i < m; ++i) x[i] *= nrm;
+  // descending order of the diagonal (ties by index); padding rows excluded
+  for (int c = t; c < m; c += 1024) {
+    const float tc = C[c * P + c];
+    int rank = 0;
+    for (int o = 0; o < m; ++o) {
+      const float to = C[o * P + o];
+      if (to > tc || (to == tc && o < c)) ++rank;
+    }
+    for (int i = 0; i < m; ++i) X[(size_t)i * m + rank] = (double)V[c * P + i];
+  }
+  if (t == 0) info[0] = (double)sweeps;
+}
+
+inline size_t rr_eig32_smem_bytes() { return sizeof(float) * 3 * (size_t)kRRMax * kRRMax; }
+
+// Stage 2a.  S = X^T Hs X and R = I - X^T X ([m][m] each), Hs = (H + H^T)/2; block j computes
+// column j.
+__global__ void __launch_bounds__(64) k_rr_oa_products(const double* H, int ld, const double* X, int m, double* S,
+                                                       double* R) {
+  __shared__ double xj[kRRMax], pj[kRRMax];
+  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  for (int i = t; i < m; i += nt) xj[i] = X[(size_t)i * m + j];
+  __syncthreads();
+  for (int i = t; i < m; i += nt) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += 0.5 * (H[(size_t)k * ld + i] + H[(size_t)i * ld + k]) * xj[k];
+    pj[i] = s;
+  }
+  __syncthreads();
+  for (int i = t; i < m; i += nt) {
+    double s = 0.0, r = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double xki = X[(size_t)k * m + i];
+      s += xki * pj[k];
+      r += xki * xj[k];
+    }
+    S[(size_t)i * m + j] = s;
+    R[(size_t)i * m + j] = (i == j ? 1.0 : 0.0) - r;
   }
 }
 
-// Stage 3 (one block): re-orthogonalisation inside clusters, back-transformation, output.
-__global__ void __launch_bounds__(256) k_tri_finish(double* scratch, int mmax, int m, int nvec, double* theta,
-                                                    double* Y, int ldy) {
-  const TriScratch S = TriScratch::at(scratch, mmax);
-  extern __shared__ double sm[];
-  double* Z = sm;                       // [nvec][m]
-  double* A = Z + (size_t)nvec * m;     // [m*m] reflectors
-  double* dots = A + (size_t)m * m;     // [kTriMaxVec]
+// Stage 2b.  One refinement step for columns j < gridDim.x (block j, 64 threads):
+// Xout[:, j] = X[:, j] + X E[:, j] (ldo = leading dimension of Xout) and lam_out[j].
+// set_delta != 0: the step's error bound delta = 2 (||S - diag(lambda)||_F + max|lambda| ||R||_F)
+// is computed (by every block, identically) and block 0 stores it in *delta; otherwise *delta is
+// read.
+__global__ void __launch_bounds__(64) k_rr_oa_update(const double* X, const double* S, const double* R, int m,
+                                                     double* Xout, int ldo, double* lam_out, double* delta,
+                                                     int set_delta) {
+  __shared__ double lam[kRRMax], e[kRRMax], red[6];
+  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  for (int i = t; i < m; i += nt) lam[i] = S[(size_t)i * m + i] / (1.0 - R[(size_t)i * m + i]);
+  __syncthreads();
+  double dl;
+  if (set_delta) {
+    double so = 0.0, ro = 0.0, lm = 0.0;
+    for (int q = t; q < m * m; q += nt) {
+      const int i = q / m, k = q % m;
+      const double sv = S[q] - (i == k ? lam[i] : 0.0);
+      so += sv * sv;
+      ro += R[q] * R[q];
+    }
+    for (int i = t; i < m; i += nt) lm = fmax(lm, fabs(lam[i]));
+    for (int o = 16; o > 0; o >>= 1) {
+      so += __shfl_xor_sync(0xffffffffu, so, o);
+      ro += __shfl_xor_sync(0xffffffffu, ro, o);
+      lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    }
+    if ((t & 31) == 0) {
+      red[3 * (t >> 5)] = so;
+      red[3 * (t >> 5) + 1] = ro;
+      red[3 * (t >> 5) + 2] = lm;
+    }
+    __syncthreads();
+    so = red[0] + red[3];
+    ro = red[1] + red[4];
+    lm = fmax(red[2], red[5]);
+    dl = 2.0 * (sqrt(so) + lm * sqrt(ro));
+    if (j == 0 && t == 0) *delta = dl;
+  } else {
+    dl = *delta;
+  }
+  for (int i = t; i < m; i += nt) {
+    const double rij = R[(size_t)i * m + j];
+    double eij = 0.5 * rij;
+    if (i != j && fabs(lam[j] - lam[i]) > dl) eij = (S[(size_t)i * m + j] + lam[j] * rij) / (lam[j] - lam[i]);
+    e[i] = eij;
+  }
+  __syncthreads();
+  for (int r = t; r < m; r += nt) {
+    double s = X[(size_t)r * m + j];
+    for (int i = 0; i < m; ++i) s += X[(size_t)r * m + i] * e[i];
+    Xout[(size_t)r * ldo + j] = s;
+  }
+  if (t == 0 && lam_out) lam_out[j] = lam[j];
+}
+
+// Stage 3 (one block).  The nvec refined columns Xw [m][ldw] with their lam are sorted by
+// descending lam; each run of neighbours closer than *delta (a cluster the refinement did not
+// split) is diagonalised by FP64 Jacobi rotations of its block B = Z^T Hs Z.  Outputs
+// theta[nvec] (descending) and Y [m][ldy].  Scratch in shared memory (dynamic): Z [nvec][m],
+// HZ [kRRClusterMax][m].
+constexpr int kRRClusterMax = 16;
+__global__ void __launch_bounds__(256) k_rr_finish(const double* H, int ld, int m, int nvec, const double* Xw, int ldw,
+                                                   const double* lam_in, const double* delta, double* theta, double* Y,
+                                                   int ldy) {
+  extern __shared__ double smd[];
+  double* Z = smd;                                   // [nvec][m]
+  double* HZ = Z + (size_t)nvec * m;                 // [kRRClusterMax][m]
+  __shared__ double l[kRRMax], B[kRRClusterMax * kRRClusterMax], Q[kRRClusterMax * kRRClusterMax];
+  __shared__ int rk[kRRClusterMax];
   const int t = threadIdx.x, nt = blockDim.x;
-  for (int q = t; q < nvec * m; q += nt) Z[q] = S.Z[q];
-  for (int q = t; q < m * m; q += nt) A[q] = S.A[q];
-  double tnorm = 0.0;
-  for (int i = 0; i < m; ++i) {
-    const double r = (i > 0 ? fabs(S.e[i - 1]) : 0.0) + (i < m - 1 ? fabs(S.e[i]) : 0.0);
-    tnorm = fmax(tnorm, fabs(S.d[i]) + r);
+  for (int c = t; c < nvec; c += nt) {
+    const double lc = lam_in[c];
+    int rank = 0;
+    for (int o = 0; o < nvec; ++o) {
+      const double lo = lam_in[o];
+      if (lo > lc || (lo == lc && o < c)) ++rank;
+    }
+    l[rank] = lc;
+    for (int i = 0; i < m; ++i) Z[(size_t)rank * m + i] = Xw[(size_t)i * ldw + c];
   }
   __syncthreads();
-  for (int cc = 1; cc < nvec; ++cc) {
-    int c0 = cc;
-    while (c0 > 0 && fabs(S.lam[c0 - 1] - S.lam[cc]) < 1e-6 * tnorm) --c0;
-    if (c0 == cc) continue;  // uniform across the block
-    double* x = Z + (size_t)cc * m;
-    const int w = t >> 5, lane = t & 31;
-    for (int jv = c0 + w; jv < cc; jv += nt >> 5) {  // one warp per previous cluster member
-      const double* y = Z + (size_t)jv * m;
-      double s = 0.0;
-      for (int i = lane; i < m; i += 32) s += y[i] * x[i];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) dots[jv] = s;
+  const double dl = *delta;
+  int c0 = 0;
+  while (c0 < nvec) {
+    int c1 = c0 + 1;
+    while (c1 < nvec && c1 - c0 < kRRClusterMax && fabs(l[c1 - 1] - l[c1]) <= dl) ++c1;
+    const int c = c1 - c0;
+    if (c > 1) {
+      // HZ = Hs Z_c, B = Z_c^T HZ
+      for (int q = t; q < c * m; q += nt) {
+        const int a = q / m, i = q % m;
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s += 0.5 * (H[(size_t)k * ld + i] + H[(size_t)i * ld + k]) * Z[(size_t)(c0 + a) * m + k];
+        HZ[(size_t)a * m + i] = s;
+      }
+      __syncthreads();
+      for (int q = t; q < c * c; q += nt) {
+        const int a = q / c, b = q % c;
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s += Z[(size_t)(c0 + a) * m + k] * HZ[(size_t)b * m + k];
+        B[q] = s;
+        Q[q] = (a == b) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      if (t == 0) {
+        for (int a = 0; a < c; ++a)
+          for (int b = a + 1; b < c; ++b) {
+            const double s = 0.5 * (B[a * c + b] + B[b * c + a]);
+            B[a * c + b] = s;
+            B[b * c + a] = s;
+          }
+        for (int sweep = 0; sweep < 12; ++sweep) {
+          double off = 0.0, tot = 0.0;
+          for (int q = 0; q < c * c; ++q) {
+            tot += B[q] * B[q];
+            if (q / c != q % c) off += B[q] * B[q];
+          }
+          if (!(off > 1e-32 * tot)) break;
+          for (int p = 0; p < c - 1; ++p)
+            for (int r = p + 1; r < c; ++r) {
+              const double apr = B[p * c + r];
+              if (apr == 0.0) continue;
+              const double tau = (B[r * c + r] - B[p * c + p]) / (2.0 * apr);
+              const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+              const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
+              for (int k = 0; k < c; ++k) {  // rows p, r
+                const double xp = B[p * c + k], xr = B[r * c + k];
+                B[p * c + k] = cs * xp - sn * xr;
+                B[r * c + k] = sn * xp + cs * xr;
+              }
+              for (int k = 0; k < c; ++k) {  // columns p, r and the rotation
+                const double xp = B[k * c + p], xr = B[k * c + r];
+                B[k * c + p] = cs * xp - sn * xr;
+                B[k * c + r] = sn * xp + cs * xr;
+                const double qp = Q[k * c + p], qr = Q[k * c + r];
+                Q[k * c + p] = cs * qp - sn * qr;
+                Q[k * c + r] = sn * qp + cs * qr;
+              }
+            }
+        }
+        // order the cluster's eigenpairs by descending value
+        for (int a = 0; a < c; ++a) {
+          int rank = 0;
+          for (int o = 0; o < c; ++o)
+            if (B[o * c + o] > B[a * c + a] || (B[o * c + o] == B[a * c + a] && o < a)) ++rank;
+          rk[a] = rank;
+        }
+        for (int a = 0; a < c; ++a) l[c0 + rk[a]] = B[a * c + a];
+      }
+      __syncthreads();
+      // Z_c <- Z_c Q (columns permuted into descending order), through HZ as scratch
+      for (int q = t; q < c * m; q += nt) {
+        const int a = q / m, i = q % m;
+        double s = 0.0;
+        for (int k = 0; k < c; ++k) s += Z[(size_t)(c0 + k) * m + i] * Q[k * c + a];
+        HZ[(size_t)rk[a] * m + i] = s;
+      }
+      __syncthreads();
+      for (int q = t; q < c * m; q += nt) Z[(size_t)c0 * m + q] = HZ[q];
+      __syncthreads();
     }
-    __syncthreads();
-    for (int i = t; i < m; i += nt) {
-      double v = x[i];
-      for (int jv = c0; jv < cc; ++jv) v -= dots[jv] * Z[(size_t)jv * m + i];
-      x[i] = v;
-    }
-    __syncthreads();
-    if (t < 32) {
-      double s = 0.0;
-      for (int i = t; i < m; i += 32) s += x[i] * x[i];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (t == 0) dots[kTriMaxVec - 1] = 1.0 / sqrt(s);
-    }
-    __syncthreads();
-    const double sc = dots[kTriMaxVec - 1];
-    for (int i = t; i < m; i += nt) x[i] *= sc;
-    __syncthreads();
+    c0 = c1;
   }
-  // back-transformation, one thread per vector
-  if (t < nvec) {
-    double* x = Z + (size_t)t * m;
-    for (int k = m - 3; k >= 0; --k) {
-      const double bk = S.beta[k];
-      if (bk == 0.0) continue;
-      double dot = x[k + 1];
-      for (int i = k + 2; i < m; ++i) dot += A[(size_t)i * m + k] * x[i];
-      dot *= bk;
-      x[k + 1] -= dot;
-      for (int i = k + 2; i < m; ++i) x[i] -= dot * A[(size_t)i * m + k];
-    }
-    theta[t] = S.lam[t];
-  }
-  __syncthreads();
+  for (int c = t; c < nvec; c += nt) theta[c] = l[c];
   for (int q = t; q < m * nvec; q += nt) {
     const int i = q / nvec, c = q % nvec;
     Y[(size_t)i * ldy + c] = Z[(size_t)c * m + i];
   }
 }
 
-inline size_t tri_reduce_smem_bytes() { return sizeof(double) * ((size_t)kRRMax * kRRMax + 3 * (size_t)kRRMax + 8); }
-inline size_t tri_finish_smem_bytes() {
-  return sizeof(double) * ((size_t)kTriMaxVec * kRRMax + (size_t)kRRMax * kRRMax + kTriMaxVec);
-}
-
-inline size_t small_eig_tridiag_smem_bytes() {
-  return sizeof(double) * ((size_t)kRRMax * kRRMax + 4 * (size_t)kRRMax + kTriMaxVec + (size_t)kTriMaxVec * kRRMax + 64);
-}
-
-inline size_t small_rr_smem_bytes() {
-  return sizeof(double) * (3 * (size_t)kRRMax * kRRMax + 2 * kRRMax + 64) +
-         sizeof(float) * (2 * (size_t)kRRMax * kRRMax + 2 * kRRMax);
+inline size_t rr_finish_smem_bytes(int m, int nvec) {
+  return sizeof(double) * ((size_t)nvec * m + (size_t)kRRClusterMax * m);
 }
 
 }  // namespace tobk

@@ -197,8 +197,10 @@ static void layout(tobk_handle* h, Arena& a) {
   h->f = a.take<double>(g.n);
   h->u = a.take<double>(g.n);
   h->u0 = a.take<double>(g.n);
-  h->Gs0 = a.take<double>(g.m * nn * nn);
-  h->Gs = a.take<double>(g.m * nn * nn);
+  if (!h->solve_only) {
+    h->Gs0 = a.take<double>(g.m * nn * nn);
+    h->Gs = a.take<double>(g.m * nn * nn);
+  }
   const int64_t nc = h->lv[h->L - 1].g.n;
   h->Adense = a.take<double>(nc * nc);
   h->Awork = a.take<double>(nc * nc);
@@ -211,10 +213,14 @@ static void layout(tobk_handle* h, Arena& a) {
   h->cg.p1 = a.take<double>(rm * nf);
   h->cg.q = a.take<double>(rm * nf);
   h->cg.sc = a.take<double>((size_t)kMaxRhs * kScStride);
-  h->cg.partial = a.take<double>((size_t)kMaxRhs * cg_partial_stride(g.nnode));
+  h->cg.partial = a.take<double>((size_t)kMaxRhs * cg_partial_stride(g));
   h->cg.counters = a.take<unsigned>((size_t)kNumCounterSets * kMaxRhs);
   h->bwork = a.take<double>(rm * nf);
   h->xwork = a.take<double>(rm * nf);
+  if (h->solve_only) {  // linear solves only (a member of a batch): no buckling or sensitivity storage
+    h->dscal = a.take<double>(1024);
+    return;
+  }
   const int q = h->q;
   h->modes = a.take<double>((size_t)q * nf);
   h->lam = a.take<double>(q);
@@ -240,14 +246,15 @@ static void layout(tobk_handle* h, Arena& a) {
   h->Bs = a.take<double>((size_t)mm * mm);
   h->Ys = a.take<double>((size_t)mm * mm);
   h->Cs = a.take<double>((size_t)mm * mm);
-  // small eigensolver scratch: reflectors [mm*mm], d, e, beta [mm each], 48 eigenvalues, 48 vectors
-  h->tri = a.take<double>((size_t)mm * mm + 3 * (size_t)mm + 48 + 48 * (size_t)mm);
+  // Rayleigh-Ritz scratch: five [mm][mm] matrices (FP32-stage and refined eigenvectors, S, R, wanted
+  // columns), the refined eigenvalues and the refinement bound
+  h->tri = a.take<double>(5 * (size_t)mm * mm + (size_t)mm + 8);
   const int64_t gp_rows = std::max<int64_t>(gram_partial_blocks(ne), gram_partial_blocks(nf));
   h->gram_partial = a.take<double>((size_t)gp_rows * mm * std::max(mm, nb));
   h->dscal = a.take<double>(1024);
 }
 
-int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
+int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solve_only) {
   if (!d || !out) return TOBK_E_ARG;
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return TOBK_E_ARG;
@@ -266,6 +273,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out) {
   }
   tobk_handle* h = new tobk_handle();
   h->desc = *d;
+  h->solve_only = solve_only;
   h->stream = (cudaStream_t)stream;
   cudaGetDevice(&h->device);
   h->dim = d->dim;

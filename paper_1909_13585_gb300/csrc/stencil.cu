@@ -146,13 +146,25 @@ static void stencil_dispatch(const Grid& g, const T* S, const uint8_t* fixed, in
     k_apply_stencil<DIM, T, APPLY_JAC, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
 }
 
+// Right-hand sides per thread: reusing a stencil row across several RHS saves loads on large levels,
+// while small levels need every thread they can get (one RHS per thread) to hide load latency.
 template <typename T>
 void launch_apply_stencil(const Grid& g, const T* S, const uint8_t* fixed, int mode, const T* v, const T* b,
                           const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
-  if (g.dim == 2)
-    stencil_dispatch<2, T, 4>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
-  else
-    stencil_dispatch<3, T, 2>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+  const int64_t work = g.nnode;
+  if (g.dim == 2) {
+    if (work <= 8192)
+      stencil_dispatch<2, T, 1>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+    else if (work <= 32768)
+      stencil_dispatch<2, T, 2>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+    else
+      stencil_dispatch<2, T, 4>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+  } else {
+    if (work <= 8192)
+      stencil_dispatch<3, T, 1>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+    else
+      stencil_dispatch<3, T, 2>(g, S, fixed, mode, v, b, dinv, y, sm, nr, stride, s);
+  }
 }
 
 template void launch_apply_stencil<double>(const Grid&, const double*, const uint8_t*, int, const double*,

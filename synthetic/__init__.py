@@ -220,10 +220,21 @@ def config(name: str) -> Problem:
     raise KeyError(name)
 
 
+def batch_levels(nel_long: int, nel_short: int, coarsest_short: int = 8) -> int:
+    """Multigrid levels of a batch design: halve both axes while the short side is even and larger
+    than coarsest_short (and the long side stays even)."""
+    levels, t, a = 1, nel_short, nel_long
+    while t % 2 == 0 and t > coarsest_short and a % 2 == 0:
+        t //= 2
+        a //= 2
+        levels += 1
+    return levels
+
+
 def batch_configs(count: int = 64, seed0: int = 100) -> List[Problem]:
     """Uneven batch of 2D columns: nel_long = a * nel_short with a in {2, 3, 4},
     nel_short in {32, 48, 64, ..., 256}, nel_long <= 512; volfrac ~ U[0.3, 0.6], radius in [2, 4].
-    Each design coarsens until the short side has at most 16 elements."""
+    Each design coarsens until the short side has at most 8 elements (batch_levels)."""
     out = []
     rng = np.random.default_rng(seed0)
     shorts = [s for s in range(32, 257, 16)]
@@ -233,13 +244,8 @@ def batch_configs(count: int = 64, seed0: int = 100) -> List[Problem]:
             s = int(shorts[int(rng.integers(0, len(shorts)))])
             if a * s <= 512:
                 break
-        levels = 1
-        t = s
-        while t % 2 == 0 and t > 16 and (a * t) % 2 == 0:
-            t //= 2
-            levels += 1
         vf = float(rng.uniform(0.3, 0.6))
         r = float(rng.uniform(2.0, 4.0))
-        out.append(column_2d(a * s, s, seed=seed0 + b, radius=r, volfrac=vf,
-                             name=f"batch{b}", mg_levels=levels, eig_level=1, num_modes=6))
+        out.append(column_2d(a * s, s, seed=seed0 + b, radius=r, volfrac=vf, name=f"batch{b}",
+                             mg_levels=batch_levels(a * s, s), eig_level=1, num_modes=6))
     return out

@@ -245,3 +245,17 @@ def test_adjoint_rhs_matches_directional_derivative_of_G():
     gp = phi @ (op.G(u + t * w) @ phi)
     gm = phi @ (op.G(u - t * w) @ phi)
     assert b @ w == pytest.approx((gp - gm) / (2 * t), rel=1e-10)
+
+
+def test_batch_configs_shapes_and_levels():
+    """The uneven 2D batch workload: 64 designs, 64 x 32 up to 512 x 256, aspect 2:1 to 4:1, each
+    axis divisible by 2^(levels - 1), coarsest short side at most 8 elements."""
+    import synthetic
+    bs = synthetic.batch_configs()
+    assert len(bs) == 64
+    for p in bs:
+        nx, ny = p.nel[0], p.nel[1]
+        assert 32 <= nx <= 256 and ny in (2 * nx, 3 * nx, 4 * nx) and ny <= 512
+        assert nx % 2 ** (p.mg_levels - 1) == 0 and ny % 2 ** (p.mg_levels - 1) == 0
+        assert nx >> (p.mg_levels - 1) <= 8 or (nx >> (p.mg_levels - 1)) % 2 == 1
+        assert 0.3 <= p.meta["volfrac"] <= 0.6 and abs(p.x.mean() - p.meta["volfrac"]) < 1e-5
