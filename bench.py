@@ -37,10 +37,6 @@ METRIC = "DOF*RHS solved/s at rel. residual 1e-8"
 UNIT = "DOF*RHS/s"
 WORKLOAD = "column480x160"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 ALU roofline: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz (maximum SM clock); a
-# register-only FMA probe measured 1.194 TFLOP/s at 1995 MHz, i.e. the same 2 FMA/clk/SM.
-FP64_PEAK_GFLOPS = 152 * 4 * 2.070
-FP32_PEAK_GFLOPS = 152 * 256 * 2.070
 
 
 def parse():
@@ -157,6 +153,23 @@ def measure_batch(pkg, torch, steps, warmup, dev, flush, count=64, nadj=6):
             "rhs_per_design": 1 + nadj, "precision": "fp32_vcycle", "autotuned_variants": list(variants),
             "iterations_max": max(i["iterations"] for i in infos),
             "rel_residual_max": max(i["rel_residual"] for i in infos), "steps": steps, "warmup": warmup}
+
+
+def measure_learned(pkg, torch, dev, flush, designs=4):
+    """Learned warm start on held-out 128 x 64 x 64 designs: network inference + mgPCG from its guess
+    against plain mgPCG from zero, both to relative residual 1e-8 (one RHS per design)."""
+    from paper_1909_13585_gb300 import learned
+    if not os.path.exists(learned.WEIGHTS):
+        return {"unavailable": "no trained weights in the package"}
+    X = learned.densities(range(learned.TEST_SEEDS[0], learned.TEST_SEEDS[0] + designs), workers=1)
+    net = learned.load_weights(pkg, torch, learned.WEIGHTS, stream=torch.cuda.Stream(device=dev))
+    learned.evaluate(pkg, torch, net, X[:1], flush=flush)  # warm-up (graph capture, allocations)
+    rows = learned.evaluate(pkg, torch, net, X, flush=flush)
+    net.close()
+    sm = learned.summary(rows)
+    dofs = learned.problem(X[0]).num_dofs
+    return {"value": dofs / (sm["ms_learned_mean"] / 1e3), "value_plain": dofs / (sm["ms_plain_mean"] / 1e3),
+            "unit": UNIT, "dofs": dofs, "rhs_per_step": 1, "held_out_designs": designs, **sm}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -278,55 +291,71 @@ def config_dict(p, precision):
 # ------------------------------------------------------------------------------------------------
 # roofline of the dominant kernel class
 # ------------------------------------------------------------------------------------------------
-def kernel_source_hash():
+def sources_hash(paths):
     h = hashlib.sha1()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1909_13585_gb300", "csrc"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(ROOT, "paper_1909_13585_gb300", "csrc", f), "rb").read())
+    for f in paths:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:12]
 
 
 def profiled_traffic(kclass, workload):
-    """DRAM bytes per launch of the kernel class from a committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+    """DRAM bytes per launch of the kernel class from the committed ncu summary
+    profiles/<class>_<workload>.md, if the sources it lists are unchanged since the capture (their
+    hash matches), else None."""
     path = os.path.join(ROOT, "profiles", f"{kclass}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    hm = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not hm or hm.group(1) != kernel_source_hash():
+    sm = re.search(r"sources:\s*(.+)", txt)
+    hm = re.search(r"sources_hash:\s*([0-9a-f]+)", txt)
+    if not (m and sm and hm):
+        return None
+    paths = sm.group(1).split()
+    if not all(os.path.exists(os.path.join(ROOT, f)) for f in paths) or sources_hash(paths) != hm.group(1):
         return None
     return float(m.group(1))
 
 
+# Algorithmic FP64 operations (add, multiply or fused multiply-add: one FP64-pipe issue each) per
+# node and right-hand side of the fine-level factored Q4 kernels: 41 per element for the forces
+# (one element per node), 6 to gather the four element contributions of a node's two DOFs, plus the
+# per-DOF update: Chebyshev/Jacobi step 5 x 2, residual 1 x 2, CG direction (z + beta p, p.q) 2 x 2.
+Q4_FP64_OPS_PER_NODE = {"fine_smooth": 41 + 6 + 10, "fine_residual": 41 + 6 + 2, "fine_cg_matvec": 41 + 6 + 4}
+# FP64 pipe: 152 SMs x 2 FP64 instructions per clock x 2070 MHz (the maximum SM clock); a register-only
+# FMA probe on this part measured 1.194 TFLOP/s at 1995 MHz, i.e. the same 2 FMA per clock per SM.
+FP64_OPS_PEAK_G = 152 * 2 * 2.070
+
+
 def roofline(prof, p, peaks, precision):
-    """Dominant kernel class by device time; algorithmic work per launch from its DOF x RHS."""
+    """Roofline of the dominant kernel class (most device time): achieved = algorithmic work per
+    launch (from the DOF x RHS the class processed) / average launch time (CUDA events on the
+    solver's stream)."""
     name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    nd = p.dim * 2 ** p.dim
-    m, n = p.num_elements, p.num_dofs
-    out = {"kernel_class": name, "launches": rec["launches"], "avg_launch_us": 1e3 * rec["ms"] / max(rec["launches"], 1)}
-    rhs_total = rec["dof_rhs"] / n if name.startswith("fine") else None
-    per_launch_s = 1e-3 * rec["ms"] / max(rec["launches"], 1)
-    if name.startswith("fine") and rhs_total is not None:
-        # element products: 2 nd^2 flop per element per RHS (+ 3 flop per DOF of the update)
-        flops = rhs_total * (2.0 * nd * nd * m + 3.0 * n) / rec["launches"]
-        word = 8 if precision == "fp64" else 4
-        bytes_ = rhs_total * (4 * word * n) / rec["launches"] + 8 * m + n
-        peak = FP64_PEAK_GFLOPS if precision == "fp64" else FP32_PEAK_GFLOPS
-        achieved = flops / per_launch_s / 1e9
-        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                    "frac": achieved / peak,
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (FP32: x128)",
+    m, n, nnode = p.num_elements, p.num_dofs, p.num_nodes
+    launches = max(rec["launches"], 1)
+    per_launch_s = 1e-3 * rec["ms"] / launches
+    out = {"kernel_class": name, "launches": rec["launches"], "avg_launch_us": 1e6 * per_launch_s}
+    hbm = peaks.get("hbm_gbs", 6792.7)
+    if name in Q4_FP64_OPS_PER_NODE and p.dim == 2 and precision == "fp64":
+        rhs_per_launch = rec["dof_rhs"] / n / launches
+        ops = rhs_per_launch * nnode * Q4_FP64_OPS_PER_NODE[name]
+        # bytes: per RHS read v, b (and d_in), write y (and d_out); per node dinv, fixed; per element E
+        vec_words = {"fine_smooth": 5, "fine_residual": 3, "fine_cg_matvec": 5}[name]
+        bytes_ = rhs_per_launch * 8.0 * vec_words * n + 8.0 * n + n + 8.0 * m
+        achieved = ops / per_launch_s / 1e9
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_OPS_PEAK_G, "unit": "G FP64 ops/s",
+                    "frac": achieved / FP64_OPS_PEAK_G,
+                    "peak_source": "derived: 152 SMs x 2 FP64 pipe issues/clk x 2070 MHz (measured FMA probe agrees)",
+                    "algorithmic_fp64_ops_per_launch": ops, "algorithmic_bytes_per_launch": bytes_,
                     "hbm_gbs_at_same_time": bytes_ / per_launch_s / 1e9,
-                    "hbm_frac_of_measured": (bytes_ / per_launch_s / 1e9) / peaks.get("hbm_gbs", 6792.7),
-                    "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_})
+                    "hbm_frac_of_measured": bytes_ / per_launch_s / 1e9 / hbm})
     else:
-        bytes_ = 8.0 * 4 * rec["dof_rhs"] / max(rec["launches"], 1)
+        word = 8 if precision == "fp64" else 4
+        bytes_ = 4.0 * word * rec["dof_rhs"] / launches  # read v, b, dinv-scaled update, write y per DOF x RHS
         achieved = bytes_ / per_launch_s / 1e9
-        out.update({"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6792.7), "unit": "GB/s",
-                    "frac": achieved / peaks.get("hbm_gbs", 6792.7), "peak_source": "of measured",
-                    "algorithmic_bytes_per_launch": bytes_})
+        out.update({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "peak_source": "of measured", "algorithmic_bytes_per_launch": bytes_})
     out["traffic"] = profiled_traffic(name, p.name)
     return out
 
@@ -461,6 +490,7 @@ def ours(args):
         forms["cantilever96x48x48_fp32_vcycle_fused"] = measure_form(pkg, torch, "cantilever96x48x48",
                                                                      pkg.TOBK_FP32_VCYCLE, True, fs, fw, dev, flush)
         forms["batch64_column2d_fp32_vcycle"] = measure_batch(pkg, torch, fs, fw, dev, flush)
+        forms["cantilever128x64x64_learned_warm_start"] = measure_learned(pkg, torch, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

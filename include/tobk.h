@@ -240,6 +240,65 @@ int tobk_batch_autotune(tobk_batch* b, int* fine_variant, int* coarse_variant);
 /* Sets the variants explicitly (same numbering). */
 int tobk_batch_set_variants(tobk_batch* b, int fine_variant, int coarse_variant);
 
+/* ---- learned warm start (not part of the paper's method) -------------------------------------
+ * A small 3D U-Net maps a design (densities x [m] and load f [n] of an H8 grid) to an initial guess
+ * u0 [n] for tobk_set_initial_guess; mgPCG then runs to the same tolerance as without it, so the
+ * network can change the iteration count but never the accepted accuracy.  Architecture: `levels`
+ * encoder levels of two 3x3x3 convolutions + ReLU (2x2x2 average pooling between levels), a
+ * decoder with nearest 2x upsampling and skip concatenation, a 1x1x1 output head on the finest
+ * decoder level plus a coarse-correction head on the bottleneck (upsampled and added), node
+ * averaging of the per-element output times a fixed output scale c (t), and a per-design scale
+ * s = mean(E_kappa) / (largest element load sum): u0 = t / s.  Input features: 2x - 1 and the
+ * element load sums normalised by their largest magnitude.  Loss of a sample with solution u,
+ * t* = s u, K the sample's stiffness: the relative energy-norm error (t - t*)^T K (t - t*) /
+ * t*^T K t* over the free DOFs (default; what CG convergence depends on), or the relative squared
+ * error sum_free (t - t*)^2 / sum_free t*^2.
+ * Parameters: one FP32 vector (Adam's master copy) in the order enc_l a, enc_l b (l = 0..L-1),
+ * dec_l a, dec_l b (l = L-2..0), head, coarse head; each layer W [Cout][Cin][taps] then b [Cout];
+ * the convolutions use a bfloat16 copy with FP32 accumulation.  Hand-written CUDA kernels for the
+ * forward and backward passes and the Adam update; all pointers below are DEVICE pointers. */
+typedef enum { TOBK_UNET_LOSS_MSE = 0, TOBK_UNET_LOSS_ENERGY = 1 } tobk_unet_loss_kind;
+typedef struct {
+  int nel[3];           /* H8 element grid (x, y, z); each divisible by 2^(levels-1) */
+  int levels;           /* 1..4 */
+  int channels[4];      /* per level, multiples of 16, at most 256 */
+  int in_channels;      /* 4 */
+  int out_channels;     /* 3 */
+  double penal, E0, Emin;  /* SIMP parameters of the designs (scale s, energy loss) */
+  double nu;            /* Poisson ratio (energy loss) */
+  int loss;             /* tobk_unet_loss_kind: relative energy-norm error of the guess (default) or
+                           relative squared error of the scaled displacements */
+  unsigned long long seed; /* weight initialisation (He normal, zero biases) */
+} tobk_unet_desc;
+typedef struct tobk_unet tobk_unet;
+/* defaults: 128 x 64 x 64, 4 levels, channels 16/32/64/64, p 3, E0 1, Emin 1e-6 */
+int tobk_unet_default_desc(tobk_unet_desc* desc);
+int tobk_unet_create(const tobk_unet_desc* desc, void* cuda_stream, tobk_unet** out);
+void tobk_unet_destroy(tobk_unet* net);
+const char* tobk_unet_last_error(const tobk_unet* net);
+int64_t tobk_unet_num_params(const tobk_unet* net);
+/* The output scale c of the guess t = c * (node average of the output) (default 1; chosen from the
+ * training data so that the network's outputs are of order one). */
+int tobk_unet_set_output_scale(tobk_unet* net, double scale);
+double tobk_unet_output_scale(const tobk_unet* net);
+/* The design scale s = mean(E_kappa) / (largest element load sum) of x [m] (FP32), f [n] -> *s (host). */
+int tobk_unet_design_scale(tobk_unet* net, const float* x, const double* f, double* s);
+/* Parameters, Adam moments and step count (checkpoint / resume); any array pointer may be NULL on
+ * get; on set, NULL moments restart Adam from zero.  on_device selects device or host arrays. */
+int tobk_unet_get_state(tobk_unet* net, float* params, float* adam_m, float* adam_v, long long* step, int on_device);
+int tobk_unet_set_state(tobk_unet* net, const float* params, const float* adam_m, const float* adam_v, long long step,
+                        int on_device);
+/* u0 [n] (FP64, zero at fixed DOFs) from x [m] (FP64), f [n] (FP64), fixed [n]. */
+int tobk_unet_predict(tobk_unet* net, const double* x, const double* f, const uint8_t* fixed, double* u0);
+/* Loss of one sample (x [m] FP32, target solution [n] FP32) and its gradient grad [num_params]
+ * (may be NULL). */
+int tobk_unet_loss_grad(tobk_unet* net, const float* x, const double* f, const float* target, const uint8_t* fixed,
+                        float* loss, float* grad);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the mean gradient of nbatch samples
+ * x [nbatch][m], target [nbatch][n] (FP32) sharing f and fixed; *loss = mean sample loss. */
+int tobk_unet_train_step(tobk_unet* net, const float* x, const double* f, const float* target, const uint8_t* fixed,
+                         int nbatch, float lr, float* loss);
+
 /* ---- allocation-free residual check ------------------------------------------------------------
  * Not part of the paper's method (it has no counterpart there): a utility for callers that must not
  * allocate device memory when they verify a solution, e.g. code running while a stream is being

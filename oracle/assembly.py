@@ -65,3 +65,32 @@ def restrict_free(A: sp.spmatrix, fixed: np.ndarray) -> sp.csr_matrix:
     """Rows and columns of the free DOFs (Dirichlet DOFs eliminated)."""
     free = np.flatnonzero(fixed == 0)
     return A.tocsr()[free][:, free].tocsr()
+
+
+def apply_K(nel, dim, x, nu, penal, E0, Emin, V) -> np.ndarray:
+    """y = K[x] v for each row v of V (all DOFs, no BCs), element by element without assembly:
+    y = sum_e E_kappa(x_e) A_e^T K_e0 A_e v (Sec. 2).  For grids too large to assemble cheaply."""
+    Ke0 = elements.stiffness_ke0(dim, nu)
+    edofs = grid.element_dofs(nel, dim)
+    Ek, _, _, _ = elements.simp(np.asarray(x, dtype=np.float64), penal, E0, Emin)
+    V = np.atleast_2d(np.asarray(V, dtype=np.float64))
+    n = V.shape[1]
+    out = np.zeros_like(V)
+    for r in range(V.shape[0]):
+        Fe = Ek[:, None] * (V[r][edofs] @ Ke0.T)
+        out[r] = np.bincount(edofs.reshape(-1), weights=Fe.reshape(-1), minlength=n)
+    return out
+
+
+def apply_G(nel, dim, x, u, nu, penal, E0, Emin, V) -> np.ndarray:
+    """y = G[x, u] v for each row v of V, element by element: sum_e E_sigma(x_e) A_e^T G_e0[u_e] A_e v."""
+    edofs = grid.element_dofs(nel, dim)
+    _, Es, _, _ = elements.simp(np.asarray(x, dtype=np.float64), penal, E0, Emin)
+    Ge = element_stress_stiffness(nel, dim, u, nu)
+    V = np.atleast_2d(np.asarray(V, dtype=np.float64))
+    n = V.shape[1]
+    out = np.zeros_like(V)
+    for r in range(V.shape[0]):
+        Fe = Es[:, None] * np.einsum("mij,mj->mi", Ge, V[r][edofs])
+        out[r] = np.bincount(edofs.reshape(-1), weights=Fe.reshape(-1), minlength=n)
+    return out

@@ -65,6 +65,19 @@ _SIGS = {
     "tobk_batch_solve": (C.c_int, [_H, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
     "tobk_batch_autotune": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "tobk_batch_set_variants": (C.c_int, [_H, C.c_int, C.c_int]),
+    "tobk_unet_default_desc": (C.c_int, [C.c_void_p]),
+    "tobk_unet_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(_H)]),
+    "tobk_unet_destroy": (None, [_H]),
+    "tobk_unet_last_error": (C.c_char_p, [_H]),
+    "tobk_unet_num_params": (C.c_int64, [_H]),
+    "tobk_unet_set_output_scale": (C.c_int, [_H, C.c_double]),
+    "tobk_unet_output_scale": (C.c_double, [_H]),
+    "tobk_unet_design_scale": (C.c_int, [_H, _P, _P, C.POINTER(C.c_double)]),
+    "tobk_unet_get_state": (C.c_int, [_H, _P, _P, _P, C.POINTER(C.c_longlong), C.c_int]),
+    "tobk_unet_set_state": (C.c_int, [_H, _P, _P, _P, C.c_longlong, C.c_int]),
+    "tobk_unet_predict": (C.c_int, [_H, _P, _P, _P, _P]),
+    "tobk_unet_loss_grad": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_float), _P]),
+    "tobk_unet_train_step": (C.c_int, [_H, _P, _P, _P, _P, C.c_int, C.c_float, C.POINTER(C.c_float)]),
     "tobk_launch_count": (C.c_longlong, []),
     "tobk_profile_enable": (C.c_int, [_H, C.c_int]),
     "tobk_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
@@ -343,3 +356,91 @@ class Batch:
 
     def set_variants(self, fine, coarse):
         self._check(self.lib.tobk_batch_set_variants(self.h, fine, coarse))
+
+
+class tobk_unet_desc(C.Structure):
+    _fields_ = [("nel", C.c_int * 3), ("levels", C.c_int), ("channels", C.c_int * 4), ("in_channels", C.c_int),
+                ("out_channels", C.c_int), ("penal", C.c_double), ("E0", C.c_double), ("Emin", C.c_double),
+                ("nu", C.c_double), ("loss", C.c_int), ("seed", C.c_ulonglong)]
+
+
+TOBK_UNET_LOSS_MSE, TOBK_UNET_LOSS_ENERGY = 0, 1
+
+
+class UNet:
+    """Owner of a tobk_unet (the learned warm start): device tensors in, device tensors out."""
+
+    def __init__(self, nel=(128, 64, 64), levels=4, channels=(16, 32, 64, 64), seed=1234, *, stream=None,
+                 penal=3.0, E0=1.0, Emin=1e-6, nu=0.3, loss=TOBK_UNET_LOSS_ENERGY):
+        self.lib = load()
+        d = tobk_unet_desc()
+        self.lib.tobk_unet_default_desc(C.byref(d))
+        for a in range(3):
+            d.nel[a] = nel[a]
+        d.levels = levels
+        for l in range(4):
+            d.channels[l] = channels[l] if l < levels else 0
+        d.penal, d.E0, d.Emin, d.seed, d.nu, d.loss = penal, E0, Emin, seed, nu, loss
+        h = _H()
+        s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = self.lib.tobk_unet_create(C.byref(d), C.c_void_p(s), C.byref(h))
+        if rc != TOBK_OK:
+            raise TobkError(rc, "tobk_unet_create failed")
+        self.h = h
+        self.stream = stream
+        self.nel, self.levels, self.channels = tuple(nel), levels, tuple(channels[:levels])
+        self.num_params = int(self.lib.tobk_unet_num_params(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tobk_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != TOBK_OK:
+            raise TobkError(rc, self.lib.tobk_unet_last_error(self.h).decode())
+
+    def set_output_scale(self, c):
+        self._check(self.lib.tobk_unet_set_output_scale(self.h, float(c)))
+
+    def output_scale(self):
+        return float(self.lib.tobk_unet_output_scale(self.h))
+
+    def design_scale(self, x, f):
+        s = C.c_double()
+        self._check(self.lib.tobk_unet_design_scale(self.h, x.data_ptr(), f.data_ptr(), C.byref(s)))
+        return s.value
+
+    def get_state(self, params, m=None, v=None):
+        step = C.c_longlong()
+        pp, dev = _ptr(params)
+        self._check(self.lib.tobk_unet_get_state(self.h, pp, _ptr(m)[0] if m is not None else None,
+                                                 _ptr(v)[0] if v is not None else None, C.byref(step), dev))
+        return step.value
+
+    def set_state(self, params, m=None, v=None, step=0):
+        pp, dev = _ptr(params)
+        self._check(self.lib.tobk_unet_set_state(self.h, pp, _ptr(m)[0] if m is not None else None,
+                                                 _ptr(v)[0] if v is not None else None, step, dev))
+
+    def predict(self, x, f, fixed, u0):
+        self._check(self.lib.tobk_unet_predict(self.h, x.data_ptr(), f.data_ptr(), fixed.data_ptr(), u0.data_ptr()))
+
+    def loss_grad(self, x, f, target, fixed, grad=None):
+        loss = C.c_float()
+        self._check(self.lib.tobk_unet_loss_grad(self.h, x.data_ptr(), f.data_ptr(), target.data_ptr(),
+                                                 fixed.data_ptr(), C.byref(loss),
+                                                 grad.data_ptr() if grad is not None else None))
+        return loss.value
+
+    def train_step(self, x, f, target, fixed, nbatch, lr):
+        loss = C.c_float()
+        self._check(self.lib.tobk_unet_train_step(self.h, x.data_ptr(), f.data_ptr(), target.data_ptr(),
+                                                  fixed.data_ptr(), nbatch, lr, C.byref(loss)))
+        return loss.value

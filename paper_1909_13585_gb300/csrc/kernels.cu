@@ -135,6 +135,10 @@ void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double
     launch_fine_q4<double>(op.g, op.scale64, op.fixed, op.T0, mode, v, b, dinv, y, sm, nr, stride, s);
     return;
   }
+  if (!op.stored && op.g.dim == 3) {
+    launch_fine_h8<double>(op.g, op.scale64, op.fixed, op.nu, mode, v, b, dinv, y, sm, nr, stride, s);
+    return;
+  }
   if (op.g.dim == 2)
     apply_dim<2>(op, mode, v, b, dinv, y, sm, nr, stride, s);
   else
@@ -149,6 +153,10 @@ void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float
   }
   if (!op.stored && op.g.dim == 2) {
     launch_fine_q4<float>(op.g, op.scale32, op.fixed, op.T0, mode, v, b, dinv, y, sm, nr, stride, s);
+    return;
+  }
+  if (!op.stored && op.g.dim == 3) {
+    launch_fine_h8<float>(op.g, op.scale32, op.fixed, op.nu, mode, v, b, dinv, y, sm, nr, stride, s);
     return;
   }
   if (op.g.dim == 2)
@@ -948,7 +956,7 @@ __global__ void __launch_bounds__(kThreads) k_true_residual(const __grid_constan
 
 int64_t cg_partial_stride(const Grid& g) {
   const int64_t a = (g.nnode + kThreads - 1) / kThreads;
-  return 4 * std::max<int64_t>(std::max<int64_t>(a, kVecBlocks), g.dim == 2 ? fine_q4_tiles(g) : 0);
+  return 4 * std::max<int64_t>(std::max<int64_t>(a, kVecBlocks), g.dim == 2 ? fine_q4_tiles(g) : fine_h8_blocks(g));
 }
 
 template <int DIM, class Op>
@@ -993,6 +1001,11 @@ void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_
                          int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   if (d.g.dim == 2 && !d.stored) {
     launch_fine_q4_cg_direction(d.g, d.scale64, d.fixed, d.T0, z, p_old, p_new, q, nr, stride, sc, partial,
+                                counters + 2 * kMaxRhs, cg_partial_stride(d.g), s);
+    return;
+  }
+  if (d.g.dim == 3 && !d.stored) {
+    launch_fine_h8_cg_direction(d.g, d.scale64, d.fixed, d.nu, z, p_old, p_new, q, nr, stride, sc, partial,
                                 counters + 2 * kMaxRhs, cg_partial_stride(d.g), s);
     return;
   }

@@ -32,6 +32,7 @@ struct LevelOpDesc {
   // ([node][neighbour][d][d]); when set, smoother and residual launches use it
   const double* S64 = nullptr;
   const float* S32 = nullptr;
+  double nu = 0.3;  // Poisson ratio (the factored fine H8 operator builds its constants from it)
 };
 
 // Assembles the per-node stencil of a stored-element-matrix level (rows/columns of fixed DOFs
@@ -103,6 +104,16 @@ void launch_stress_gs_dev(const Grid& g, const double* u, const double* Es, cons
 int64_t cg_partial_stride(const Grid& g);
 // Thread blocks of the factored fine Q4 kernels for one RHS (tiles of 32 x 8 nodes).
 int64_t fine_q4_tiles(const Grid& g);
+// Largest number of thread blocks per RHS of the factored fine H8 kernels.
+int64_t fine_h8_blocks(const Grid& g);
+// Factored fine H8 operator: y = K v | b - K v | smoothing step (same contract as launch_apply).
+template <typename T>
+void launch_fine_h8(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int mode, const T* v, const T* b,
+                    const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s);
+// CG direction on the fine H8 level in factored form (same contract as launch_cg_direction).
+void launch_fine_h8_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, double nu, const double* z,
+                                 const double* p_old, double* p_new, double* q, int nr, int64_t stride, double* sc,
+                                 double* partial, unsigned* counters, int64_t pstride, cudaStream_t s);
 // CG direction on the fine Q4 level in factored form: p_new = z + beta p_old, q = K p_new,
 // sc[SC_PQ] = p_new . q, sc[SC_ALPHA] (same contract as launch_cg_direction).
 void launch_fine_q4_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, const double* Ke0,

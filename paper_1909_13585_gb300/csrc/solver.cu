@@ -421,6 +421,7 @@ LevelOpDesc level_op(tobk_handle* h, int j) {
   LevelOpDesc d{};
   d.g = h->lv[j].g;
   d.fixed = h->lv[j].fixed;
+  d.nu = h->desc.nu;
   if (j == 0) {
     d.stored = false;
     d.scale64 = h->Ek;

@@ -115,7 +115,7 @@ def density_field(shape_zyx: Tuple[int, ...], seed: int, radius: float, volfrac:
     s = (s - s.mean()) / s.std()
     base = volfrac + amplitude * s
     lo, hi = -1.0, 1.0
-    for _ in range(200):
+    for _ in range(64):  # the bracket [-1, 1] shrinks below one unit in the last place of c
         c = 0.5 * (lo + hi)
         m = np.clip(base + c, xmin, 1.0).mean()
         if m < volfrac:

@@ -259,3 +259,21 @@ def test_batch_configs_shapes_and_levels():
         assert nx % 2 ** (p.mg_levels - 1) == 0 and ny % 2 ** (p.mg_levels - 1) == 0
         assert nx >> (p.mg_levels - 1) <= 8 or (nx >> (p.mg_levels - 1)) % 2 == 1
         assert 0.3 <= p.meta["volfrac"] <= 0.6 and abs(p.x.mean() - p.meta["volfrac"]) < 1e-5
+
+
+def test_elementwise_apply_equals_assembled_operators():
+    """The assembly-free K v and G v of the oracle (used for full-size checks) equal the assembled
+    sparse operators."""
+    import synthetic
+    from oracle import assembly
+    for p in (synthetic.column_2d(12, 6, seed=4, radius=2, mg_levels=1),
+              synthetic.cantilever_3d(6, 4, 2, seed=5, radius=1.5, volfrac=0.4, mg_levels=1)):
+        rng = np.random.default_rng(1)
+        V = rng.standard_normal((2, p.num_dofs))
+        u = rng.standard_normal(p.num_dofs)
+        K = assembly.assemble_K(p.nel, p.dim, p.x, p.nu, p.penal, p.E0, p.Emin)
+        G = assembly.assemble_G(p.nel, p.dim, p.x, u, p.nu, p.penal, p.E0, p.Emin)
+        yk = assembly.apply_K(p.nel, p.dim, p.x, p.nu, p.penal, p.E0, p.Emin, V)
+        yg = assembly.apply_G(p.nel, p.dim, p.x, u, p.nu, p.penal, p.E0, p.Emin, V)
+        assert np.allclose(yk, (K @ V.T).T, rtol=1e-12, atol=1e-12 * np.abs(yk).max())
+        assert np.allclose(yg, (G @ V.T).T, rtol=1e-12, atol=1e-12 * np.abs(yg).max())
