@@ -114,7 +114,7 @@ def train(net, torch, Xd, U, f, fixed, epochs=4, batch=4, lr=2e-3, seed=0, log=N
 def _params_only(net, torch):
     P = torch.zeros(net.num_params, dtype=torch.float32)
     net.get_state(P)
-    return (P,)
+    return P
 
 
 def save_weights(net, torch, path):
@@ -221,7 +221,7 @@ def main():
         Xd = torch.from_numpy(X).to(dev)
         if args.init:
             net = load_weights(pkg, torch, args.init, stream=stream)
-            net.set_state(*_params_only(net, torch), 0)  # keep the weights, restart Adam
+            net.set_state(_params_only(net, torch), None, None, 0)  # keep the weights, restart Adam
         else:
             net = pkg.UNet(NEL, LEVELS, CHANNELS, stream=stream)
             net.set_output_scale(output_scale(net, Xd, U, fixed, f))

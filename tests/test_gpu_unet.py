@@ -38,10 +38,10 @@ def _smooth_target(p):
     return u
 
 
-@pytest.mark.parametrize("loss", ["energy", "mse"])
-def test_loss_gradient_and_prediction_match_oracle(loss):
+@pytest.mark.parametrize("kind", ["energy", "mse"])
+def test_loss_gradient_and_prediction_match_oracle(kind):
     torch, pkg = require_gpu()
-    net = pkg.UNet(NEL, LEVELS, CH, loss=pkg.binding.TOBK_UNET_LOSS_ENERGY if loss == "energy" else
+    net = pkg.UNet(NEL, LEVELS, CH, loss=pkg.binding.TOBK_UNET_LOSS_ENERGY if kind == "energy" else
                    pkg.binding.TOBK_UNET_LOSS_MSE)
     assert net.num_params == ou.num_params(LEVELS, list(CH))
     theta = _theta(net.num_params)
@@ -61,7 +61,7 @@ def test_loss_gradient_and_prediction_match_oracle(loss):
     loss = net.loss_grad(x32, f, tgt, fx, g)
     lo, go = ou.gradient(theta.astype(np.float64), p.x.astype(np.float32).astype(np.float64), p.f,
                          u.astype(np.float32).astype(np.float64), p.fixed, p.nel, LEVELS, list(CH), out_scale=c,
-                         loss=loss)
+                         loss=kind)
     assert loss == pytest.approx(lo, rel=1e-4)
     gg = g.cpu().numpy().astype(np.float64)
     assert np.abs(gg - go).max() <= 2e-3 * np.abs(go).max()
