@@ -1,0 +1,45 @@
+"""The trained warm start on held-out designs of the 128 x 64 x 64 cantilever workload: plain mgPCG
+from the network's guess reaches the same relative residual as from zero (the network can change
+the iteration count, never the accepted accuracy), the guess is a finite-energy approximation of
+the solution, and what it gains or loses in iterations is reported (bench.py reports the same on
+more designs)."""
+import numpy as np
+import pytest
+
+from oracle import assembly
+from tests.gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_trained_warm_start_keeps_the_tolerance_and_reports_its_gain():
+    torch, pkg = require_gpu()
+    from paper_1909_13585_gb300 import learned
+    X = learned.densities(range(learned.TEST_SEEDS[0], learned.TEST_SEEDS[0] + 2), workers=1)
+    stream = torch.cuda.Stream()
+    net = learned.load_weights(pkg, torch, learned.WEIGHTS, stream=stream)
+    rows = learned.evaluate(pkg, torch, net, X)
+    for r in rows:
+        assert r["plain"]["converged"] == 1 and r["learned"]["converged"] == 1
+        assert r["plain"]["rel_residual"] <= 1e-8 and r["learned"]["rel_residual"] <= 1e-8
+        assert abs(r["learned"]["iterations"] - r["plain"]["iterations"]) <= 8
+    # energy-norm error of the guess against the solution, with the oracle's operator
+    p = learned.problem(X[0])
+    s = pkg.Solver(p, stream=stream, precision=pkg.TOBK_FP32_VCYCLE, max_rhs=1)
+    s.solve_equilibrium()
+    u = s.get_field(pkg.TOBK_FIELD_U)
+    dev = torch.device("cuda")
+    u0 = torch.zeros(p.num_dofs, dtype=torch.float64, device=dev)
+    net.predict(torch.from_numpy(p.x).to(dev), torch.from_numpy(p.f).to(dev),
+                torch.from_numpy(p.fixed.astype(np.uint8)).to(dev), u0)
+    torch.cuda.synchronize()
+    e = u0.cpu().numpy() - u
+    Ke = assembly.apply_K(p.nel, p.dim, p.x, p.nu, p.penal, p.E0, p.Emin, e)[0]
+    Ku = assembly.apply_K(p.nel, p.dim, p.x, p.nu, p.penal, p.E0, p.Emin, u)[0]
+    free = p.fixed == 0
+    rel = float(e[free] @ Ke[free] / (u[free] @ Ku[free]))
+    print(f"relative energy error of the guess {rel:.3f}; iterations plain / learned "
+          f"{[r['plain']['iterations'] for r in rows]} / {[r['learned']['iterations'] for r in rows]}")
+    assert np.isfinite(rel) and rel < 1.5
+    s.close()
+    net.close()
