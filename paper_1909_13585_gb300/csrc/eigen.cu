@@ -187,7 +187,6 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   double* Rinv = M + (size_t)nb * nb;
   static bool rr_configured = false;
   if (!rr_configured) {
-    cudaFuncSetAttribute(k_rr_eig32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_eig32_smem_bytes());
     cudaFuncSetAttribute(k_rr_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)rr_finish_smem_bytes(kRRMax, kRRMax));
     rr_configured = true;
@@ -253,12 +252,17 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     const int nvec = std::min(m, keep_max);
     prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)m);
     // warm start from the previous refined eigenvectors while the basis only grew since then
-    ::tobk::note_launch(), k_rr_eig32<<<1, 1024, rr_eig32_smem_bytes(), st>>>(h->Hs, m, mmax, rrX1, rr_prev, rrX0,
-                                                                              sinfo + 2);
-    ::tobk::note_launch(), k_rr_oa_products<<<m, 64, 0, st>>>(h->Hs, mmax, rrX0, m, rrS, rrR);
-    ::tobk::note_launch(), k_rr_oa_update<<<m, 64, 0, st>>>(rrX0, rrS, rrR, m, rrX1, m, nullptr, rrDelta, 1);
-    ::tobk::note_launch(), k_rr_oa_products<<<m, 64, 0, st>>>(h->Hs, mmax, rrX1, m, rrS, rrR);
-    ::tobk::note_launch(), k_rr_oa_update<<<nvec, 64, 0, st>>>(rrX1, rrS, rrR, m, rrXw, mmax, rrLam, rrDelta, 0);
+    ::tobk::note_launch(), launch_rr_eig32(h->Hs, m, mmax, rrX1, rr_prev, rrX0, sinfo + 2, st);
+    // refinement: X0 -> X1 -> X0 ... (the last step writes the nvec wanted columns to Xw); the error
+    // bound of the FP32 result decides the clusters of every step and of the finish
+    for (int step = 0; step < kRRRefineSteps; ++step) {
+      const bool last = step == kRRRefineSteps - 1;
+      double* xin = (step & 1) ? rrX1 : rrX0;
+      double* xout = last ? rrXw : ((step & 1) ? rrX0 : rrX1);
+      ::tobk::note_launch(), k_rr_oa_products<<<m, 64, 0, st>>>(h->Hs, mmax, xin, m, rrS, rrR);
+      ::tobk::note_launch(), k_rr_oa_update<<<last ? nvec : m, 64, 0, st>>>(xin, rrS, rrR, m, xout, last ? mmax : m,
+                                                                           last ? rrLam : nullptr, rrDelta, step == 0);
+    }
     ::tobk::note_launch(), k_rr_finish<<<1, 256, rr_finish_smem_bytes(m, nvec), st>>>(
         h->Hs, mmax, m, nvec, rrXw, mmax, rrLam, rrDelta, theta, h->Ys, mmax);
     prof_end(h);

@@ -1083,12 +1083,24 @@ __global__ void k_gram_partial(const double* __restrict__ A, int na, const doubl
   }
 }
 
-__global__ void k_gram_final(const double* __restrict__ partial, int nchunks, int nout, double* __restrict__ C) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nout) return;
+// C[o] = sum over chunks of partial[c][o]: a block sums 32 consecutive outputs, its 8 warps take every
+// 8th chunk (coalesced over the outputs) and the 8 partial sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ partial, int nchunks, int nout,
+                                                    double* __restrict__ C) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * nout + t];
-  C[t] = s;
+  if (o < nout)
+    for (int c = w; c < nchunks; c += 8) s += partial[(size_t)c * nout + o];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && o < nout) {
+    double a = red[0][lane];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) a += red[k][lane];
+    C[o] = a;
+  }
 }
 
 int gram_partial_blocks(int64_t n) { return (int)((n + kGramChunk - 1) / kGramChunk); }
@@ -1103,7 +1115,7 @@ void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, in
     configured = true;
   }
   ::tobk::note_launch(), k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, partial);
-  ::tobk::note_launch(), k_gram_final<<<blocks_for((int64_t)na * nb), kThreads, 0, s>>>(partial, chunks, na * nb, C);
+  ::tobk::note_launch(), k_gram_final<<<(na * nb + 31) / 32, 256, 0, s>>>(partial, chunks, na * nb, C);
 }
 
 // Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j]; one thread per row index, up to 32 outputs per

@@ -106,6 +106,14 @@ __global__ void k_permute_scale(const double* A, const int* perm, const double* 
   B[(int64_t)r * stride + k] = scale[r] * A[(int64_t)perm[r] * stride + k];
 }
 
+// X[r] = s[r] A[r] for the q columns of length n.
+__global__ void k_scale_cols(const double* A, const double* s, double* X, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int r = blockIdx.y;
+  X[(int64_t)r * n + k] = s[r] * A[(int64_t)r * n + k];
+}
+
 __global__ void k_rq(const double* num, const double* den, int q, double* lam) {
   const int i = threadIdx.x;
   if (i < q) lam[i] = -num[i] / den[i];
@@ -165,12 +173,19 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
       cudaMemsetAsync(F.b, 0, sizeof(double) * q * F.g.n, st);
       launch_prolong_add(F.g, C.g, F.fixed, C.b, F.b, q, F.g.n, C.g.n, st);
     }
-    // step 3: K Phi = G Psi (one multi-RHS mgPCG solve on the fine grid)
+    // step 3: K Phi = G Psi (one multi-RHS mgPCG solve on the fine grid).  Initial guess
+    // Phi_0 = -Psi / lambda_c: (K + lambda_c G) Psi is the fine residual of the prolongated coarse
+    // pair, and with Galerkin coarse operators its restriction to Omega_l is the coarse eigen
+    // residual (1e-8), so the starting error has no component the coarse space represents.
     double* rhs = h->bwork;
     apply_G_level(h, 0, h->lv[0].b, rhs, q, n);
     double* Phi = h->xwork;
+    double s_h[64];
+    for (int i = 0; i < q; ++i) s_h[i] = (lam_h[i] > 0.0 && std::isfinite(lam_h[i])) ? -1.0 / lam_h[i] : 0.0;
+    cudaMemcpyAsync(den, s_h, sizeof(double) * q, cudaMemcpyHostToDevice, st);
+    ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), q), 256, 0, st>>>(h->lv[0].b, den, Phi, n);
     tobk_solve_info si{};
-    int src = pcg_solve(h, 0, rhs, Phi, q, h->desc.rtol, h->desc.max_iter, false, h->desc.precision, &si);
+    int src = pcg_solve(h, 0, rhs, Phi, q, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &si);
     if (src && src != TOBK_E_NOT_CONVERGED) return src;
     // step 4: Rayleigh quotients lambda_i = -phi^T K phi / phi^T G phi
     double* KP = h->lv[0].z;

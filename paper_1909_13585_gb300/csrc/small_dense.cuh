@@ -7,7 +7,7 @@
 // and FP64 accuracy is recovered by a refinement made only of matrix products, spread over one
 // thread block per column:
 //   1. k_rr_eig32 (one block): all m eigenvectors of H by cyclic Jacobi sweeps in FP32.
-//   2. two refinement steps in FP64 (Ogita & Aishima, "Iterative refinement for symmetric
+//   2. kRRRefineSteps refinement steps in FP64 (Ogita & Aishima, "Iterative refinement for symmetric
 //      eigenvalue decomposition", Japan J. Indust. Appl. Math. 35 (2018)): with X the current
 //      eigenvector matrix, R = I - X^T X, S = X^T H X, lambda_i = s_ii / (1 - r_ii),
 //      E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for i != j, E_ii = r_ii / 2, and
@@ -23,30 +23,42 @@
 namespace tobk {
 
 constexpr int kRRMax = 64;  // largest projected problem (the FP32 stage pads to it)
+// FP32 stage stopping rule: off-diagonal mass below this fraction of the total (off-diagonal entries
+// about 3e-6 of the norm); each of the kRRRefineSteps FP64 refinement steps then squares the error.
+constexpr double kRRJacobiTol2 = 1e-11;
+constexpr int kRRRefineSteps = 2;
+static_assert(kRRRefineSteps >= 2, "the eigensolver's warm start reads the first refined X");
 
 // Stage 1.  All m eigenvectors of H [m][ld] (symmetric part) in FP32 by cyclic Jacobi, written in
 // FP64 to X [m][m] (column c = eigenvector of the c-th largest eigenvalue).  The matrix is padded
-// to kRRMax = 64 rows (padding rows are never rotated); one round applies 32 disjoint rotations
-// J_k to C <- J C J^T as independent 2 x 2 blocks (one thread per pair of pairs), so a round costs
-// two barriers.  Warm start: when mprev > 0, Xp [mprev][mprev] (the previous eigenvectors of the
-// leading mprev x mprev block, FP64) starts the accumulated rotation V = diag(Xp, I), so that the
-// old block is already nearly diagonal.  info[0] = sweeps.
-__global__ void __launch_bounds__(1024) k_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev,
-                                                   double* X, double* info) {
-  constexpr int P = kRRMax;  // padded size (even)
+// to P (a multiple of 8, P >= m; padding rows are never rotated).  One round applies P/2 disjoint
+// rotations J_k (round-robin pairing) to C <- J C J^T as independent 2 x 2 blocks, one thread per
+// pair of pairs (warp A, lane B), so a round costs two barriers.  The rotations only steer the FP32
+// stage (the FP64 refinement below fixes the digits), so they use fast reciprocal / square-root
+// approximations.  Shared arrays have the odd row stride P + 1, so that row and column walks are
+// free of bank conflicts.  Warm start: when mprev > 0, Xp [mprev][mprev] (the previous eigenvectors
+// of the leading mprev x mprev block, FP64) starts the accumulated rotation V = diag(Xp, I), so that
+// the old block is already nearly diagonal.  info[0] = sweeps.
+template <int P>
+__global__ void __launch_bounds__(16 * P) k_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev,
+                                                     double* X, double* info, double tol2) {
+  static_assert(P % 8 == 0 && P <= kRRMax, "padded size");  // P % 8 == 0: NP * P is a multiple of 32
+  constexpr int NP = P / 2;    // rotations per round
+  constexpr int NT = 32 * NP;  // threads: warp A, lane B < NP owns the 2 x 2 block (A, B)
+  constexpr int LD = P + 1;
+  constexpr int SZ = P * LD;
   extern __shared__ float sm32[];
-  float* C = sm32;       // [P*P]
-  float* V = C + P * P;  // [P*P] accumulated rotations, transposed: V[col * P + row]
-  float* T = V + P * P;  // [P*P]
-  __shared__ float cs[P / 2], sn[P / 2];
-  __shared__ int pp[P / 2], qq[P / 2];
-  __shared__ unsigned char pair_tab[(P - 1) * P];  // round-robin pairing: round r, slot k -> (p, q)
-  __shared__ double red[64];
+  float* C = sm32;           // rotated matrix
+  float* V = sm32 + SZ;      // accumulated rotations, transposed: V[col * LD + row]
+  float* T = sm32 + 2 * SZ;  // set-up scratch
+  __shared__ float4 rot[NP];                       // (c, s, p, q) of the round's slots
+  __shared__ unsigned char pair_tab[(P - 1) * P];  // round r, slot k -> (p, q)
+  __shared__ double red[2 * (NT / 32)];
   __shared__ double hmax_s;
   __shared__ int done_s;
-  const int t = threadIdx.x;  // blockDim.x == 1024 == (P/2)^2
-  for (int q = t; q < (P - 1) * (P / 2); q += 1024) {
-    const int round = q / (P / 2), k = q % (P / 2);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int q = t; q < (P - 1) * NP; q += NT) {
+    const int round = q / NP, k = q % NP;
     int p, r;
     if (k == 0) {
       p = P - 1;
@@ -60,132 +72,158 @@ __global__ void __launch_bounds__(1024) k_rr_eig32(const double* H, int m, int l
   }
   // scale by max |H| so that the FP32 working range holds any problem scaling
   double mx = 0.0;
-  for (int q = t; q < m * m; q += 1024) mx = fmax(mx, fabs(H[(size_t)(q / m) * ld + q % m]));
+  for (int q = t; q < m * m; q += NT) mx = fmax(mx, fabs(H[(size_t)(q / m) * ld + q % m]));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((t & 31) == 0) red[t >> 5] = mx;
+  if (lane == 0) red[warp] = mx;
   __syncthreads();
   if (t == 0) {
     double a = 0.0;
-    for (int w = 0; w < 32; ++w) a = fmax(a, red[w]);
+    for (int w = 0; w < NT / 32; ++w) a = fmax(a, red[w]);
     hmax_s = a > 0.0 ? a : 1.0;
   }
   __syncthreads();
   const float inv = (float)(1.0 / hmax_s);
-  for (int q = t; q < P * P; q += 1024) {
-    const int i = q >> 6, j = q & (P - 1);
+  for (int q = t; q < P * P; q += NT) {
+    const int i = q / P, j = q % P;
     float h = 0.f, v = (i == j) ? 1.f : 0.f;
     if (i < m && j < m) h = inv * (float)(0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]));
     if (i < mprev && j < mprev) v = (float)Xp[(size_t)i * mprev + j];
-    T[q] = h;
-    V[j * P + i] = v;
+    C[i * LD + j] = h;
+    V[j * LD + i] = v;
   }
   __syncthreads();
-  if (mprev > 0) {  // C = V^T T V
-    for (int q = t; q < P * P; q += 1024) {  // C <- T V
-      const int i = q >> 6, j = q & (P - 1);
+  if (mprev > 0) {  // C <- V^T C V
+    for (int q = t; q < P * P; q += NT) {  // T <- C V
+      const int i = q / P, j = q % P;
       float a = 0.f;
-      for (int k = 0; k < P; ++k) a += T[i * P + k] * V[j * P + k];
-      C[q] = a;
+#pragma unroll 8
+      for (int k = 0; k < P; ++k) a += C[i * LD + k] * V[j * LD + k];
+      T[i * LD + j] = a;
     }
     __syncthreads();
-    for (int q = t; q < P * P; q += 1024) {  // T <- V^T C
-      const int i = q >> 6, j = q & (P - 1);
+    for (int q = t; q < P * P; q += NT) {  // C <- V^T T
+      const int i = q / P, j = q % P;
       float a = 0.f;
-      for (int k = 0; k < P; ++k) a += V[i * P + k] * C[k * P + j];
-      T[q] = a;
+#pragma unroll 8
+      for (int k = 0; k < P; ++k) a += V[i * LD + k] * T[k * LD + j];
+      C[i * LD + j] = a;
     }
     __syncthreads();
   }
-  for (int q = t; q < P * P; q += 1024) C[q] = T[q];
-  __syncthreads();
   int sweeps = 0;
   for (; sweeps < 30; ++sweeps) {
-    // convergence: off-diagonal mass below 1e-11 of the total (about 3e-6 relative)
+    // convergence: off-diagonal mass below tol2 of the total
     double o = 0.0, a = 0.0;
-    for (int q = t; q < P * P; q += 1024) {
-      const double v = (double)C[q] * (double)C[q];
+    for (int q = t; q < P * P; q += NT) {
+      const int i = q / P, j = q % P;
+      const double v = (double)C[i * LD + j] * (double)C[i * LD + j];
       a += v;
-      if ((q >> 6) != (q & (P - 1))) o += v;
+      if (i != j) o += v;
     }
     for (int s = 16; s > 0; s >>= 1) {
       o += __shfl_xor_sync(0xffffffffu, o, s);
       a += __shfl_xor_sync(0xffffffffu, a, s);
     }
-    if ((t & 31) == 0) {
-      red[2 * (t >> 5)] = o;
-      red[2 * (t >> 5) + 1] = a;
+    if (lane == 0) {
+      red[2 * warp] = o;
+      red[2 * warp + 1] = a;
     }
     __syncthreads();
     if (t == 0) {
       double oo = 0.0, aa = 0.0;
-      for (int w = 0; w < 32; ++w) {
+      for (int w = 0; w < NT / 32; ++w) {
         oo += red[2 * w];
         aa += red[2 * w + 1];
       }
-      done_s = !(oo > 1e-11 * aa);
+      done_s = !(oo > tol2 * aa);
     }
     __syncthreads();
     if (done_s) break;
     for (int round = 0; round < P - 1; ++round) {
-      if (t < P / 2) {  // rotation of pair slot t (round-robin pairing of P indices)
-        const int p = pair_tab[2 * (round * (P / 2) + t)], q = pair_tab[2 * (round * (P / 2) + t) + 1];
+      if (t < NP) {  // rotation of slot t
+        const int p = pair_tab[2 * (round * NP + t)], q = pair_tab[2 * (round * NP + t) + 1];
         float c = 1.f, s = 0.f;
-        if (p < m && q < m) {
-          const float apq = C[p * P + q];
-          if (apq != 0.f) {
-            const float tau = (C[q * P + q] - C[p * P + p]) / (2.f * apq);
-            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + tt * tt);
-            s = tt * c;
-          }
+        const float apq = C[p * LD + q];
+        if (p < m && q < m && apq != 0.f) {
+          const float tau = __fdividef(C[q * LD + q] - C[p * LD + p], 2.f * apq);
+          const float at = fabsf(tau);
+          // tan of the rotation angle, 1 / (|tau| + sqrt(1 + tau^2)), signed like tau
+          float tt = at < 1e18f ? __fdividef(1.f, at + (1.f + at * at) * rsqrtf(1.f + at * at)) : __fdividef(0.5f, at);
+          tt = tau >= 0.f ? tt : -tt;
+          c = rsqrtf(1.f + tt * tt);
+          s = tt * c;
         }
-        pp[t] = p;
-        qq[t] = q;
-        cs[t] = c;
-        sn[t] = s;
+        rot[t] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
       }
       __syncthreads();
-      {  // block (A, B) of pair slots: rows (p1, q1), columns (p2, q2): B' = J_A B J_B^T
-        const int A = t >> 5, Bs = t & 31;
-        const int p1 = pp[A], q1 = qq[A], p2 = pp[Bs], q2 = qq[Bs];
-        const float c1 = cs[A], s1 = sn[A], c2 = cs[Bs], s2 = sn[Bs];
-        const float b00 = C[p1 * P + p2], b01 = C[p1 * P + q2], b10 = C[q1 * P + p2], b11 = C[q1 * P + q2];
-        // left: rows p1, q1
-        const float l00 = c1 * b00 - s1 * b10, l01 = c1 * b01 - s1 * b11;
-        const float l10 = s1 * b00 + c1 * b10, l11 = s1 * b01 + c1 * b11;
-        // right: columns p2, q2
-        C[p1 * P + p2] = c2 * l00 - s2 * l01;
-        C[p1 * P + q2] = s2 * l00 + c2 * l01;
-        C[q1 * P + p2] = c2 * l10 - s2 * l11;
-        C[q1 * P + q2] = s2 * l10 + c2 * l11;
-        // accumulated rotation V <- V J^T: columns p, q of two pair slots, row t & 63
-        const int row = t & (P - 1);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = (t >> 6) + 16 * h;
-          const int p = pp[k], q = qq[k];
-          const float vp = V[p * P + row], vq = V[q * P + row];
-          V[p * P + row] = cs[k] * vp - sn[k] * vq;
-          V[q * P + row] = sn[k] * vp + cs[k] * vq;
-        }
+      if (lane < NP) {  // block (A, B): rows (p1, q1) of slot A = warp, columns (p2, q2) of slot B = lane
+        const float4 ra = rot[warp], rb = rot[lane];
+        const int p1 = __float_as_int(ra.z), q1 = __float_as_int(ra.w);
+        const int p2 = __float_as_int(rb.z), q2 = __float_as_int(rb.w);
+        const float b00 = C[p1 * LD + p2], b01 = C[p1 * LD + q2], b10 = C[q1 * LD + p2], b11 = C[q1 * LD + q2];
+        const float l00 = ra.x * b00 - ra.y * b10, l01 = ra.x * b01 - ra.y * b11;
+        const float l10 = ra.y * b00 + ra.x * b10, l11 = ra.y * b01 + ra.x * b11;
+        C[p1 * LD + p2] = rb.x * l00 - rb.y * l01;
+        C[p1 * LD + q2] = rb.y * l00 + rb.x * l01;
+        C[q1 * LD + p2] = rb.x * l10 - rb.y * l11;
+        C[q1 * LD + q2] = rb.y * l10 + rb.x * l11;
+      }
+      // accumulated rotation V <- V J^T: (slot k, row) items
+      for (int it = t; it < NP * P; it += NT) {
+        const int k = it / P, row = it % P;
+        const float4 rk = rot[k];
+        const int pk = __float_as_int(rk.z), qk = __float_as_int(rk.w);
+        const float vp = V[pk * LD + row], vq = V[qk * LD + row];
+        V[pk * LD + row] = rk.x * vp - rk.y * vq;
+        V[qk * LD + row] = rk.y * vp + rk.x * vq;
       }
       __syncthreads();
     }
   }
   // descending order of the diagonal (ties by index); padding rows excluded
-  for (int c = t; c < m; c += 1024) {
-    const float tc = C[c * P + c];
+  for (int c = t; c < m; c += NT) {
+    const float tc = C[c * LD + c];
     int rank = 0;
     for (int o = 0; o < m; ++o) {
-      const float to = C[o * P + o];
+      const float to = C[o * LD + o];
       if (to > tc || (to == tc && o < c)) ++rank;
     }
-    for (int i = 0; i < m; ++i) X[(size_t)i * m + rank] = (double)V[c * P + i];
+    for (int i = 0; i < m; ++i) X[(size_t)i * m + rank] = (double)V[c * LD + i];
   }
   if (t == 0) info[0] = (double)sweeps;
 }
 
-inline size_t rr_eig32_smem_bytes() { return sizeof(float) * 3 * (size_t)kRRMax * kRRMax; }
+template <int P>
+inline size_t rr_eig32_smem_bytes() {
+  return sizeof(float) * 3 * (size_t)P * (P + 1);
+}
+
+// Stage 1 launch: the smallest padded size (a multiple of 8) that holds m.
+template <int P>
+inline void rr_eig32_launch(const double* H, int m, int ld, const double* Xp, int mprev, double* X, double* info,
+                            double tol2, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_rr_eig32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_eig32_smem_bytes<P>());
+    configured = true;
+  }
+  k_rr_eig32<P><<<1, 16 * P, rr_eig32_smem_bytes<P>(), st>>>(H, m, ld, Xp, mprev, X, info, tol2);
+}
+
+inline void launch_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev, double* X, double* info,
+                            cudaStream_t st, double tol2 = kRRJacobiTol2) {
+  switch ((m + 7) / 8) {
+    case 0:
+    case 1:
+    case 2: rr_eig32_launch<16>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+    case 3: rr_eig32_launch<24>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+    case 4: rr_eig32_launch<32>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+    case 5: rr_eig32_launch<40>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+    case 6: rr_eig32_launch<48>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+    case 7: rr_eig32_launch<56>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+    default: rr_eig32_launch<64>(H, m, ld, Xp, mprev, X, info, tol2, st); break;
+  }
+}
 
 // Stage 2a.  S = X^T Hs X and R = I - X^T X ([m][m] each), Hs = (H + H^T)/2; block j computes
 // column j.
