@@ -55,7 +55,7 @@ typedef enum {
   TOBK_E_CUDA = 4,           /* a CUDA call failed; the message names it */
   TOBK_E_NOT_CONVERGED = 5,  /* iteration limit reached; outputs hold the last iterate */
   TOBK_E_BREAKDOWN = 6,      /* CG breakdown (p^T K p <= 0): K not positive definite on the free DOFs */
-  TOBK_E_TIMEOUT = 7,        /* reserved: bounded device wait expired */
+  TOBK_E_TIMEOUT = 7,        /* a bounded device wait expired (tensor-core inference) */
   TOBK_E_NONFINITE = 8       /* a NaN/Inf appeared in an iterate */
 } tobk_status;
 
@@ -288,8 +288,24 @@ int tobk_unet_design_scale(tobk_unet* net, const float* x, const double* f, doub
 int tobk_unet_get_state(tobk_unet* net, float* params, float* adam_m, float* adam_v, long long* step, int on_device);
 int tobk_unet_set_state(tobk_unet* net, const float* params, const float* adam_m, const float* adam_v, long long step,
                         int on_device);
-/* u0 [n] (FP64, zero at fixed DOFs) from x [m] (FP64), f [n] (FP64), fixed [n]. */
+/* u0 [n] (FP64, zero at fixed DOFs) from x [m] (FP64), f [n] (FP64), fixed [n].  With tensor cores
+ * enabled (the default) the 3x3x3 convolutions run as tcgen05 implicit GEMMs with the activations
+ * rounded to bfloat16 (FP32 accumulation); TOBK_E_TIMEOUT if one of their bounded device waits gave
+ * up (no output is valid then). */
 int tobk_unet_predict(tobk_unet* net, const double* x, const double* f, const uint8_t* fixed, double* u0);
+/* Selects the inference convolutions: enable != 0 tensor cores (tcgen05, BF16 operands), 0 the FP32
+ * direct convolution that training uses.  Layers whose output channels are not 16, 32, 64 or 128
+ * always use the direct convolution. */
+int tobk_unet_set_tensor_cores(tobk_unet* net, int enable);
+/* One 3x3x3 convolution on the tensor cores (the kernel of tobk_unet_predict), for unit tests:
+ * out[co][z][y][x] = bias[co] + sum_ci sum_tap w[co][ci][tap] bf16(in[ci][(z,y,x) + tap]) with zero
+ * padding, taps ordered (dz, dy, dx) in {-1,0,1}^3 with dx fastest, then max(0, .) if relu.
+ * in [Cin][D][H][W], out [Cout][D][H][W] (FP32, device), weight [Cout][Cin][27] and bias [Cout]
+ * (FP32, device; rounded to bfloat16; bias may be NULL).  Cout in {16, 32, 64, 128}; stream-ordered
+ * on cuda_stream and synchronised before return.  TOBK_E_ARG for unsupported shapes, TOBK_E_TIMEOUT
+ * if a bounded device wait gave up. */
+int tobk_conv3_bf16(const float* in, int Cin, int D, int H, int W, const float* weight, const float* bias, int Cout,
+                    int relu, float* out, void* cuda_stream);
 /* Loss of one sample (x [m] FP32, target solution [n] FP32) and its gradient grad [num_params]
  * (may be NULL). */
 int tobk_unet_loss_grad(tobk_unet* net, const float* x, const double* f, const float* target, const uint8_t* fixed,

@@ -194,24 +194,27 @@ def features(x, f, nel, penal=3.0, E0=1.0, Emin=1e-6):
     return feat, Ek.mean() / fmax
 
 
-def forward(theta, feat, levels, channels, bf16=True):
-    """Element output y [3][nz][ny][nx] and the cache for backward."""
+def forward(theta, feat, levels, channels, bf16=True, act_bf16=False):
+    """Element output y [3][nz][ny][nx] and the cache for backward.  act_bf16: the input of every
+    3x3x3 convolution is rounded to bfloat16 first (the operands of the tensor-core inference path;
+    the 1x1x1 heads keep their FP32 inputs)."""
     P = unpack(bf16_round(theta) if bf16 else np.asarray(theta, dtype=np.float64), levels, channels)
+    rq = (lambda a: bf16_round(a)) if act_bf16 else (lambda a: a)
     cache = {"in": [], "a": [], "e": [], "dpre": {}, "d": {}}
     h = feat
     for l in range(levels):
         if l > 0:
             h = avgpool(cache["e"][l - 1])
         cache["in"].append(h)
-        a = relu(conv3(h, *P[f"enc{l}a"]))
+        a = relu(conv3(rq(h), *P[f"enc{l}a"]))
         cache["a"].append(a)
-        cache["e"].append(relu(conv3(a, *P[f"enc{l}b"])))
+        cache["e"].append(relu(conv3(rq(a), *P[f"enc{l}b"])))
     d = cache["e"][levels - 1]
     for l in range(levels - 2, -1, -1):
         cat = np.concatenate([up(d), cache["e"][l]])
-        a = relu(conv3(cat, *P[f"dec{l}a"]))
+        a = relu(conv3(rq(cat), *P[f"dec{l}a"]))
         cache["dpre"][l] = (cat, a)
-        d = relu(conv3(a, *P[f"dec{l}b"]))
+        d = relu(conv3(rq(a), *P[f"dec{l}b"]))
         cache["d"][l] = d
     d0 = d if levels > 1 else cache["e"][0]
     cache["d0"] = d0
@@ -283,10 +286,10 @@ def gradient(theta, x, f, u, fixed, nel, levels, channels, penal=3.0, bf16=True,
     return value, flat
 
 
-def predict(theta, x, f, fixed, nel, levels, channels, penal=3.0, out_scale=1.0):
+def predict(theta, x, f, fixed, nel, levels, channels, penal=3.0, out_scale=1.0, act_bf16=False):
     """u0 [n] (node-interleaved, zero at fixed DOFs)."""
     feat, s = features(x, f, nel, penal)
-    y, _ = forward(theta, feat, levels, channels)
+    y, _ = forward(theta, feat, levels, channels, act_bf16=act_bf16)
     t, _ = node_average(y)
     u0 = out_scale * t.reshape(-1) / s
     u0[fixed == 1] = 0.0

@@ -78,6 +78,8 @@ _SIGS = {
     "tobk_unet_predict": (C.c_int, [_H, _P, _P, _P, _P]),
     "tobk_unet_loss_grad": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_float), _P]),
     "tobk_unet_train_step": (C.c_int, [_H, _P, _P, _P, _P, C.c_int, C.c_float, C.POINTER(C.c_float)]),
+    "tobk_unet_set_tensor_cores": (C.c_int, [_H, C.c_int]),
+    "tobk_conv3_bf16": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P, C.c_void_p]),
     "tobk_launch_count": (C.c_longlong, []),
     "tobk_profile_enable": (C.c_int, [_H, C.c_int]),
     "tobk_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
@@ -429,6 +431,10 @@ class UNet:
         self._check(self.lib.tobk_unet_set_state(self.h, pp, _ptr(m)[0] if m is not None else None,
                                                  _ptr(v)[0] if v is not None else None, step, dev))
 
+    def set_tensor_cores(self, enable=True):
+        """Inference convolutions on the tensor cores (default) or the FP32 direct convolution."""
+        self._check(self.lib.tobk_unet_set_tensor_cores(self.h, 1 if enable else 0))
+
     def predict(self, x, f, fixed, u0):
         self._check(self.lib.tobk_unet_predict(self.h, x.data_ptr(), f.data_ptr(), fixed.data_ptr(), u0.data_ptr()))
 
@@ -444,3 +450,17 @@ class UNet:
         self._check(self.lib.tobk_unet_train_step(self.h, x.data_ptr(), f.data_ptr(), target.data_ptr(),
                                                   fixed.data_ptr(), nbatch, lr, C.byref(loss)))
         return loss.value
+
+
+def conv3_bf16(inp, weight, bias, out, relu=True, stream=None):
+    """One 3x3x3 convolution on the tensor cores (tobk_conv3_bf16): inp [Cin][D][H][W], weight
+    [Cout][Cin][27], bias [Cout] (or None), out [Cout][D][H][W]; FP32 CUDA tensors."""
+    lib = load()
+    cin, D, H, W = inp.shape
+    cout = weight.shape[0]
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib.tobk_conv3_bf16(inp.data_ptr(), cin, D, H, W, weight.data_ptr(),
+                             bias.data_ptr() if bias is not None else None, cout, 1 if relu else 0, out.data_ptr(),
+                             C.c_void_p(s))
+    if rc != TOBK_OK:
+        raise TobkError(rc, "tobk_conv3_bf16 failed")

@@ -24,6 +24,9 @@
 // channels per block, input channels staged through shared memory 8 at a time (the backward data
 // pass is the same kernel with the weights read transposed and flipped); the weight gradient
 // reduces over voxel tiles per (16 x 16) channel block with one FP32 atomic add per weight and block.
+// Inference (predict) runs the 3x3x3 convolutions on the tensor cores by default (conv3_tc.cuh:
+// tcgen05 implicit GEMM, activations rounded to bfloat16 when staged, FP32 accumulation); training
+// keeps FP32 activations (the gradients are those of the FP32-activation network).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,6 +38,7 @@
 #include <vector>
 
 #include "../../include/tobk.h"
+#include "conv3_tc.cuh"
 #include "kernels.h"
 #include "tobk_internal.cuh"
 
@@ -512,6 +516,16 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// wt[(tap * cout + n) * Kp + k] = W[n][k][tap] (zero for k >= cin)
+__global__ void k_tc_weights(const __nv_bfloat16* __restrict__ W, int cout, int cin, int Kp,
+                             __nv_bfloat16* __restrict__ wt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)27 * cout * Kp) return;
+  const int k = (int)(i % Kp), n = (int)((i / Kp) % cout), tap = (int)(i / ((int64_t)Kp * cout));
+  wt[i] = k < cin ? W[((int64_t)n * cin + k) * 27 + tap] : __float2bfloat16(0.f);
+}
+
+
 uint64_t splitmix(uint64_t& s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -549,6 +563,10 @@ struct tobk_unet {
   float* host = nullptr;  // pinned scalars
   long long step = 0;
   float out_scale = 1.f;  // t = out_scale * (node average of the network output)
+  int tensor_cores = 1;   // inference convolutions on the tensor cores
+  __nv_bfloat16* wt = nullptr;  // 3x3x3 weights re-laid out for the tensor-core kernel [27][Cout][Kp]
+  std::vector<int64_t> wt_off;  // per layer offset into wt (-1: not a 3x3x3 layer)
+  unsigned* tc_err = nullptr;   // set by a tensor-core wait that gave up
   std::string err;
 };
 
@@ -565,9 +583,45 @@ int dec_a(const tobk_unet* u, int l) { return 2 * u->L + 2 * (u->L - 2 - l); }
 int head_i(const tobk_unet* u) { return (int)u->layers.size() - 2; }
 int chead_i(const tobk_unet* u) { return (int)u->layers.size() - 1; }
 
-void conv3_fwd(tobk_unet* u, int li, const float* in1, int C1, int up1, const float* in2, int C2, float* out,
-               const Dim3& d) {
+int kpad(int cin) { return (cin + 15) / 16 * 16; }
+
+bool tc_fits(int cout, int cin) {
+  return (cout == 16 || cout == 32 || cout == 64 || cout == 128) &&
+         tc::conv3_tc_smem(cout, kpad(cin)) <= (size_t)200 * 1024;
+}
+
+template <int N>
+void launch_conv3_tc(const tc::ConvTcArgs& a, cudaStream_t s) {
+  const size_t smem = tc::conv3_tc_smem(N, a.Kp);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaFuncSetAttribute(tc::k_conv3_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
+    configured = 200 * 1024;
+  }
+  note_launch();
+  tc::k_conv3_tc<N><<<(unsigned)((a.d.vox() + 127) / 128), 128, smem, s>>>(a);
+}
+
+void conv3_fwd_tc(tobk_unet* u, int li, const float* in1, int C1, int up1, const float* in2, int C2, float* out,
+                  const Dim3& d) {
   const auto& L = u->layers[li];
+  const tc::ConvTcArgs a{in1, nullptr, C1, up1, in2, C2, u->wt + u->wt_off[li], u->pb + L.b, out,
+                         tc::Dim3{d.D, d.H, d.W}, kpad(L.cin), 1, u->tc_err};
+  switch (L.cout) {
+    case 16: launch_conv3_tc<16>(a, u->stream); break;
+    case 32: launch_conv3_tc<32>(a, u->stream); break;
+    case 64: launch_conv3_tc<64>(a, u->stream); break;
+    default: launch_conv3_tc<128>(a, u->stream); break;
+  }
+}
+
+void conv3_fwd(tobk_unet* u, int li, const float* in1, int C1, int up1, const float* in2, int C2, float* out,
+               const Dim3& d, bool tensor_cores = false) {
+  const auto& L = u->layers[li];
+  if (tensor_cores && u->wt_off[li] >= 0) {
+    conv3_fwd_tc(u, li, in1, C1, up1, in2, C2, out, d);
+    return;
+  }
   const unsigned tiles = (unsigned)(((d.W + kTX - 1) / kTX) * ((d.H + kTY - 1) / kTY) * ((d.D + kTZ - 1) / kTZ));
   note_launch();
   k_conv3<<<dim3(tiles, (L.cout + kCOT - 1) / kCOT), 256, 0, u->stream>>>(in1, nullptr, C1, up1, in2, C2, u->pb + L.w, 0,
@@ -594,9 +648,17 @@ void conv3_wgrad(tobk_unet* u, int li, const float* g, const float* out, const f
       g, out, in1, C1, up1, in2, C2, u->g + L.w, u->g + L.b, L.cout, d);
 }
 
-void forward(tobk_unet* u) {
+void forward(tobk_unet* u, bool tensor_cores = false) {
   cudaStream_t s = u->stream;
   const int L = u->L;
+  if (tensor_cores)
+    for (size_t li = 0; li < u->layers.size(); ++li)
+      if (u->wt_off[li] >= 0) {
+        const auto& ly = u->layers[li];
+        const int64_t cnt = (int64_t)27 * ly.cout * kpad(ly.cin);
+        note_launch();
+        k_tc_weights<<<nb(cnt), 256, 0, s>>>(u->pb + ly.w, ly.cout, ly.cin, kpad(ly.cin), u->wt + u->wt_off[li]);
+      }
   for (int l = 0; l < L; ++l) {
     const Dim3& d = u->dims[l];
     const float* inp = u->feat;
@@ -607,14 +669,14 @@ void forward(tobk_unet* u) {
       inp = u->in[l];
       cin = u->c[l - 1];
     }
-    conv3_fwd(u, enc_a(u, l), inp, cin, 0, nullptr, 0, u->a[l], d);
-    conv3_fwd(u, enc_a(u, l) + 1, u->a[l], u->c[l], 0, nullptr, 0, u->e[l], d);
+    conv3_fwd(u, enc_a(u, l), inp, cin, 0, nullptr, 0, u->a[l], d, tensor_cores);
+    conv3_fwd(u, enc_a(u, l) + 1, u->a[l], u->c[l], 0, nullptr, 0, u->e[l], d, tensor_cores);
   }
   for (int l = L - 2; l >= 0; --l) {
     const Dim3& d = u->dims[l];
     const float* coarse = (l + 1 == L - 1) ? u->e[L - 1] : u->d[l + 1];
-    conv3_fwd(u, dec_a(u, l), coarse, u->c[l + 1], 1, u->e[l], u->c[l], u->da[l], d);
-    conv3_fwd(u, dec_a(u, l) + 1, u->da[l], u->c[l], 0, nullptr, 0, u->d[l], d);
+    conv3_fwd(u, dec_a(u, l), coarse, u->c[l + 1], 1, u->e[l], u->c[l], u->da[l], d, tensor_cores);
+    conv3_fwd(u, dec_a(u, l) + 1, u->da[l], u->c[l], 0, nullptr, 0, u->d[l], d, tensor_cores);
   }
   const float* d0 = L > 1 ? u->d[0] : u->e[0];
   const auto& H = u->layers[head_i(u)];
@@ -788,6 +850,19 @@ bool unet_layout(tobk_unet* u, Arena& a) {
   u->gscale = scal + 8;
   u->partial = a.take<double>(3 * ((3 * nnode + 255) / 256 + 1));
   got.push_back(u->partial);
+  int64_t nwt = 0;
+  u->wt_off.assign(u->layers.size(), -1);
+  for (size_t li = 0; li < u->layers.size(); ++li) {
+    const auto& ly = u->layers[li];
+    if (ly.taps == 27 && tc_fits(ly.cout, ly.cin)) {
+      u->wt_off[li] = nwt;
+      nwt += (int64_t)27 * ly.cout * kpad(ly.cin);
+    }
+  }
+  u->wt = a.take<__nv_bfloat16>(std::max<int64_t>(nwt, 8));
+  got.push_back(u->wt);
+  u->tc_err = a.take<unsigned>(4);
+  got.push_back(u->tc_err);
   if (a.base == nullptr) return true;
   for (void* p : got)
     if (p == nullptr) return false;
@@ -917,6 +992,52 @@ const char* tobk_unet_last_error(const tobk_unet* u) { return u ? u->err.c_str()
 
 int64_t tobk_unet_num_params(const tobk_unet* u) { return u ? u->np : -1; }
 
+int tobk_unet_set_tensor_cores(tobk_unet* u, int enable) {
+  if (!u) return TOBK_E_ARG;
+  u->tensor_cores = enable ? 1 : 0;
+  return TOBK_OK;
+}
+
+int tobk_conv3_bf16(const float* in, int Cin, int D, int H, int W, const float* weight, const float* bias,
+                    int Cout, int relu, float* out, void* cuda_stream) {
+  if (!in || !weight || !out || Cin <= 0 || D <= 0 || H <= 0 || W <= 0 || !tc_fits(Cout, Cin)) return TOBK_E_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int Kp = kpad(Cin);
+  const int64_t nw = (int64_t)Cout * Cin * 27, nwt = (int64_t)27 * Cout * Kp;
+  void* buf = nullptr;
+  const size_t bytes = sizeof(__nv_bfloat16) * (size_t)(nw + nwt + Cout + 8) + 64;
+  if (cudaMallocAsync(&buf, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return TOBK_E_NOMEM;
+  }
+  __nv_bfloat16* wb = (__nv_bfloat16*)buf;
+  __nv_bfloat16* wt = wb + ((nw + 7) / 8) * 8;
+  __nv_bfloat16* bb = wt + nwt;
+  unsigned* err = (unsigned*)(((uintptr_t)(bb + Cout) + 15) & ~(uintptr_t)15);
+  cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  note_launch();
+  k_to_bf16<<<nb(nw), 256, 0, s>>>(weight, wb, nw);
+  if (bias) {
+    note_launch();
+    k_to_bf16<<<nb(Cout), 256, 0, s>>>(bias, bb, Cout);
+  }
+  note_launch();
+  k_tc_weights<<<nb(nwt), 256, 0, s>>>(wb, Cout, Cin, Kp, wt);
+  const tc::ConvTcArgs a{in, nullptr, Cin, 0, nullptr, 0, wt, bias ? bb : nullptr, out, tc::Dim3{D, H, W}, Kp,
+                         relu ? 1 : 0, err};
+  switch (Cout) {
+    case 16: launch_conv3_tc<16>(a, s); break;
+    case 32: launch_conv3_tc<32>(a, s); break;
+    case 64: launch_conv3_tc<64>(a, s); break;
+    default: launch_conv3_tc<128>(a, s); break;
+  }
+  unsigned flag = 0;
+  cudaMemcpyAsync(&flag, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return TOBK_E_CUDA;
+  return flag ? TOBK_E_TIMEOUT : TOBK_OK;
+}
+
 int tobk_unet_set_output_scale(tobk_unet* u, double scale) {
   if (!u || !(scale > 0.0) || !std::isfinite(scale)) return TOBK_E_ARG;
   u->out_scale = (float)scale;
@@ -964,7 +1085,17 @@ int tobk_unet_set_state(tobk_unet* u, const float* params, const float* adam_m, 
 int tobk_unet_predict(tobk_unet* u, const double* x, const double* f, const uint8_t* fixed, double* u0) {
   if (!u || !x || !f || !fixed || !u0) return TOBK_E_ARG;
   features(u, nullptr, x, f);
-  forward(u);
+  forward(u, u->tensor_cores != 0);
+  if (u->tensor_cores) {
+    unsigned flag = 0;
+    cudaMemcpyAsync(u->host, u->tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, u->stream);
+    cudaStreamSynchronize(u->stream);
+    std::memcpy(&flag, u->host, sizeof(unsigned));
+    if (flag) {
+      cudaMemsetAsync(u->tc_err, 0, sizeof(unsigned), u->stream);
+      return ufail(u, TOBK_E_TIMEOUT, "predict: a tensor-core wait gave up");
+    }
+  }
   const Dim3& d0 = u->dims[0];
   const int64_t nnode = (int64_t)(d0.D + 1) * (d0.H + 1) * (d0.W + 1);
   note_launch();

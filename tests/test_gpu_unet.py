@@ -72,12 +72,46 @@ def test_loss_gradient_and_prediction_match_oracle(kind):
         a, b = gg[k:k + sz], go[k:k + sz]
         assert np.linalg.norm(a - b) <= 5e-3 * np.linalg.norm(b) + 1e-12, name
         k += sz
-    # prediction
+    # prediction with the FP32 direct convolution (the training forward)
     u0 = torch.zeros(p.num_dofs, dtype=torch.float64, device="cuda")
+    net.set_tensor_cores(False)
     net.predict(torch.from_numpy(p.x).cuda(), f, fx, u0)
     ref = ou.predict(theta.astype(np.float64), p.x, p.f, p.fixed, p.nel, LEVELS, list(CH), out_scale=c)
     assert np.abs(u0.cpu().numpy() - ref).max() <= 1e-4 * np.abs(ref).max()
+    # prediction on the tensor cores (tcgen05, activations rounded to bfloat16): against the oracle
+    # with the same roundings.  The two sides' FP32 / FP64 sums differ by ~1e-6, so an activation
+    # occasionally rounds to the neighbouring bfloat16 value (2^-8 relative) on one side only; those
+    # rare one-ulp differences, diluted over 27 Cin products per output, stay well below 3e-3.
+    net.set_tensor_cores(True)
+    u1 = torch.zeros(p.num_dofs, dtype=torch.float64, device="cuda")
+    net.predict(torch.from_numpy(p.x).cuda(), f, fx, u1)
+    ref_bf = ou.predict(theta.astype(np.float64), p.x, p.f, p.fixed, p.nel, LEVELS, list(CH), out_scale=c,
+                        act_bf16=True)
+    assert np.abs(u1.cpu().numpy() - ref_bf).max() <= 3e-3 * np.abs(ref_bf).max()
     net.close()
+
+
+@pytest.mark.parametrize("cin,cout,dims", [(16, 16, (5, 7, 37)), (4, 16, (3, 9, 20)), (48, 32, (6, 8, 38)),
+                                           (128, 64, (4, 6, 30)), (64, 128, (3, 4, 44))])
+def test_tensor_core_conv3_matches_oracle(cin, cout, dims):
+    """One 3x3x3 convolution on the tensor cores (tcgen05 implicit GEMM) against the oracle's direct
+    convolution, on bfloat16-representable inputs and weights, so that both sides multiply the same
+    numbers and differ only by FP32 accumulation (at most 27 * 128 products per output): several
+    128-voxel tiles with a ragged last tile, input channels padded to 16, and 16 to 128 outputs."""
+    torch, pkg = require_gpu()
+    rng = np.random.default_rng(cin * 1000 + cout)
+    D, H, W = dims
+    a = ou.bf16_round(rng.uniform(-1.0, 1.0, (cin, D, H, W)))
+    w = ou.bf16_round(rng.uniform(-0.2, 0.2, (cout, cin, 27)))
+    b = ou.bf16_round(rng.uniform(-0.1, 0.1, cout))
+    ref = ou.relu(ou.conv3(a, w, b))
+    out = torch.zeros((cout, D, H, W), dtype=torch.float32, device="cuda")
+    pkg.binding.conv3_bf16(torch.from_numpy(a.astype(np.float32)).cuda(),
+                           torch.from_numpy(w.astype(np.float32)).cuda(),
+                           torch.from_numpy(b.astype(np.float32)).cuda(), out, relu=True)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert (got[ref == 0.0] == 0.0).mean() > 0.99  # ReLU zeros where the exact result is negative
 
 
 def test_checkpoint_round_trip_and_adam_lowers_the_loss():

@@ -52,6 +52,19 @@ def test_bf16_rounding_is_round_to_nearest_even():
     assert abs(r[4] - 1e-3) <= 2 ** -8 * 1e-3
 
 
+def test_bf16_activations_change_the_prediction_by_bf16_rounding_only():
+    """act_bf16 rounds every 3x3x3 convolution input to bfloat16: the prediction moves by about the
+    bfloat16 resolution (2^-8 relative per operand), not more, and is not identical."""
+    L, ch = 2, [16, 16]
+    p = synthetic.cantilever_3d(8, 4, 4, seed=4, radius=1.5, volfrac=0.4, mg_levels=1, eig_level=1, num_modes=1)
+    rng = np.random.default_rng(7)
+    theta = 0.15 * rng.standard_normal(unet.num_params(L, ch))
+    a = unet.predict(theta, p.x, p.f, p.fixed, p.nel, L, ch, out_scale=10.0)
+    b = unet.predict(theta, p.x, p.f, p.fixed, p.nel, L, ch, out_scale=10.0, act_bf16=True)
+    d = np.abs(a - b).max() / np.abs(a).max()
+    assert 0.0 < d < 2e-2
+
+
 @pytest.mark.parametrize("loss", ["energy", "mse"])
 def test_gradient_matches_central_differences(loss):
     L, ch = 2, [2, 3]
