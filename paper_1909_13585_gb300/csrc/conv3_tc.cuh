@@ -213,5 +213,144 @@ __global__ void __launch_bounds__(128) k_conv3_tc(ConvTcArgs a) {
 
 inline size_t conv3_tc_smem(int N, int Kp) { return (size_t)(Kp / 8) * 2048 + (size_t)(Kp / 8) * N * 16; }
 
+// Row variant for grids whose x extent W is a multiple of 128: a CTA's 128 voxels are 128
+// consecutive x of one (y, z) line, so the activations of all 27 taps are rows of one halo slab
+// (3 planes x 3 lines x 130 x, zero outside the grid) staged once in the canonical layout, and the
+// A operand of tap (dz, dy, dx) is the slab seen from row ((dz + 1) 3 + dy + 1) 130 + dx + 1: a
+// descriptor offset, no copy.  The weights of all taps are staged once as well, and one thread
+// issues the 27 Kp / 16 MMAs back to back with a single commit.
+constexpr int kSlabRows = 9 * 130;
+
+__host__ __device__ inline size_t conv3_tc_row_smem(int N, int Kp) {
+  return (size_t)(Kp / 8) * kSlabRows * 16 + (size_t)27 * (Kp / 8) * N * 16;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_conv3_tc_row(ConvTcArgs a) {
+  static_assert(N == 16 || N == 32 || N == 64 || N == 128, "output channels");
+  constexpr int NCOL = N < 32 ? 32 : N;
+  constexpr uint32_t IDESC = idesc_bf16(N);
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int K8 = a.Kp / 8;
+  uint8_t* sS = smem;                                   // slab [K8][9 lines][130 x][16 B]
+  uint8_t* sB = smem + (size_t)K8 * kSlabRows * 16;     // weights [27][K8][N rows][16 B]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_s;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t V = a.d.vox();
+  const int tiles_x = a.d.W / 128;
+  const int64_t line = blockIdx.x / tiles_x;  // (z, y) line index
+  const int x0 = (int)(blockIdx.x % tiles_x) * 128;
+  const int y = (int)(line % a.d.H), z = (int)(line / a.d.H);
+  const Dim3 dc{a.d.D / 2, a.d.H / 2, a.d.W / 2};
+  const int Cin = a.C1 + a.C2;
+  const int64_t V1 = a.up1 ? dc.vox() : V;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                 "r"(NCOL)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // slab: row s = (l * 130 + xi), l = 3 (dz + 1) + (dy + 1), x = x0 + xi - 1
+  for (int q = t; q < K8 * kSlabRows; q += 128) {
+    const int s = q % kSlabRows, k8 = q / kSlabRows;
+    const int l = s / 130, xi = s % 130;
+    const int xx = x0 + xi - 1, yy = y + l % 3 - 1, zz = z + l / 3 - 1;
+    const bool in = xx >= 0 && xx < a.d.W && yy >= 0 && yy < a.d.H && zz >= 0 && zz < a.d.D;
+    int64_t i1 = 0, i2 = 0;
+    if (in) {
+      i2 = ((int64_t)zz * a.d.H + yy) * a.d.W + xx;
+      i1 = a.up1 ? ((int64_t)(zz >> 1) * dc.H + (yy >> 1)) * dc.W + (xx >> 1) : i2;
+    }
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      float f[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = k8 * 8 + e + h;
+        float v = 0.f;
+        if (in && c < Cin) {
+          if (c < a.C1) {
+            v = a.in1[(int64_t)c * V1 + i1];
+            if (a.mask1 && !(a.mask1[(int64_t)c * V1 + i1] > 0.f)) v = 0.f;
+          } else {
+            v = a.in2[(int64_t)(c - a.C1) * V + i2];
+          }
+        }
+        f[h] = v;
+      }
+      pk[e / 2] = pack_bf16(f[0], f[1]);
+    }
+    *reinterpret_cast<uint4*>(sS + ((size_t)k8 * kSlabRows + s) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+  for (int q = t; q < 27 * K8 * N; q += 128) {
+    const int n = q % N, k8 = (q / N) % K8, tap = q / (N * K8);
+    const uint4 w = *reinterpret_cast<const uint4*>(a.Wt + ((size_t)tap * N + n) * a.Kp + k8 * 8);
+    *reinterpret_cast<uint4*>(sB + (((size_t)tap * K8 + k8) * N + n) * 16) = w;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_s;
+  const uint32_t mb = smem_u32(&mbar);
+  if (t == 0) {
+    const uint32_t lbo_a = kSlabRows * 16, lbo_b = N * 16;
+    for (int tap = 0; tap < 27; ++tap) {
+      const int row0 = ((tap / 9) * 3 + (tap / 3) % 3) * 130 + tap % 3;
+      for (int j = 0; j < a.Kp / 16; ++j) {
+        const uint64_t ad = smem_desc(smem_u32(sS + ((size_t)(2 * j) * kSlabRows + row0) * 16), lbo_a, 128);
+        const uint64_t bd = smem_desc(smem_u32(sB + ((size_t)tap * K8 + 2 * j) * (N * 16)), lbo_b, 128);
+        const uint32_t acc = (tap > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+            : "memory");
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                 : "memory");
+  }
+  const bool w = mbar_wait(mb, 0);
+  if (!w) {
+    if (t == 0) atomicExch(a.err, 1u);
+    mbar_wait(mb, 0);  // one more bounded wait for the operations in flight
+  }
+  const bool ok = __syncthreads_and(w) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int64_t vrow = (line * a.d.W) + x0 + t;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + lane_base + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float v = __uint_as_float(r[i]) + (a.bias ? __bfloat162float(a.bias[c0 + i]) : 0.f);
+        if (a.relu) v = fmaxf(v, 0.f);
+        a.out[(int64_t)(c0 + i) * V + vrow] = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL) : "memory");
+}
+
 }  // namespace tc
 }  // namespace tobk

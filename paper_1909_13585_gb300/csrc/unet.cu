@@ -590,16 +590,22 @@ bool tc_fits(int cout, int cin) {
          tc::conv3_tc_smem(cout, kpad(cin)) <= (size_t)200 * 1024;
 }
 
+// the row variant (one halo slab per 128-voxel x run) when W is a multiple of 128 and its slab
+// fits, else the per-tap gather variant
 template <int N>
 void launch_conv3_tc(const tc::ConvTcArgs& a, cudaStream_t s) {
-  const size_t smem = tc::conv3_tc_smem(N, a.Kp);
-  static size_t configured = 0;
-  if (smem > configured) {
+  static bool configured = false;
+  if (!configured) {
     cudaFuncSetAttribute(tc::k_conv3_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
-    configured = 200 * 1024;
+    cudaFuncSetAttribute(tc::k_conv3_tc_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024));
+    configured = true;
   }
+  const unsigned grid = (unsigned)((a.d.vox() + 127) / 128);
   note_launch();
-  tc::k_conv3_tc<N><<<(unsigned)((a.d.vox() + 127) / 128), 128, smem, s>>>(a);
+  if (a.d.W % 128 == 0 && tc::conv3_tc_row_smem(N, a.Kp) <= (size_t)200 * 1024)
+    tc::k_conv3_tc_row<N><<<grid, 128, tc::conv3_tc_row_smem(N, a.Kp), s>>>(a);
+  else
+    tc::k_conv3_tc<N><<<grid, 128, tc::conv3_tc_smem(N, a.Kp), s>>>(a);
 }
 
 void conv3_fwd_tc(tobk_unet* u, int li, const float* in1, int C1, int up1, const float* in2, int C2, float* out,
