@@ -288,15 +288,16 @@ int tobk_unet_design_scale(tobk_unet* net, const float* x, const double* f, doub
 int tobk_unet_get_state(tobk_unet* net, float* params, float* adam_m, float* adam_v, long long* step, int on_device);
 int tobk_unet_set_state(tobk_unet* net, const float* params, const float* adam_m, const float* adam_v, long long step,
                         int on_device);
-/* u0 [n] (FP64, zero at fixed DOFs) from x [m] (FP64), f [n] (FP64), fixed [n].  With tensor cores
- * enabled (the default) the 3x3x3 convolutions run as tcgen05 implicit GEMMs with the activations
- * rounded to bfloat16 (FP32 accumulation); TOBK_E_TIMEOUT if one of their bounded device waits gave
- * up (no output is valid then). */
+/* u0 [n] (FP64, zero at fixed DOFs) from x [m] (FP64), f [n] (FP64), fixed [n].  3x3x3 convolutions
+ * that run on the tensor cores (see tobk_unet_set_tensor_cores) are tcgen05 implicit GEMMs with the
+ * activations rounded to bfloat16 (FP32 accumulation); TOBK_E_TIMEOUT if one of their bounded
+ * device waits gave up (no output is valid then). */
 int tobk_unet_predict(tobk_unet* net, const double* x, const double* f, const uint8_t* fixed, double* u0);
-/* Selects the inference convolutions: enable != 0 tensor cores (tcgen05, BF16 operands), 0 the FP32
- * direct convolution that training uses.  Layers whose output channels are not 16, 32, 64 or 128
- * always use the direct convolution. */
-int tobk_unet_set_tensor_cores(tobk_unet* net, int enable);
+/* Selects the inference convolutions: mode 0 the FP32 direct convolution that training uses; 1 (the
+ * default) the tensor cores on levels of at least 128 * 2 * 152 voxels (two 128-voxel tiles per
+ * SM; smaller levels stay direct, which is faster there); 2 the tensor cores on every level.
+ * Layers whose output channels are not 16, 32, 64 or 128 always use the direct convolution. */
+int tobk_unet_set_tensor_cores(tobk_unet* net, int mode);
 /* One 3x3x3 convolution on the tensor cores (the kernel of tobk_unet_predict), for unit tests:
  * out[co][z][y][x] = bias[co] + sum_ci sum_tap w[co][ci][tap] bf16(in[ci][(z,y,x) + tap]) with zero
  * padding, taps ordered (dz, dy, dx) in {-1,0,1}^3 with dx fastest, then max(0, .) if relu.

@@ -431,9 +431,10 @@ class UNet:
         self._check(self.lib.tobk_unet_set_state(self.h, pp, _ptr(m)[0] if m is not None else None,
                                                  _ptr(v)[0] if v is not None else None, step, dev))
 
-    def set_tensor_cores(self, enable=True):
-        """Inference convolutions on the tensor cores (default) or the FP32 direct convolution."""
-        self._check(self.lib.tobk_unet_set_tensor_cores(self.h, 1 if enable else 0))
+    def set_tensor_cores(self, mode=1):
+        """Inference convolutions: 0 / False the FP32 direct convolution, 1 / True the tensor cores on
+        large levels (default), 2 the tensor cores on every level."""
+        self._check(self.lib.tobk_unet_set_tensor_cores(self.h, int(mode)))
 
     def predict(self, x, f, fixed, u0):
         self._check(self.lib.tobk_unet_predict(self.h, x.data_ptr(), f.data_ptr(), fixed.data_ptr(), u0.data_ptr()))

@@ -255,38 +255,75 @@ __global__ void __launch_bounds__(128) k_conv3_tc_row(ConvTcArgs a) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // slab: row s = (l * 130 + xi), l = 3 (dz + 1) + (dy + 1), x = x0 + xi - 1
-  for (int q = t; q < K8 * kSlabRows; q += 128) {
-    const int s = q % kSlabRows, k8 = q / kSlabRows;
-    const int l = s / 130, xi = s % 130;
-    const int xx = x0 + xi - 1, yy = y + l % 3 - 1, zz = z + l / 3 - 1;
-    const bool in = xx >= 0 && xx < a.d.W && yy >= 0 && yy < a.d.H && zz >= 0 && zz < a.d.D;
-    int64_t i1 = 0, i2 = 0;
-    if (in) {
-      i2 = ((int64_t)zz * a.d.H + yy) * a.d.W + xx;
-      i1 = a.up1 ? ((int64_t)(zz >> 1) * dc.H + (yy >> 1)) * dc.W + (xx >> 1) : i2;
-    }
-    uint32_t pk[4];
+  // slab: row s = (l * 130 + xi), l = 3 (dz + 1) + (dy + 1), x = x0 + xi - 1.  Work item = (8-channel
+  // block k8, line l, group g): g < 32 stages the 4 interior rows xi = 1 + 4g .. 4 + 4g from one
+  // float4 (float2 when upsampled) per channel, g = 32 and 33 the edge rows xi = 0 and 129.
+  for (int q = t; q < K8 * 9 * 34; q += 128) {
+    const int g = q % 34, l = (q / 34) % 9, k8 = q / (34 * 9);
+    const int yy = y + l % 3 - 1, zz = z + l / 3 - 1;
+    const bool line_in = yy >= 0 && yy < a.d.H && zz >= 0 && zz < a.d.D;
+    const int64_t base2 = ((int64_t)zz * a.d.H + yy) * a.d.W;                 // full-resolution line
+    const int64_t base1 = a.up1 ? ((int64_t)(zz >> 1) * dc.H + (yy >> 1)) * dc.W : base2;
+    if (g < 32) {
+      const int xx = x0 + 4 * g;  // 4 interior voxels, all inside the line
+      float f[4][8];
 #pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      float f[2];
+      for (int e = 0; e < 8; ++e) {
+        const int c = k8 * 8 + e;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (line_in && c < Cin) {
+          if (c < a.C1) {
+            if (a.up1) {
+              const float2 h = __ldg(reinterpret_cast<const float2*>(a.in1 + (int64_t)c * V1 + base1 + (xx >> 1)));
+              v = make_float4(h.x, h.x, h.y, h.y);
+              if (a.mask1) {
+                const float2 m = __ldg(reinterpret_cast<const float2*>(a.mask1 + (int64_t)c * V1 + base1 + (xx >> 1)));
+                if (!(m.x > 0.f)) v.x = v.y = 0.f;
+                if (!(m.y > 0.f)) v.z = v.w = 0.f;
+              }
+            } else {
+              v = __ldg(reinterpret_cast<const float4*>(a.in1 + (int64_t)c * V1 + base1 + xx));
+              if (a.mask1) {
+                const float4 m = __ldg(reinterpret_cast<const float4*>(a.mask1 + (int64_t)c * V1 + base1 + xx));
+                if (!(m.x > 0.f)) v.x = 0.f;
+                if (!(m.y > 0.f)) v.y = 0.f;
+                if (!(m.z > 0.f)) v.z = 0.f;
+                if (!(m.w > 0.f)) v.w = 0.f;
+              }
+            }
+          } else {
+            v = __ldg(reinterpret_cast<const float4*>(a.in2 + (int64_t)(c - a.C1) * V + base2 + xx));
+          }
+        }
+        f[0][e] = v.x, f[1][e] = v.y, f[2][e] = v.z, f[3][e] = v.w;
+      }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = k8 * 8 + e + h;
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<uint4*>(sS + ((size_t)k8 * kSlabRows + l * 130 + 1 + 4 * g + i) * 16) =
+            make_uint4(pack_bf16(f[i][0], f[i][1]), pack_bf16(f[i][2], f[i][3]), pack_bf16(f[i][4], f[i][5]),
+                       pack_bf16(f[i][6], f[i][7]));
+    } else {
+      const int xi = g == 32 ? 0 : 129, xx = x0 + xi - 1;
+      const bool in = line_in && xx >= 0 && xx < a.d.W;
+      float f[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = k8 * 8 + e;
         float v = 0.f;
         if (in && c < Cin) {
           if (c < a.C1) {
-            v = a.in1[(int64_t)c * V1 + i1];
-            if (a.mask1 && !(a.mask1[(int64_t)c * V1 + i1] > 0.f)) v = 0.f;
+            const int64_t i1 = base1 + (a.up1 ? (xx >> 1) : xx);
+            v = __ldg(a.in1 + (int64_t)c * V1 + i1);
+            if (a.mask1 && !(__ldg(a.mask1 + (int64_t)c * V1 + i1) > 0.f)) v = 0.f;
           } else {
-            v = a.in2[(int64_t)(c - a.C1) * V + i2];
+            v = __ldg(a.in2 + (int64_t)(c - a.C1) * V + base2 + xx);
           }
         }
-        f[h] = v;
+        f[e] = v;
       }
-      pk[e / 2] = pack_bf16(f[0], f[1]);
+      *reinterpret_cast<uint4*>(sS + ((size_t)k8 * kSlabRows + l * 130 + xi) * 16) =
+          make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
     }
-    *reinterpret_cast<uint4*>(sS + ((size_t)k8 * kSlabRows + s) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
   for (int q = t; q < 27 * K8 * N; q += 128) {
     const int n = q % N, k8 = (q / N) % K8, tap = q / (N * K8);

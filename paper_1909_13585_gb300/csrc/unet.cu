@@ -563,7 +563,7 @@ struct tobk_unet {
   float* host = nullptr;  // pinned scalars
   long long step = 0;
   float out_scale = 1.f;  // t = out_scale * (node average of the network output)
-  int tensor_cores = 1;   // inference convolutions on the tensor cores
+  int tensor_cores = 1;   // inference convolutions: 0 direct, 1 tensor cores on large grids, 2 always
   __nv_bfloat16* wt = nullptr;  // 3x3x3 weights re-laid out for the tensor-core kernel [27][Cout][Kp]
   std::vector<int64_t> wt_off;  // per layer offset into wt (-1: not a 3x3x3 layer)
   unsigned* tc_err = nullptr;   // set by a tensor-core wait that gave up
@@ -624,7 +624,10 @@ void conv3_fwd_tc(tobk_unet* u, int li, const float* in1, int C1, int up1, const
 void conv3_fwd(tobk_unet* u, int li, const float* in1, int C1, int up1, const float* in2, int C2, float* out,
                const Dim3& d, bool tensor_cores = false) {
   const auto& L = u->layers[li];
-  if (tensor_cores && u->wt_off[li] >= 0) {
+  // the tensor-core kernels serialise 27 staged taps per 128-voxel tile: below ~2 tiles per SM the
+  // direct convolution (many more, smaller blocks) is faster, so mode 1 keeps it there
+  const bool big = d.vox() >= (int64_t)128 * 2 * 152;
+  if (tensor_cores && u->wt_off[li] >= 0 && (u->tensor_cores == 2 || big)) {
     conv3_fwd_tc(u, li, in1, C1, up1, in2, C2, out, d);
     return;
   }
@@ -998,9 +1001,9 @@ const char* tobk_unet_last_error(const tobk_unet* u) { return u ? u->err.c_str()
 
 int64_t tobk_unet_num_params(const tobk_unet* u) { return u ? u->np : -1; }
 
-int tobk_unet_set_tensor_cores(tobk_unet* u, int enable) {
-  if (!u) return TOBK_E_ARG;
-  u->tensor_cores = enable ? 1 : 0;
+int tobk_unet_set_tensor_cores(tobk_unet* u, int mode) {
+  if (!u || mode < 0 || mode > 2) return TOBK_E_ARG;
+  u->tensor_cores = mode;
   return TOBK_OK;
 }
 

@@ -80,7 +80,7 @@ def test_loss_gradient_and_prediction_match_oracle(kind):
     assert np.abs(u0.cpu().numpy() - ref).max() <= 1e-4 * np.abs(ref).max()
     # prediction on the tensor cores (tcgen05, activations rounded to bfloat16): against the oracle
     # with the same roundings
-    net.set_tensor_cores(True)
+    net.set_tensor_cores(2)  # every level (this grid is below the size where mode 1 would use them)
     u1 = torch.zeros(p.num_dofs, dtype=torch.float64, device="cuda")
     net.predict(torch.from_numpy(p.x).cuda(), f, fx, u1)
     ref_bf = ou.predict(theta.astype(np.float64), p.x, p.f, p.fixed, p.nel, LEVELS, list(CH), out_scale=c,
@@ -172,6 +172,7 @@ def test_tensor_core_prediction_on_128_wide_grid():
     theta = _theta(net.num_params, seed=9, scale=0.06)  # a gain of about one per layer, as after training
     net.set_state(torch.from_numpy(theta).cuda())
     net.set_output_scale(20.0)
+    net.set_tensor_cores(2)
     x = torch.from_numpy(p.x).cuda()
     f = torch.from_numpy(p.f).cuda()
     fx = torch.from_numpy(p.fixed.astype(np.uint8)).cuda()
