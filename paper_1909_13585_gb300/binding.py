@@ -132,6 +132,17 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _arr(a, kind):
+    """(pointer, on_device, element count) of a contiguous array of the element type the C-ABI
+    expects: kind "f64" (densities, loads, displacements) or "u8" (fixed-DOF masks)."""
+    ok = {"f64": ("float64",), "u8": ("uint8", "bool")}[kind]
+    name = str(a.dtype).replace("torch.", "")
+    if name not in ok:
+        raise TypeError(f"expected {kind} data, got {a.dtype}")
+    ptr, dev = _ptr(a)
+    return ptr, dev, int(a.size if isinstance(a, np.ndarray) else a.numel())
+
+
 class Solver:
     """Owner of one tobk handle.  Arrays may be numpy (host) or torch tensors (host or device).
 
@@ -196,23 +207,23 @@ class Solver:
         self.set_densities(np.ascontiguousarray(p.x, dtype=np.float64))
 
     def set_densities(self, x):
-        ptr, dev = _ptr(x)
-        self._check(self.lib.tobk_set_densities(self.h, ptr, self.m, dev))
+        ptr, dev, cnt = _arr(x, "f64")
+        self._check(self.lib.tobk_set_densities(self.h, ptr, cnt, dev))
 
     def set_load(self, f):
-        ptr, dev = _ptr(f)
-        self._check(self.lib.tobk_set_load(self.h, ptr, self.n, dev))
+        ptr, dev, cnt = _arr(f, "f64")
+        self._check(self.lib.tobk_set_load(self.h, ptr, cnt, dev))
 
     def set_fixed(self, fixed):
-        ptr, dev = _ptr(fixed)
-        self._check(self.lib.tobk_set_fixed(self.h, ptr, self.n, dev))
+        ptr, dev, cnt = _arr(fixed, "u8")
+        self._check(self.lib.tobk_set_fixed(self.h, ptr, cnt, dev))
 
     def set_initial_guess(self, u0):
         if u0 is None:
             self._check(self.lib.tobk_set_initial_guess(self.h, None, 0, 0))
             return
-        ptr, dev = _ptr(u0)
-        self._check(self.lib.tobk_set_initial_guess(self.h, ptr, self.n, dev))
+        ptr, dev, cnt = _arr(u0, "f64")
+        self._check(self.lib.tobk_set_initial_guess(self.h, ptr, cnt, dev))
 
     # -- the method ------------------------------------------------------------------------------
     def solve_equilibrium(self, allow_not_converged=False):

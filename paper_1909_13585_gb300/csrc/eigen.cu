@@ -56,7 +56,7 @@ __global__ void k_scatter_sym(const double* C, int rows, int cols, int col0, dou
 }
 
 // Cholesky M = R^T R of a small SPD matrix (k <= 32) and Rinv = R^{-1} (upper triangular).
-// info[0] = 0 on success, 1 when a pivot is not positive.
+// info[0] is set to 1 when a pivot is not positive (and left unchanged otherwise).
 __global__ void k_small_cholinv(const double* M, int k, double* Rinv, double* info) {
   __shared__ double L[32 * 32];
   __shared__ double Li[32 * 32];
@@ -101,7 +101,7 @@ __global__ void k_small_cholinv(const double* M, int k, double* Rinv, double* in
     const int i = q / k, j = q % k;
     Rinv[q] = Li[j * k + i];
   }
-  if (t == 0) info[0] = bad ? 1.0 : 0.0;
+  if (t == 0 && bad) info[0] = 1.0;
 }
 
 // Column-wise dot products out[i] = sum_k A_i[k] B_i[k] (two stage, deterministic).
@@ -211,6 +211,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   double* rrLam = rrXw + (size_t)mmax * mmax;
   double* rrDelta = rrLam + mmax;
   int rr_prev = 0;  // size of the previous projected problem whose eigenvectors are in rrX1 (0: none)
+  cudaMemsetAsync(sinfo, 0, sizeof(double), st);  // Cholesky breakdown flag (sticky)
   const bool trace = std::getenv("TOBK_EIG_TRACE") != nullptr;
   int rc = TOBK_OK;
   for (it = 0; it < h->desc.eig_max_iter; ++it) {
@@ -280,6 +281,11 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     cudaStreamSynchronize(st);
     rc = check_cuda(h, "eigen_solve");
     if (rc) break;
+    if (h->hscal[384] != 0.0) {  // the K-orthonormalised expansion lost rank
+      rc = fail(h, TOBK_E_BREAKDOWN,
+                "eigensolver basis lost rank (the level has too few free DOFs for the block of q + 4 vectors)");
+      break;
+    }
     for (int i = 0; i < kk; ++i) hth[i] = h->hscal[i];
     if (trace)
       std::fprintf(stderr, "[tobk eig] level %d it %d m %d nadd %d theta0 %.9e thetaq %.9e fp32 sweeps %g\n", j, it, m,
