@@ -361,6 +361,26 @@ def roofline(prof, p, peaks, precision):
 
 
 # ------------------------------------------------------------------------------------------------
+# multi-rank aggregation (one process per GPU; each rank solves its own replica of the workload)
+# ------------------------------------------------------------------------------------------------
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks (the job's time is its slowest rank's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step, steps, world, max_ms):
+    """Whole-job units per second: every rank processes units_per_step in each of `steps` steps
+    (weak scaling), and the job takes its slowest rank's max_ms."""
+    return world * units_per_step * steps / (max_ms / 1e3)
+
+
+# ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
 def ours(args):
@@ -432,13 +452,8 @@ def ours(args):
     barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * units * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = job_throughput(units, args.steps, world, total_ms)
 
     # per-phase times and kernel-class profile over K more steps (profiling on)
     phases = {}
@@ -478,8 +493,8 @@ def ours(args):
             ev[k][1].record(stream)
             lam_sum += float(lam[0]) + J
         torch.cuda.synchronize()
-        e2e_ms = sum(a.elapsed_time(b) for a, b in ev)
-        e2e = {"value": world * units * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+        e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+        e2e = {"value": job_throughput(units, args.steps, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": 8 * m + 8 * n + n, "d2h_bytes_per_step": 8 * q + 8 * q * m + 8 * m + 8}
 
     forms = {}
