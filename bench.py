@@ -327,15 +327,24 @@ Q4_FP64_OPS_PER_NODE = {"fine_smooth": 41 + 6 + 10, "fine_residual": 41 + 6 + 2,
 FP64_OPS_PEAK_G = 152 * 2 * 2.070
 
 
+# kernel classes of the library's profiler that are one kernel each (the fine-level operator in its
+# three modes); the others (coarse levels, transfers, vector and eigensolver kernels) aggregate
+# several different kernels and are reported by class only
+SINGLE_KERNEL_CLASSES = ("fine_smooth", "fine_residual", "fine_cg_matvec")
+
+
 def roofline(prof, p, peaks, precision):
-    """Roofline of the dominant kernel class (most device time): achieved = algorithmic work per
-    launch (from the DOF x RHS the class processed) / average launch time (CUDA events on the
-    solver's stream)."""
-    name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    """Roofline of the dominant kernel (the single-kernel class with the most device time):
+    achieved = algorithmic work per launch (from the DOF x RHS the class processed) / average launch
+    time (CUDA events on the solver's stream)."""
+    name, rec = max(((k, v) for k, v in prof.items() if k in SINGLE_KERNEL_CLASSES), key=lambda kv: kv[1]["ms"])
     m, n, nnode = p.num_elements, p.num_dofs, p.num_nodes
     launches = max(rec["launches"], 1)
     per_launch_s = 1e-3 * rec["ms"] / launches
-    out = {"kernel_class": name, "launches": rec["launches"], "avg_launch_us": 1e6 * per_launch_s}
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    out = {"kernel_class": name, "launches": rec["launches"], "avg_launch_us": 1e6 * per_launch_s,
+           "share_of_class_time": rec["ms"] / sum(v["ms"] for v in prof.values()),
+           "largest_class": {"name": top[0], "ms": top[1]["ms"], "launches": top[1]["launches"]}}
     hbm = peaks.get("hbm_gbs", 6792.7)
     if name in Q4_FP64_OPS_PER_NODE and p.dim == 2 and precision == "fp64":
         rhs_per_launch = rec["dof_rhs"] / n / launches

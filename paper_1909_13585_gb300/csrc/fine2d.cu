@@ -1,6 +1,7 @@
 // Fine-level (matrix-free) Q4 operator in factored form (q4_element.cuh), element by element on
-// shared-memory tiles: a block computes the elements around a 32 x 8 tile of nodes once, stores
-// their nodal forces in shared memory and gathers the four contributions of each node.  On GB300,
+// shared-memory tiles: a block computes the 32 x 8 elements around a 31 x 7 tile of nodes once (one
+// element per thread, so the FP64-bound force phase is a single full round), stores their nodal
+// forces in shared memory and gathers the four contributions of each node.  On GB300,
 // where FP64 runs at 2 FMA/clk/SM, the FP64 fine-level smoother is bound by the element's
 // arithmetic, so the ~41 operations of the factored form (against 64 multiply-adds for the dense
 // 8 x 8 product) set its speed.
@@ -13,7 +14,9 @@
 namespace tobk {
 
 namespace {
-constexpr int TX = 32, TY = 8;
+constexpr int TX = 31, TY = 7;  // node tile; (TX + 1) (TY + 1) = 256 elements = one per thread
+constexpr int kThreadsQ4 = 256;
+static_assert((TX + 1) * (TY + 1) == kThreadsQ4, "one element per thread");
 constexpr int EX = TX + 1, EY = TY + 1;  // element tile
 constexpr int NX = TX + 2, NY = TY + 2;  // node tile
 }  // namespace
@@ -23,7 +26,7 @@ template <typename T>
 __device__ __forceinline__ void q4_tile_forces(const Grid& g, const T* __restrict__ Ek, const Q4Consts<T>& cst, int x0,
                                                int y0, const T (&su)[NY][NX], const T (&sv)[NY][NX],
                                                T (&fe)[EY][EX][8]) {
-  for (int q = threadIdx.x; q < EX * EY; q += TX * TY) {
+  for (int q = threadIdx.x; q < EX * EY; q += kThreadsQ4) {
     const int lx = q % EX, ly = q / EX;
     const int ex = x0 - 1 + lx, ey = y0 - 1 + ly;
     T f[8];
@@ -40,7 +43,7 @@ __device__ __forceinline__ void q4_tile_forces(const Grid& g, const T* __restric
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(TX* TY) k_fine_q4(Grid g, const T* __restrict__ Ek, const uint8_t* __restrict__ fixed,
+__global__ void __launch_bounds__(kThreadsQ4) k_fine_q4(Grid g, const T* __restrict__ Ek, const uint8_t* __restrict__ fixed,
                                                     Q4Consts<T> cst, const T* __restrict__ v, const T* __restrict__ b,
                                                     const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
                                                     int64_t stride, const double* __restrict__ act) {
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(TX* TY) k_fine_q4(Grid g, const T* __restrict_
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nnx = g.nn[0], nny = g.nn[1];
   const int64_t off = (int64_t)rhs * stride;
-  for (int q = tid; q < NX * NY; q += TX * TY) {
+  for (int q = tid; q < NX * NY; q += kThreadsQ4) {
     const int lx = q % NX, ly = q / NX;
     const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
     T a = T(0), c = T(0);
@@ -67,9 +70,9 @@ __global__ void __launch_bounds__(TX* TY) k_fine_q4(Grid g, const T* __restrict_
   __syncthreads();
   q4_tile_forces<T>(g, Ek, cst, x0, y0, su, sv, fe);
   __syncthreads();
-  const int tx = tid % TX, ty = tid / TX;
+  const int tx = tid % TX, ty = tid / TX;  // threads TX * TY .. 255 only computed elements
   const int X = x0 + tx, Y = y0 + ty;
-  if (X >= nnx || Y >= nny) return;
+  if (tid >= TX * TY || X >= nnx || Y >= nny) return;
   // elements around node (X, Y): (X-1,Y-1) local node 2, (X,Y-1) node 3, (X-1,Y) node 1, (X,Y) node 0
   const T fx = fe[ty][tx][4] + fe[ty][tx + 1][6] + fe[ty + 1][tx][2] + fe[ty + 1][tx + 1][0];
   const T fy = fe[ty][tx][5] + fe[ty][tx + 1][7] + fe[ty + 1][tx][3] + fe[ty + 1][tx + 1][1];
@@ -105,11 +108,11 @@ void launch_fine_q4(const Grid& g, const T* Ek, const uint8_t* fixed, const doub
   const double* act = active_rhs();
   note_launch();
   if (mode == APPLY_KV)
-    k_fine_q4<T, APPLY_KV><<<grid, TX * TY, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+    k_fine_q4<T, APPLY_KV><<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
   else if (mode == APPLY_RES)
-    k_fine_q4<T, APPLY_RES><<<grid, TX * TY, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+    k_fine_q4<T, APPLY_RES><<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
   else
-    k_fine_q4<T, APPLY_JAC><<<grid, TX * TY, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+    k_fine_q4<T, APPLY_JAC><<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
 }
 
 template void launch_fine_q4<double>(const Grid&, const double*, const uint8_t*, const double*, int, const double*,
@@ -122,7 +125,7 @@ int64_t fine_q4_tiles(const Grid& g) { return (int64_t)((g.nn[0] + TX - 1) / TX)
 
 // CG direction on the fine level (FP64): p = z + beta p_old (zero at fixed DOFs), q = K p, and the
 // per-RHS reduction p.q -> sc[SC_PQ], alpha = (p.r) / (p.q) (last block of the RHS).
-__global__ void __launch_bounds__(TX* TY) k_fine_q4_cg_direction(Grid g, const double* __restrict__ Ek,
+__global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, const double* __restrict__ Ek,
                                                                  const uint8_t* __restrict__ fixed, Q4Consts<double> cst,
                                                                  const double* __restrict__ z,
                                                                  const double* __restrict__ p_old,
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(TX* TY) k_fine_q4_cg_direction(Grid g, const d
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nnx = g.nn[0], nny = g.nn[1];
   const int64_t off = (int64_t)rhs * stride;
-  for (int t = tid; t < NX * NY; t += TX * TY) {
+  for (int t = tid; t < NX * NY; t += kThreadsQ4) {
     const int lx = t % NX, ly = t / NX;
     const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
     double a = 0.0, c = 0.0;
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(TX* TY) k_fine_q4_cg_direction(Grid g, const d
   const int tx = tid % TX, ty = tid / TX;
   const int X = x0 + tx, Y = y0 + ty;
   double v[1] = {0.0};
-  if (X < nnx && Y < nny) {
+  if (tid < TX * TY && X < nnx && Y < nny) {
     const double fx = fe[ty][tx][4] + fe[ty][tx + 1][6] + fe[ty + 1][tx][2] + fe[ty + 1][tx + 1][0];
     const double fy = fe[ty][tx][5] + fe[ty][tx + 1][7] + fe[ty + 1][tx][3] + fe[ty + 1][tx + 1][1];
     const int64_t idx = 2 * (X + (int64_t)nnx * Y);
@@ -193,8 +196,8 @@ void launch_fine_q4_cg_direction(const Grid& g, const double* Ek, const uint8_t*
   const Q4Consts<double> cst = q4_consts<double>(Ke0);
   dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)nr);
   note_launch();
-  k_fine_q4_cg_direction<<<grid, TX * TY, 0, s>>>(g, Ek, fixed, cst, z, p_old, p_new, q, stride, sc, partial, counters,
-                                                   pstride);
+  k_fine_q4_cg_direction<<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, z, p_old, p_new, q, stride, sc, partial, counters,
+                                                      pstride);
 }
 
 }  // namespace tobk
