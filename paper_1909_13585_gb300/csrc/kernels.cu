@@ -272,13 +272,17 @@ void launch_jacobi0_32(const float* b, const float* dinv, float* z, SmoothArgs<f
 // coupled with weight 1 when f = 2C and 1/2 when |f - 2C| = 1.
 template <int DIM, typename T>
 __global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c, const T* __restrict__ rf,
-                           T* __restrict__ bc, int64_t sf, int64_t sc, const double* __restrict__ act) {
+                           T* __restrict__ bc, int64_t sf, int64_t sc, const double* __restrict__ act,
+                           const T* __restrict__ dinv_c, const T* __restrict__ coef_c, T* __restrict__ zc,
+                           T* __restrict__ dc) {
   if (rhs_done(act)) return;
   const int64_t cn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int I, J, K;
   if (!node_coords(gc, cn, I, J, K)) return;
   rf += (int64_t)blockIdx.y * sf;
   bc += (int64_t)blockIdx.y * sc;
+  if (zc) zc += (int64_t)blockIdx.y * sc;
+  if (dc) dc += (int64_t)blockIdx.y * sc;
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
@@ -304,7 +308,13 @@ __global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const int64_t idx = DIM * cn + c;
-    bc[idx] = fixed_c[idx] ? T(0) : acc[c];
+    const T bi = fixed_c[idx] ? T(0) : acc[c];
+    bc[idx] = bi;
+    if (zc) {  // the coarse level's first smoothing step from z = 0 (k_jacobi0), fused
+      const T zi = coef_c[1] * dinv_c[idx] * bi;
+      zc[idx] = zi;
+      if (dc) dc[idx] = zi;
+    }
   }
 }
 
@@ -352,12 +362,14 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const uint8_t* __restrict__ fixe
 
 template <typename T>
 static void restrict_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const T* rf, T* bc, int nr,
-                          int64_t sf, int64_t sc, cudaStream_t s) {
+                          int64_t sf, int64_t sc, cudaStream_t s, const T* dinv_c, const T* coef_c, T* zc, T* dc) {
   dim3 grid(blocks_for(gc.nnode), nr);
   if (gf.dim == 2)
-    ::tobk::note_launch(), k_restrict<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs());
+    ::tobk::note_launch(), k_restrict<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs(),
+                                                                      dinv_c, coef_c, zc, dc);
   else
-    ::tobk::note_launch(), k_restrict<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs());
+    ::tobk::note_launch(), k_restrict<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs(),
+                                                                      dinv_c, coef_c, zc, dc);
 }
 template <typename T>
 static void prolong_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const T* zc, T* zf, int nr,
@@ -370,12 +382,14 @@ static void prolong_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f,
 }
 
 void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc, int nr,
-                     int64_t sf, int64_t sc, cudaStream_t s) {
-  restrict_impl<double>(gf, gc, fixed_c, rf, bc, nr, sf, sc, s);
+                     int64_t sf, int64_t sc, cudaStream_t s, const double* dinv_c, const double* coef_c, double* zc,
+                     double* dc) {
+  restrict_impl<double>(gf, gc, fixed_c, rf, bc, nr, sf, sc, s, dinv_c, coef_c, zc, dc);
 }
 void launch_restrict32(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const float* rf, float* bc, int nr,
-                       int64_t sf, int64_t sc, cudaStream_t s) {
-  restrict_impl<float>(gf, gc, fixed_c, rf, bc, nr, sf, sc, s);
+                       int64_t sf, int64_t sc, cudaStream_t s, const float* dinv_c, const float* coef_c, float* zc,
+                       float* dc) {
+  restrict_impl<float>(gf, gc, fixed_c, rf, bc, nr, sf, sc, s, dinv_c, coef_c, zc, dc);
 }
 void launch_prolong_add(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* zc, double* zf,
                         int nr, int64_t sf, int64_t sc, cudaStream_t s) {

@@ -68,11 +68,15 @@ void launch_jacobi0(const double* b, const double* dinv, double* z, SmoothArgs<d
                     int64_t stride, cudaStream_t s);
 void launch_jacobi0_32(const float* b, const float* dinv, float* z, SmoothArgs<float> sm, int64_t n, int nr,
                        int64_t stride, cudaStream_t s);
-// coarse b = P^T r_fine (masked); fine z += P z_coarse (masked)
+// coarse b = P^T r_fine (masked); fine z += P z_coarse (masked).  With zc != null the restriction
+// also takes the coarse level's first smoothing step from z = 0: zc = coef_c[1] dinv_c b (and dc = zc
+// when dc != null), the work of launch_jacobi0 on the coarse level.
 void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc,
-                     int nr, int64_t sf, int64_t sc, cudaStream_t s);
+                     int nr, int64_t sf, int64_t sc, cudaStream_t s, const double* dinv_c = nullptr,
+                     const double* coef_c = nullptr, double* zc = nullptr, double* dc = nullptr);
 void launch_restrict32(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const float* rf, float* bc,
-                       int nr, int64_t sf, int64_t sc, cudaStream_t s);
+                       int nr, int64_t sf, int64_t sc, cudaStream_t s, const float* dinv_c = nullptr,
+                       const float* coef_c = nullptr, float* zc = nullptr, float* dc = nullptr);
 void launch_prolong_add(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* zc, double* zf,
                         int nr, int64_t sf, int64_t sc, cudaStream_t s);
 void launch_prolong_add32(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const float* zc, float* zf,

@@ -513,7 +513,8 @@ void prof_flush(tobk_handle* h) {
   h->prof_pending.clear();
 }
 
-static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* z, double* t) {
+// z0_ready: the restriction into this level already took the first smoothing step (z, dA written)
+static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* z, double* t, bool z0_ready = false) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[j];
   const int64_t n = L.g.n;
@@ -529,9 +530,11 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
   // smoothing steps: Chebyshev keeps its increment in dA/dB; damped Jacobi needs none
   double* dA = L.dA;
   double* dB = L.dB;
-  prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
-  launch_jacobi0(b, L.dinv, z, SmoothArgs<double>{L.coef, nullptr, dA}, n, nr, n, s);
-  prof_end(h);
+  if (!z0_ready) {
+    prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
+    launch_jacobi0(b, L.dinv, z, SmoothArgs<double>{L.coef, nullptr, dA}, n, nr, n, s);
+    prof_end(h);
+  }
   for (int it = 1; it < h->desc.nu_pre; ++it) {
     prof_begin(h, ks, (double)nr * n);
     launch_apply(op, APPLY_JAC, z, b, L.dinv, t, SmoothArgs<double>{L.coef + 2 * it, dA, dB}, nr, n, s);
@@ -543,10 +546,14 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
   launch_apply(op, APPLY_RES, z, b, nullptr, L.r, SmoothArgs<double>{}, nr, n, s);
   prof_end(h);
   Level& C = h->lv[j + 1];
+  const bool fuse = j + 1 < h->L - 1;  // the coarse level smooths (it is not the dense coarsest)
   prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
-  launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s);
+  if (fuse)
+    launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s, C.dinv, C.coef, C.z, C.dA);
+  else
+    launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s);
   prof_end(h);
-  double* zc = vcycle64(h, j + 1, nr, C.b, C.z, C.t);
+  double* zc = vcycle64(h, j + 1, nr, C.b, C.z, C.t, fuse);
   prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
   launch_prolong_add(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
   prof_end(h);
@@ -561,7 +568,7 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
   return z;
 }
 
-static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, float* t) {
+static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, float* t, bool z0_ready = false) {
   cudaStream_t s = h->stream;
   Level& L = h->lv[j];
   const int64_t n = L.g.n;
@@ -576,9 +583,11 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
   const LevelOpDesc op = level_op(h, j);
   float* dA = L.dA32;
   float* dB = L.dB32;
-  prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
-  launch_jacobi0_32(b, L.dinv32, z, SmoothArgs<float>{L.coef32, nullptr, dA}, n, nr, n, s);
-  prof_end(h);
+  if (!z0_ready) {
+    prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
+    launch_jacobi0_32(b, L.dinv32, z, SmoothArgs<float>{L.coef32, nullptr, dA}, n, nr, n, s);
+    prof_end(h);
+  }
   for (int it = 1; it < h->desc.nu_pre; ++it) {
     prof_begin(h, ks, (double)nr * n);
     launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t, SmoothArgs<float>{L.coef32 + 2 * it, dA, dB}, nr, n, s);
@@ -590,10 +599,14 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
   launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, SmoothArgs<float>{}, nr, n, s);
   prof_end(h);
   Level& C = h->lv[j + 1];
+  const bool fuse = j + 1 < h->L - 1;
   prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
-  launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s);
+  if (fuse)
+    launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s, C.dinv32, C.coef32, C.z32, C.dA32);
+  else
+    launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s);
   prof_end(h);
-  float* zc = vcycle32(h, j + 1, nr, C.b32, C.z32, C.t32);
+  float* zc = vcycle32(h, j + 1, nr, C.b32, C.z32, C.t32, fuse);
   prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
   launch_prolong_add32(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
   prof_end(h);
