@@ -775,6 +775,14 @@ void launch_mask_copy(const double* src, const uint8_t* fixed, double* dst, int6
 // ================================================================================================
 constexpr int kVecBlocks = 4 * 152;  // vector kernels: grid-stride over DOFs with a fixed grid
 
+// Blocks per right-hand side of the grid-stride vector kernels: about kVecBlocks in total over the
+// nr right-hand sides (each block then streams many elements; thousands of short blocks would pay
+// their reduction and scheduling cost more often than they move data), at most one per kThreads DOFs.
+inline unsigned vec_blocks(int64_t n, int nr) {
+  const int64_t per = std::max<int64_t>(8, (kVecBlocks + nr - 1) / std::max(nr, 1));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(per, (n + kThreads - 1) / kThreads));
+}
+
 __device__ __forceinline__ double* rhs_sc(double* sc, int r) { return sc + (size_t)r * kScStride; }
 
 template <int DIM, class Op>
@@ -999,7 +1007,7 @@ void launch_cg_init(const LevelOpDesc& d, const double* b, double* x, double* r,
 void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q, const double* p, bool flexible,
                     int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = 4 * kVecBlocks;
-  const unsigned g = (unsigned)std::min<int64_t>(kVecBlocks, (n + kThreads - 1) / kThreads);
+  const unsigned g = vec_blocks(n, nr);
   ::tobk::note_launch(), k_cg_dots<<<dim3(g, nr), kThreads, 0, s>>>(n, z, r, q, p, flexible ? 1 : 0, stride, sc, partial, counters + kMaxRhs, ps);
 }
 
@@ -1039,7 +1047,7 @@ void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_
 void launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, int nr, int64_t stride,
                       double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = 4 * kVecBlocks;
-  const unsigned g = (unsigned)std::min<int64_t>(kVecBlocks, (n + kThreads - 1) / kThreads);
+  const unsigned g = vec_blocks(n, nr);
   ::tobk::note_launch(), k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial, counters + 3 * kMaxRhs, ps);
 }
 
