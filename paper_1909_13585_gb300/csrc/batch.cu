@@ -61,7 +61,7 @@ struct BItem {
 // ------------------------------------------------------------------------------------------------
 // kernels (blockIdx.y = right-hand side, or RHS group for the stencil kernel)
 // ------------------------------------------------------------------------------------------------
-constexpr int kBElem = 1024;  // DOFs per item of the elementwise lists (4 per thread)
+constexpr int kBElem = 4096;  // DOFs per item of the elementwise lists (16 per thread: few, long blocks)
 
 __device__ __forceinline__ bool b_active(const BDesign& d, int rhs) { return d.sc[rhs * kScStride + SC_ACTIVE] != 0.0; }
 
