@@ -2,7 +2,7 @@
 (Sec. 2.1 steps 1-4), adjoint right-hand sides and solutions (eq. AdjointSystem) and the
 sensitivities (eq. SensitivityLambda), in 2D and 3D.
 
-Tolerances (stated in the task for FP64 mode): load factors within 1e-6 relative; sensitivities
+Tolerances (FP64 mode): load factors within 1e-6 relative; sensitivities
 within 1e-5 of max |.|.  Modes and sensitivities are gated only for load factors whose relative gap
 to their neighbours exceeds 1e-4 (eigenvectors of clustered eigenvalues are not unique)."""
 import numpy as np
