@@ -127,3 +127,104 @@ def assemble_G(nel, dim, x, u, nu, penal, E0, Emin):
     u = np.asarray(u, dtype=np.float64)
     Ge = np.stack([stress_stiffness_ge0(dim, nu, u[d]) for d in edofs])
     return _assemble(nel, dim, Es[:, None, None] * Ge)
+
+
+# ------------------------------------------------------------------------------------------------
+# buckling analysis and sensitivities with the incompatible-mode elements (Sec. 2 with K_c, G_c)
+# ------------------------------------------------------------------------------------------------
+def adjoint_element_vector(dim: int, nu: float, phie: np.ndarray) -> np.ndarray:
+    """d/du_e of phi_e^T G_c[u_e] phi_e (unit modulus).  With phi~ = T phi_e (nodal and internal
+    amplitudes), phi_e^T G_c[u_e] phi_e = sum_gp w |J| sigma(u_e) . h(phi~), where sigma(u_e) =
+    D B~ T u_e is the enhanced stress and h the Voigt form (doubled shear) of
+    H_ab = sum_c (d_a phi~_c)(d_b phi~_c); so the derivative is sum_gp w |J| (B~ T)^T D h(phi~)."""
+    D = elements.constitutive(dim, nu)
+    T = condensation(dim, nu)
+    pts, wts = elements.gauss_points(dim)
+    nf = 2 ** dim + dim
+    P = (T @ np.asarray(phie, dtype=np.float64)).reshape(nf, dim)
+    out = np.zeros(dim * 2 ** dim)
+    for xi, w in zip(pts, wts):
+        dF = _functions_grad(xi)
+        grad = dF @ P                      # grad[a, c] = d phi~_c / d x_a
+        H = grad @ grad.T
+        if dim == 2:
+            h = np.array([H[0, 0], H[1, 1], 2.0 * H[0, 1]])
+        else:
+            h = np.array([H[0, 0], H[1, 1], H[2, 2], 2.0 * H[0, 1], 2.0 * H[1, 2], 2.0 * H[2, 0]])
+        out += w * elements.detJ(dim) * (_strain_matrix(dF) @ T).T @ D @ h
+    return out
+
+
+def adjoint_rhs(nel, dim, x, phi, nu, penal, E0, Emin) -> np.ndarray:
+    """b = phi^T (grad_u G) phi for the condensed elements, full DOF set (eq. AdjointSystem)."""
+    edofs = grid.element_dofs(nel, dim)
+    _, Es, _, _ = elements.simp(np.asarray(x, dtype=np.float64), penal, E0, Emin)
+    phi = np.asarray(phi, dtype=np.float64)
+    b = np.zeros(dim * grid.num_nodes(nel, dim))
+    for e, d in enumerate(edofs):
+        np.add.at(b, d, Es[e] * adjoint_element_vector(dim, nu, phi[d]))
+    return b
+
+
+class Problem:
+    """The oracle's problem view (the interface of oracle.lba.Problem: K, Kf, fixed, free, solve,
+    to_full, G) with the incompatible-mode elements."""
+
+    def __init__(self, prob):
+        import scipy.sparse.linalg as spla
+        from . import assembly
+        self.p = prob
+        self.dim = prob.dim
+        self.nel = prob.nel
+        self.fixed = np.asarray(prob.fixed, dtype=np.uint8)
+        self.free = np.flatnonzero(self.fixed == 0)
+        self.n = prob.num_dofs
+        self.K = assemble_K(prob.nel, prob.dim, prob.x, prob.nu, prob.penal, prob.E0, prob.Emin)
+        self.Kf = assembly.restrict_free(self.K, self.fixed)
+        self._splu = spla.splu
+        self._lu = None
+
+    def solve(self, B: np.ndarray) -> np.ndarray:
+        if self._lu is None:
+            self._lu = self._splu(self.Kf.tocsc())
+        return self._lu.solve(np.asarray(B, dtype=np.float64))
+
+    def to_full(self, vf: np.ndarray) -> np.ndarray:
+        out = np.zeros((self.n,) + vf.shape[1:])
+        out[self.free] = vf
+        return out
+
+    def G(self, u: np.ndarray):
+        p = self.p
+        return assemble_G(p.nel, p.dim, p.x, u, p.nu, p.penal, p.E0, p.Emin)
+
+
+def sensitivities(op: Problem, u, lam, Phi):
+    """dlambda/dx [q, m], dJ/dx [m] and the adjoint solutions Z [n, q] with the condensed elements:
+    the formula of oracle.sensitivity (eq. SensitivityLambda with the factor -1/(phi^T G phi)) on
+    K_c and G_c[u_e]."""
+    p = op.p
+    dim, nel = p.dim, p.nel
+    x = np.asarray(p.x, dtype=np.float64)
+    edofs = grid.element_dofs(nel, dim)
+    _, _, dEk, dEs = elements.simp(x, p.penal, p.E0, p.Emin)
+    Kc = stiffness_ke0(dim, p.nu)
+    Ge = np.stack([stress_stiffness_ge0(dim, p.nu, u[d]) for d in edofs])
+    G = op.G(u)
+    q = Phi.shape[1]
+    B = np.stack([adjoint_rhs(nel, dim, x, Phi[:, i], p.nu, p.penal, p.E0, p.Emin) for i in range(q)], axis=1)
+    B[op.fixed == 1] = 0.0
+    Z = op.to_full(op.solve(B[op.free]))
+    Ue = u[edofs]
+    Ku = np.einsum("ij,mj->mi", Kc, Ue)
+    dJ = -dEk * np.einsum("mi,mi->m", Ue, Ku)
+    dlam = np.zeros((q, x.size))
+    for i in range(q):
+        ph = Phi[:, i]
+        Pe = ph[edofs]
+        Ze = Z[:, i][edofs]
+        pKp = np.einsum("mi,ij,mj->m", Pe, Kc, Pe)
+        pGp = np.einsum("mi,mij,mj->m", Pe, Ge, Pe)
+        zKu = np.einsum("mi,mi->m", Ze, Ku)
+        dlam[i] = -(dEk * pKp + lam[i] * dEs * pGp - lam[i] * dEk * zKu) / (ph @ (G @ ph))
+    return dlam, dJ, Z

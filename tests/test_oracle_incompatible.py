@@ -145,3 +145,73 @@ def test_euler_column_with_incompatible_modes():
     assert abs(errs_c[0]) < 1e-3
     assert all(abs(c) < abs(q) for c, q in zip(errs_c, errs_p))
     assert abs(errs_c[1]) < abs(errs_c[0]) + 1e-4
+
+
+def test_adjoint_rhs_is_the_derivative_of_phi_G_phi():
+    """b . w = d/dt phi^T G[u + t w] phi (G is linear in u, so the central difference is exact up to
+    rounding), with the condensed elements."""
+    p = synthetic.column_2d(6, 4, seed=10, radius=1.5)
+    op = incompatible.Problem(p)
+    u = op.to_full(op.solve(np.asarray(p.f)[op.free]))
+    rng = np.random.default_rng(11)
+    phi, w = rng.standard_normal(p.num_dofs), rng.standard_normal(p.num_dofs)
+    b = incompatible.adjoint_rhs(p.nel, 2, p.x, phi, p.nu, p.penal, p.E0, p.Emin)
+    t = 1e-3
+    gp = phi @ (op.G(u + t * w) @ phi)
+    gm = phi @ (op.G(u - t * w) @ phi)
+    assert b @ w == pytest.approx((gp - gm) / (2 * t), rel=1e-10)
+
+
+def test_incompatible_sensitivities_central_difference():
+    """Exact LBA path with the condensed elements: dlambda/dx and dJ/dx against central differences
+    (h = 1e-5 x_e) on 12 random elements, 1e-5 of max |.| where the load factors are separated."""
+    p = synthetic.column_2d(10, 4, seed=8, radius=1.5)
+    q = 3
+
+    def values(prob):
+        op = incompatible.Problem(prob)
+        u = op.to_full(op.solve(np.asarray(prob.f)[op.free]))
+        lam, Phi, _ = lba.exact_lba(op, u, q)
+        return op, u, float(np.asarray(prob.f) @ u), lam, Phi
+
+    op, u, J, lam, Phi = values(p)
+    dlam, dJ, _ = incompatible.sensitivities(op, u, lam, Phi)
+    gaps = np.minimum(np.abs(np.diff(np.r_[-np.inf, lam])), np.abs(np.diff(np.r_[lam, np.inf])))
+    rng = np.random.default_rng(9)
+    x0 = p.x.copy()
+    for e in rng.choice(p.x.size, size=12, replace=False):
+        h = 1e-5 * x0[e]
+        vals = []
+        for s in (+1, -1):
+            p.x = x0.copy()
+            p.x[e] += s * h
+            _, _, Js, lams, _ = values(p)
+            vals.append((Js, lams))
+        p.x = x0
+        assert (vals[0][0] - vals[1][0]) / (2 * h) == pytest.approx(dJ[e], abs=1e-5 * np.abs(dJ).max())
+        fdl = (vals[0][1] - vals[1][1]) / (2 * h)
+        for i in range(q):
+            if gaps[i] / lam[i] > 1e-4:
+                assert fdl[i] == pytest.approx(dlam[i, e], abs=1e-5 * np.abs(dlam[i]).max())
+
+
+def test_incompatible_multilevel_rayleigh_bound_and_3d_adjoint():
+    """The multilevel path (Sec. 2.1 steps 1-4) runs unchanged on the condensed elements, and its
+    first load factor is a Rayleigh quotient, hence not below the exact one; the 3D adjoint
+    right-hand side is the derivative of phi^T G[u] phi."""
+    p = synthetic.column_2d(24, 8, seed=7, radius=2, mg_levels=3, eig_level=2, num_modes=3)
+    op = incompatible.Problem(p)
+    u = op.to_full(op.solve(np.asarray(p.f)[op.free]))
+    ml = lba.multilevel_lba(op, u, 3, 2)
+    lam_exact, _, _ = lba.exact_lba(op, u, 1)
+    assert ml["lam"][0] >= lam_exact[0] * (1 - 1e-10)
+    assert ml["lam"][0] <= lam_exact[0] * 1.1
+    q3 = synthetic.cantilever_3d(4, 2, 2, seed=3, radius=1.5, volfrac=0.5, mg_levels=1, eig_level=1, num_modes=1)
+    op3 = incompatible.Problem(q3)
+    u3 = op3.to_full(op3.solve(np.asarray(q3.f)[op3.free]))
+    rng = np.random.default_rng(4)
+    phi, w = rng.standard_normal(q3.num_dofs), rng.standard_normal(q3.num_dofs)
+    b = incompatible.adjoint_rhs(q3.nel, 3, q3.x, phi, q3.nu, q3.penal, q3.E0, q3.Emin)
+    t = 1e-3
+    d = (phi @ (op3.G(u3 + t * w) @ phi) - phi @ (op3.G(u3 - t * w) @ phi)) / (2 * t)
+    assert b @ w == pytest.approx(d, rel=1e-10)
