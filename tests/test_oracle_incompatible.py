@@ -101,6 +101,33 @@ def test_2d_condensed_stiffness_closed_form():
     assert np.allclose(diff, c * (np.outer(gu, gu) + np.outer(gv, gv)), atol=1e-14)
 
 
+@pytest.mark.parametrize("nu", [0.2, 0.3, 0.45])
+def test_3d_condensed_stiffness_closed_form(nu):
+    """For the unit cube, condensation changes the energy only on three pairs of bilinear Walsh
+    patterns (u xy with w yz, v xy with w zx, v yz with u zx; s_S = product of the node's corner
+    signs over the axes in S): K_H8 - K_c = (1/64) sum over the pairs of a (v1 v1^T + v2 v2^T) +
+    b (v1 v2^T + v2 v1^T), a = (4/3)(mu + lambda^2/(lambda + 2 mu)), b = (4/3) lambda^2/(lambda + 2 mu);
+    the trilinear (xyz) mode and the other bilinear patterns keep their H8 energy."""
+    lam = nu / ((1 + nu) * (1 - 2 * nu))
+    mu = 1.0 / (2 * (1 + nu))
+    a = 4.0 / 3.0 * (mu + lam ** 2 / (lam + 2 * mu))
+    b = 4.0 / 3.0 * lam ** 2 / (lam + 2 * mu)
+    X = elements.NODES_H8
+    pat = {"xy": X[:, 0] * X[:, 1], "yz": X[:, 1] * X[:, 2], "zx": X[:, 2] * X[:, 0]}
+
+    def vec(S, c):
+        v = np.zeros(24)
+        v[c::3] = pat[S]
+        return v
+
+    F = np.zeros((24, 24))
+    for (s1, c1), (s2, c2) in [(("xy", 0), ("yz", 2)), (("xy", 1), ("zx", 2)), (("yz", 1), ("zx", 0))]:
+        v1, v2 = vec(s1, c1), vec(s2, c2)
+        F += (a * (np.outer(v1, v1) + np.outer(v2, v2)) + b * (np.outer(v1, v2) + np.outer(v2, v1))) / 64.0
+    diff = elements.stiffness_ke0(3, nu) - incompatible.stiffness_ke0(3, nu)
+    assert np.allclose(diff, F, atol=1e-14)
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_condensed_stress_stiffness_invariants(dim):
     rng = np.random.default_rng(3)
