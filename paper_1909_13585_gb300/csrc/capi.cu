@@ -1,4 +1,7 @@
-// extern "C" entry points of libtobk.so (declared and documented in include/tobk.h).
+// extern "C" entry points of libtobk.so (declared and documented in include/tobk.h).  The calls
+// follow the paper's problem statement: densities, loads and supports, the linear analysis
+// (Algorithm 1 step 3), the buckling analysis (Algorithm 1 steps 4-5 exact; Sec. 2.1 / Algorithm 2
+// multilevel) and the sensitivities (eq. SensitivityLambda, eq. AdjointSystem).
 #include <cuda_runtime.h>
 
 #include <cstring>

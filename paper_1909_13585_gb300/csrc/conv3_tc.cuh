@@ -1,3 +1,6 @@
+// Not part of the paper's method: the learned warm start's network (mgPCG still runs to the same
+// tolerance from its guess).
+//
 // Tensor-core (tcgen05) 3x3x3 convolution for the learned warm start's inference: an implicit GEMM
 // out[v][co] = bias[co] + sum_tap sum_ci A_tap[v][ci] W_tap[co][ci] with M = 128 voxels per CTA,
 // N = Cout, K = Cin per tap (padded to a multiple of 16), BF16 operands (the activations are rounded

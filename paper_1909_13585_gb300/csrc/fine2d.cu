@@ -1,4 +1,7 @@
-// Fine-level (matrix-free) Q4 operator in factored form (q4_element.cuh), element by element on
+// Fine-level (matrix-free) K(x) v = sum_e E_kappa(x_e) K_e0 v_e of Sec. 2 (applied inside the mgPCG of
+// Algorithm 1 step 3 and Appendix A) for Q4 elements.
+//
+// Q4 operator in factored form (q4_element.cuh), element by element on
 // shared-memory tiles: a block computes the 32 x 8 elements around a 31 x 7 tile of nodes once (one
 // element per thread, so the FP64-bound force phase is a single full round), stores their nodal
 // forces in shared memory and gathers the four contributions of each node.  On GB300,

@@ -1,4 +1,6 @@
-// Fine-level (matrix-free) H8 operator in factored form (h8_element.cuh), element by element.
+// Fine-level (matrix-free) K(x) v = sum_e E_kappa(x_e) K_e0 v_e of Sec. 2 (applied inside the mgPCG of
+// Algorithm 1 step 3 and Appendix A) for H8 elements: the operator in factored form
+// (h8_element.cuh), element by element.
 //
 // A block owns a 31 x 7 column of nodes in the (x, y) plane and a range of zc node planes, and
 // marches up in z one element layer at a time: it keeps two node planes of the input (with a

@@ -1,3 +1,5 @@
+// The unit-modulus element stiffness K_e0 of Sec. 2 for the unit-cube H8 element, in factored form.
+//
 // Factored unit-cube H8 element operator (trilinear, isotropic, exact integration = 2x2x2 Gauss).
 //
 // With centred coordinates (xi, eta, zeta) in [-1/2, 1/2]^3, a trilinear field is

@@ -1,5 +1,6 @@
 // Allocation-free residual check on the fine grid (declared as tobk_residual_noalloc in
-// include/tobk.h).
+// include/tobk.h): the relative residual ||b - K(x) x|| / ||b|| of the linear analysis (Algorithm 1
+// step 3; the stopping quantity of the mgPCG solves, Appendix A).
 //
 // Some callers cannot allocate device memory at the point where they want to verify a solution:
 // code running while a CUDA stream is being captured into a graph (cudaMalloc is not a legal

@@ -1,3 +1,6 @@
+// The unit-modulus element stiffness K_e0 of Sec. 2 for the unit-square Q4 element, in factored
+// form.
+//
 // Factored unit-square Q4 element operator (plane stress, 2 x 2 Gauss), shared by the fine-level
 // kernels of one design (fine2d.cu) and of a batch of designs (batch.cu).
 //

@@ -1,4 +1,5 @@
-// Dense Rayleigh-Ritz of the projected buckling pencil (included by eigen.cu).
+// Dense Rayleigh-Ritz of the projected buckling pencil (included by eigen.cu), the dense step of
+// the coarse eigenproblem (eq. eigenvalueProblemCoarseScale; solved to a residual of 1e-8, Appendix A).
 //
 // The eigensolver keeps its basis K-orthonormal, so the projected problem is the standard
 // symmetric eigenproblem H y = theta y with H = V^T (-G) V (size m <= kRRMax).  A dense eigensolver

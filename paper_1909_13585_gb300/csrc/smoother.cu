@@ -1,3 +1,6 @@
+// Smoother of the geometric multigrid that preconditions mgPCG (Appendix A; the paper leaves the
+// smoother open).
+//
 // Multigrid smoother set-up: the spectral radius of D^{-1} K on every level (power iteration on the
 // device) and the per-step coefficients of the smoother (damped Jacobi, or a Chebyshev polynomial
 // in D^{-1} K over [lambda_max / ratio, lambda_max]).
