@@ -139,3 +139,70 @@ def eig_residual(Kf, Gf, lam, phi_free):
     """||(K + lambda G) phi|| / ||K phi||, the residual measure of eq. eigResidual."""
     Kp = Kf @ phi_free
     return float(np.linalg.norm(Kp + lam * (Gf @ phi_free)) / np.linalg.norm(Kp))
+
+
+# ------------------------------------------------------------------------------------------------
+# Algorithm 2 with its per-level steps (the optional refinement of Sec. 2.1, Appendix A)
+# ------------------------------------------------------------------------------------------------
+def kaczmarz(A: sp.spmatrix, Psi: np.ndarray, sweeps: int) -> np.ndarray:
+    """Kaczmarz sweeps for A psi = 0 on every column of Psi (Appendix A: Gauss-Seidel on A^T A):
+    for the rows i = 0, 1, ... in turn, psi <- psi - (a_i . psi / |a_i|^2) a_i."""
+    A = A.tocsr()
+    rn = np.asarray(A.multiply(A).sum(axis=1)).ravel()
+    Psi = np.array(Psi, dtype=np.float64, copy=True)
+    for _ in range(sweeps):
+        for i in range(A.shape[0]):
+            if rn[i] == 0.0:
+                continue
+            s, e = A.indptr[i], A.indptr[i + 1]
+            cols, vals = A.indices[s:e], A.data[s:e]
+            r = vals @ Psi[cols]
+            Psi[cols] -= np.outer(vals, r / rn[i])
+    return Psi
+
+
+def ritz(Kl, Gl, Psi: np.ndarray):
+    """Rayleigh-Ritz of the pencil (K + lambda G) on span(Psi) (Algorithm 2 'R[Psi]'): the positive
+    load factors in ascending order and their K-normalised Ritz vectors."""
+    Kq = Psi.T @ (Kl @ Psi)
+    Gq = Psi.T @ (Gl @ Psi)
+    mu, Y = sla.eigh(-0.5 * (Gq + Gq.T), 0.5 * (Kq + Kq.T))
+    pos = np.flatnonzero(mu > 0)
+    order = pos[np.argsort(-mu[pos])]
+    return 1.0 / mu[order], _normalise_modes(Kl, Psi @ Y[:, order])
+
+
+def multilevel_lba_refined(op: Problem, u: np.ndarray, q: int, eig_level: int, sweeps: int = 1,
+                           ritz_projection: bool = True, dense_limit: int = 4000):
+    """Algorithm 2: the coarse eigenpairs of level eig_level, then on every level j = eig_level-1 down
+    to 1 (the fine grid; the printed loop index is garbled): prolongate Psi^j = I^j_{j+1} Psi^{j+1},
+    shift by the smallest load factor of the level above, `sweeps` Kaczmarz sweeps on
+    (K^j + shift G^j) psi = 0 for every mode, Rayleigh-Ritz on span Psi^j; finally the fine solve
+    K Phi~ = G Psi and the per-column Rayleigh quotients (lines 15-16).  With sweeps = 0 and no
+    Ritz projection this is Sec. 2.1 steps 1-4 (multilevel_lba)."""
+    G = op.G(u)
+    Gf = assembly.restrict_free(G, op.fixed)
+    nels, fixeds, Ps = transfer.hierarchy(op.nel, op.dim, op.fixed, eig_level)
+    Ks, Gs = [op.Kf], [Gf]
+    for P in Ps:
+        Ks.append((P.T @ Ks[-1] @ P).tocsr())
+        Gs.append((P.T @ Gs[-1] @ P).tocsr())
+    lam_c, Psi = buckling_pencil(Ks[-1], Gs[-1], q, dense_limit)
+    Lam = lam_c
+    levels = []
+    for j in reversed(range(len(Ps))):                               # level j + 1 (1-based) = Omega_{j+1}
+        Psi = Ps[j] @ Psi
+        if sweeps > 0:
+            Psi = kaczmarz(Ks[j] + Lam.min() * Gs[j], Psi, sweeps)
+        if ritz_projection:
+            Lam, Psi = ritz(Ks[j], Gs[j], Psi)
+            if Lam.size < q:
+                raise RuntimeError("Rayleigh-Ritz lost a positive load factor on level %d" % (j + 1))
+        levels.append(dict(level=j + 1, lam=Lam.copy(), K=Ks[j], G=Gs[j]))
+    Phi = op.solve(Gf @ Psi)
+    num = np.einsum("ij,ij->j", Phi, op.Kf @ Phi)
+    den = np.einsum("ij,ij->j", Phi, Gf @ Phi)
+    lam = -num / den
+    order = np.argsort(lam)
+    return dict(lam=lam[order], Phi=op.to_full(_normalise_modes(op.Kf, Phi[:, order])), lam_coarse=lam_c,
+                levels=levels, Gf=Gf)

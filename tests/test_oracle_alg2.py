@@ -1,0 +1,50 @@
+"""Pins of the oracle's Algorithm 2 refinement (oracle.lba.multilevel_lba_refined: per-level
+Kaczmarz smoothing and Rayleigh-Ritz, Appendix A): Kaczmarz row projections never lengthen a vector
+(A psi = 0 is consistent), the Ritz load factors bound each level's exact ones from above
+(Courant-Fischer for the K-definite pencil), the refinement without smoothing and projection is
+Sec. 2.1 steps 1-4, and the fine load factor keeps its Rayleigh bound."""
+import numpy as np
+import scipy.linalg as sla
+
+import synthetic
+from oracle import lba
+
+
+def _case():
+    p = synthetic.column_2d(32, 16, seed=13, radius=2.5, mg_levels=4, eig_level=3, num_modes=4)
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    return p, op, u
+
+
+def test_kaczmarz_projections_never_lengthen_a_vector():
+    p, op, u = _case()
+    A = op.Kf + 0.5 * lba.assembly.restrict_free(op.G(u), op.fixed)
+    rng = np.random.default_rng(1)
+    psi = rng.standard_normal((A.shape[0], 2))
+    norms = [np.linalg.norm(psi, axis=0)]
+    for _ in range(3):
+        psi = lba.kaczmarz(A, psi, 1)
+        norms.append(np.linalg.norm(psi, axis=0))
+    assert all(np.all(b <= a * (1 + 1e-14)) for a, b in zip(norms, norms[1:]))
+
+
+def test_reduces_to_sec_2_1_without_smoothing_and_projection():
+    p, op, u = _case()
+    a = lba.multilevel_lba(op, u, 4, 3)
+    b = lba.multilevel_lba_refined(op, u, 4, 3, sweeps=0, ritz_projection=False)
+    assert np.allclose(a["lam"], b["lam"], rtol=1e-12)
+
+
+def test_ritz_load_factors_bound_each_level_and_the_fine_grid():
+    p, op, u = _case()
+    r = lba.multilevel_lba_refined(op, u, 4, 3, sweeps=2)
+    for lv in r["levels"]:
+        mu = sla.eigh(-lv["G"].toarray(), lv["K"].toarray(), eigvals_only=True)
+        exact = np.sort(1.0 / mu[mu > 0])[:4]
+        assert np.all(lv["lam"][:4] >= exact * (1 - 1e-10)), (lv["level"], lv["lam"], exact)
+    lam_exact, _, _ = lba.exact_lba(op, u, 1)
+    assert r["lam"][0] >= lam_exact[0] * (1 - 1e-10)
+    # the per-level smoothing does not make the first load factor worse than Sec. 2.1's
+    plain = lba.multilevel_lba(op, u, 4, 3)
+    assert r["lam"][0] <= plain["lam"][0] * (1 + 1e-3)
