@@ -464,9 +464,11 @@ def ours(args):
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = job_throughput(units, args.steps, world, total_ms)
 
-    # per-phase times and kernel-class profile over K more steps (profiling on)
+    # per-phase device times over K more steps (CUDA events per phase and per eigensolver iteration,
+    # no per-launch events), then the kernel-class profile over K more steps (events around every
+    # launch of a class, which serialises the host side: its times feed the roofline only)
     phases = {}
-    s.profile(True)
+    s.phase_timing(True)
     for _ in range(args.steps):
         s.set_densities(x_d)
         _, i1 = s.solve_equilibrium()
@@ -475,6 +477,12 @@ def ours(args):
         for k, inf in (("linear_analysis", i1), ("buckling", i2), ("sensitivities", i3)):
             phases.setdefault(k, []).append(inf["time_ms"])
             phases.setdefault(k + "_iters", []).append(inf["iterations"])
+        for k, v in s.phase_read().items():
+            phases.setdefault("buckling." + k, []).append(v)
+    s.phase_timing(False)
+    s.profile(True)
+    for _ in range(args.steps):
+        step()
     prof = s.profile_read()
     s.profile(False)
     roof = roofline(prof, p, peaks, args.precision)
@@ -508,7 +516,7 @@ def ours(args):
 
     forms = {}
     if not args.no_forms:
-        fs, fw = min(args.steps, 3), max(3, min(args.warmup, 3))
+        fs, fw = args.steps, max(3, args.warmup)
         forms["column480x160_fp32_vcycle"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP32_VCYCLE, False,
                                                           fs, fw, dev, flush)
         forms["cantilever96x48x48_fp32_vcycle_fused"] = measure_form(pkg, torch, "cantilever96x48x48",

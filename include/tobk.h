@@ -192,6 +192,28 @@ int tobk_profile_enable(tobk_handle* h, int enable);
 int tobk_profile_read(tobk_handle* h, int kernel_class, long long* launches, double* total_ms,
                       double* dof_rhs);
 
+/* Phases of the last tobk_compute_buckling, in device milliseconds (CUDA events on the handle's
+ * stream, recorded while phase timing is on): the eigensolve (eq. eigenvalueProblemCoarseScale on
+ * Omega_l, or eq. eigenvalueProblem0 on the fine grid), and within it the multigrid preconditioner
+ * applications and the dense Rayleigh-Ritz steps; the prolongation Psi^j = I^j_{j+1} Psi^{j+1} with
+ * the right-hand sides G Psi (Sec. 2.1 step 2); the fine block solve K Phi = G Psi (eq. FineScaleBVP);
+ * the Rayleigh quotients and the normalisation of the modes (eq. FineScaleRQ); and the eigensolver's
+ * outer iterations (a count, not a time). */
+typedef enum {
+  TOBK_PHASE_EIGEN = 0,
+  TOBK_PHASE_EIGEN_PRECOND = 1,
+  TOBK_PHASE_EIGEN_RR = 2,
+  TOBK_PHASE_PROLONG = 3,
+  TOBK_PHASE_FINE_SOLVE = 4,
+  TOBK_PHASE_RQ = 5,
+  TOBK_PHASE_EIGEN_ITERS = 6,
+  TOBK_PHASE_COUNT = 7
+} tobk_phase;
+/* Turns phase timing on (1) or off (0); it adds a few CUDA events per eigensolver iteration. */
+int tobk_phase_enable(tobk_handle* h, int enable);
+/* Copies min(len, TOBK_PHASE_COUNT) phase values of the last compute_buckling to out (host). */
+int tobk_phase_read(tobk_handle* h, double* out, int len);
+
 /* ---- unit-level entry points (device pointers) ------------------------------------------------ */
 /* Element and DOF counts of a 1-based level: out[0..2] = nel, out[3] = n (DOFs), out[4] = m. */
 int tobk_level_info(tobk_handle* h, int level, int64_t* out5);
@@ -325,7 +347,9 @@ int tobk_unet_train_step(tobk_unet* net, const float* x, const double* f, const 
  *
  * For r = 0..nrhs-1 writes relres[r] = ||B_r - K(x) X_r||_2 / ||B_r||_2 over the free DOFs of the
  * fine grid described by desc (dim, nel, nu, E0, Emin, penal; other fields ignored), K(x) being the
- * SIMP stiffness of tobk_apply_K at level 1.  x [m], fixed [n] (uint8, 1 = fixed), B and X
+ * SIMP stiffness of tobk_apply_K at level 1.  Entries of X at fixed DOFs are read as zero (the
+ * residual of the free-DOF system), and when B_r is zero on the free DOFs relres[r] is the absolute
+ * residual norm ||K(x) X_r||_2.  x [m], fixed [n] (uint8, 1 = fixed), B and X
  * [nrhs][n] and relres [nrhs] are DEVICE pointers on the current device; the caller owns them.
  * The work is enqueued on cuda_stream (NULL = legacy default stream); relres is valid once that
  * stream has reached this point.
@@ -334,8 +358,10 @@ int tobk_unet_train_step(tobk_unet* net, const float* x, const double* f, const 
  * exits.  Every call on a device shares that array: calls whose kernels may overlap on the GPU
  * (different streams without ordering) race and must not be issued.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture begins.
- * Errors: TOBK_E_ARG (null pointer, bad dim or sizes, nrhs out of range), TOBK_E_CUDA. */
+ * make that first call before any stream capture begins.  Later calls whose stream is not being
+ * captured look the address up again, so that it stays valid after a device reset.
+ * Errors: TOBK_E_ARG (null pointer, bad dim or sizes, nrhs out of range, the material checks of
+ * tobk_create: -1 < nu < 0.5, E0 > 0, Emin > 0, penal >= 1), TOBK_E_CUDA. */
 int tobk_residual_noalloc(const tobk_desc* desc, const double* x, const uint8_t* fixed, const double* B,
                           const double* X, int nrhs, double* relres, void* cuda_stream);
 

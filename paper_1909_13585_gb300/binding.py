@@ -82,10 +82,13 @@ _SIGS = {
     "tobk_conv3_bf16": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int, C.c_int, _P, C.c_void_p]),
     "tobk_launch_count": (C.c_longlong, []),
     "tobk_profile_enable": (C.c_int, [_H, C.c_int]),
+    "tobk_phase_enable": (C.c_int, [_H, C.c_int]),
+    "tobk_phase_read": (C.c_int, [_H, C.POINTER(C.c_double), C.c_int]),
     "tobk_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
 }
 
+PHASES = ("eigen", "eigen_precond", "eigen_rr", "prolong", "fine_solve", "rq", "eigen_iters")
 KERNEL_CLASSES = ("fine_smooth", "fine_residual", "fine_cg_matvec", "coarse", "transfer", "coarsest",
                   "vector", "eigen_dense", "eigen_block")
 
@@ -288,6 +291,14 @@ class Solver:
             out[name] = dict(launches=int(cnt.value), ms=float(ms.value), dof_rhs=float(units.value))
         return out
 
+    def phase_timing(self, enable=True):
+        self._check(self.lib.tobk_phase_enable(self.h, 1 if enable else 0))
+
+    def phase_read(self):
+        out = (C.c_double * len(PHASES))()
+        self._check(self.lib.tobk_phase_read(self.h, out, len(PHASES)))
+        return {k: float(v) for k, v in zip(PHASES, out)}
+
     def element_matrices(self, level, which, out):
         self._check(self.lib.tobk_get_element_matrices(self.h, level, which, out.data_ptr(), out.numel()))
         return out
@@ -430,7 +441,17 @@ class UNet:
         self._check(self.lib.tobk_unet_design_scale(self.h, x.data_ptr(), f.data_ptr(), C.byref(s)))
         return s.value
 
+    def _check_state_arrays(self, *arrays):
+        for a in arrays:
+            if a is None:
+                continue
+            n = a.numel() if hasattr(a, "numel") else a.size
+            dt = str(a.dtype)
+            if n != self.num_params or "float32" not in dt:
+                raise ValueError(f"network state arrays must be float32 of length {self.num_params}, got {dt} of {n}")
+
     def get_state(self, params, m=None, v=None):
+        self._check_state_arrays(params, m, v)
         step = C.c_longlong()
         pp, dev = _ptr(params)
         self._check(self.lib.tobk_unet_get_state(self.h, pp, _ptr(m)[0] if m is not None else None,
@@ -438,6 +459,7 @@ class UNet:
         return step.value
 
     def set_state(self, params, m=None, v=None, step=0):
+        self._check_state_arrays(params, m, v)
         pp, dev = _ptr(params)
         self._check(self.lib.tobk_unet_set_state(self.h, pp, _ptr(m)[0] if m is not None else None,
                                                  _ptr(v)[0] if v is not None else None, step, dev))

@@ -175,6 +175,19 @@ int tobk_profile_read(tobk_handle* h, int kc, long long* launches, double* total
   return check_cuda(h, "profile_read");
 }
 
+int tobk_phase_enable(tobk_handle* h, int enable) {
+  TOBK_GUARD(h);
+  h->phase_on = enable != 0;
+  return TOBK_OK;
+}
+
+int tobk_phase_read(tobk_handle* h, double* out, int len) {
+  TOBK_GUARD(h);
+  if (!out || len < 0) return fail(h, TOBK_E_ARG, "bad phase output");
+  for (int k = 0; k < len && k < TOBK_PHASE_COUNT; ++k) out[k] = h->phase_ms[k];
+  return TOBK_OK;
+}
+
 int tobk_level_info(tobk_handle* h, int level, int64_t* out5) {
   TOBK_GUARD(h);
   if (!out5 || level < 1 || level > h->L) return fail(h, TOBK_E_ARG, "bad level");

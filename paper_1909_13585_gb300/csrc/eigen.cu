@@ -214,6 +214,8 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   cudaMemsetAsync(sinfo, 0, sizeof(double), st);  // Cholesky breakdown flag (sticky)
   const bool trace = std::getenv("TOBK_EIG_TRACE") != nullptr;
   int rc = TOBK_OK;
+  PhaseMarks pm(h);
+  std::vector<std::pair<int, int>> pre_marks, rr_marks;
   for (it = 0; it < h->desc.eig_max_iter; ++it) {
     // ---- K-orthogonalise the new block against the basis (classical Gram-Schmidt, twice)
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
@@ -251,6 +253,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     // ---- Rayleigh-Ritz (the basis is K-orthonormal, so V^T K V = I): the leading eigenpairs of
     // the projected matrix, FP32 decomposition + two FP64 refinement steps (small_dense.cuh)
     const int nvec = std::min(m, keep_max);
+    const int rr0 = pm.mark();
     prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)m);
     // warm start from the previous refined eigenvectors while the basis only grew since then
     ::tobk::note_launch(), launch_rr_eig32(h->Hs, m, mmax, rrX1, rr_prev, rrX0, sinfo + 2, st);
@@ -267,6 +270,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     ::tobk::note_launch(), k_rr_finish<<<1, 256, rr_finish_smem_bytes(m, nvec), st>>>(
         h->Hs, mmax, m, nvec, rrXw, mmax, rrLam, rrDelta, theta, h->Ys, mmax);
     prof_end(h);
+    rr_marks.emplace_back(rr0, pm.mark());
     rr_prev = m;
     const int kk = std::min(nb, m);
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)m * n);
@@ -313,6 +317,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     nadd = (int)sel.size();
     cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st);
     ::tobk::note_launch(), k_gather_residual<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, KX, theta, dsel, Tb, n, sd);
+    const int pre0 = pm.mark();
     if (h->desc.eig_inner_iters <= 0) {
       apply_vcycle(h, j, nadd, Tb, W);
       ++inner_total;
@@ -327,6 +332,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       }
       inner_total += si.status_detail;
     }
+    pre_marks.emplace_back(pre0, pm.mark());
     // ---- thick restart: keep the kk Ritz vectors (FP64-accurate, hence K-orthonormal)
     if (m + nadd > mmax) {
       // keep the leading min(2 nb, mmax - nb) Ritz vectors (and their K and G images)
@@ -360,6 +366,14 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (h->phase_on) {
+    double tp = 0.0, tr = 0.0;
+    for (auto& pr : pre_marks) tp += pm.ms(pr.first, pr.second);
+    for (auto& pr : rr_marks) tr += pm.ms(pr.first, pr.second);
+    h->phase_ms[TOBK_PHASE_EIGEN_PRECOND] = tp;
+    h->phase_ms[TOBK_PHASE_EIGEN_RR] = tr;
+    h->phase_ms[TOBK_PHASE_EIGEN_ITERS] = it + 1;
+  }
   if (info) {
     info->iterations = it + 1;
     info->converged = converged ? 1 : 0;

@@ -80,6 +80,9 @@ struct tobk_handle {
   double prof_ms[TOBK_KC_COUNT] = {0};
   long long prof_cnt[TOBK_KC_COUNT] = {0};
   double prof_units[TOBK_KC_COUNT] = {0};  // DOF x RHS processed by the timed launches
+  // phase timing of compute_buckling (CUDA events on the stream; see tobk_phase_read)
+  bool phase_on = false;
+  double phase_ms[TOBK_PHASE_COUNT] = {0};
 
   double compliance = 0.0;
   double lam_host[64];
@@ -121,5 +124,30 @@ void prof_end(tobk_handle* h);
 void prof_flush(tobk_handle* h);
 int fail(tobk_handle* h, int code, const std::string& msg);
 int check_cuda(tobk_handle* h, const char* where);
+
+// CUDA events recorded on the handle's stream while phase timing is on (no-ops otherwise); read
+// them only after the stream has passed the last mark.
+struct PhaseMarks {
+  tobk_handle* h;
+  std::vector<cudaEvent_t> ev;
+  explicit PhaseMarks(tobk_handle* hh) : h(hh) {}
+  int mark() {
+    if (!h->phase_on) return -1;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, h->stream);
+    ev.push_back(e);
+    return (int)ev.size() - 1;
+  }
+  double ms(int a, int b) const {
+    if (a < 0 || b < 0 || a >= (int)ev.size() || b >= (int)ev.size()) return 0.0;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+  ~PhaseMarks() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
 
 }  // namespace tobk

@@ -147,6 +147,9 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
   tobk_solve_info ei{};
   double lam_h[64];
   int rc = TOBK_OK;
+  PhaseMarks pm(h);
+  const int m_begin = pm.mark();
+  int m_eig = -1, m_prolong = -1, m_solve = -1;
   double* num = h->dscal + 768;   // [q]
   double* den = h->dscal + 832;   // [q]
   double* lraw = h->dscal + 896;  // [q]
@@ -155,6 +158,7 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     double* Phi = h->lv[0].b;     // [q][n] scratch
     rc = eigen_solve(h, 0, q, Phi, lam_h, &ei);
     if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+    m_eig = m_prolong = m_solve = pm.mark();
     double* KP = h->xwork;
     apply_K_level(h, 0, Phi, KP, q, n);
     launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
@@ -166,6 +170,7 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     double* Psi = h->lv[l].b;
     rc = eigen_solve(h, l, q, Psi, lam_h, &ei);
     if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+    m_eig = pm.mark();
     // step 2: Psi^j = I^j_{j+1} Psi^{j+1}
     for (int j = l; j >= 1; --j) {
       Level& C = h->lv[j];
@@ -184,9 +189,11 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     for (int i = 0; i < q; ++i) s_h[i] = (lam_h[i] > 0.0 && std::isfinite(lam_h[i])) ? -1.0 / lam_h[i] : 0.0;
     cudaMemcpyAsync(den, s_h, sizeof(double) * q, cudaMemcpyHostToDevice, st);
     ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), q), 256, 0, st>>>(h->lv[0].b, den, Phi, n);
+    m_prolong = pm.mark();
     tobk_solve_info si{};
     int src = pcg_solve(h, 0, rhs, Phi, q, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &si);
     if (src && src != TOBK_E_NOT_CONVERGED) return src;
+    m_solve = pm.mark();
     // step 4: Rayleigh quotients lambda_i = -phi^T K phi / phi^T G phi
     double* KP = h->lv[0].z;
     double* GP = h->lv[0].t;
@@ -199,10 +206,17 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     ei.iterations += si.iterations;
   }
   cudaMemcpyAsync(h->hscal, h->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
+  const int m_end = pm.mark();
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
   int crc = check_cuda(h, "compute_buckling");
   if (crc) return crc;
+  if (h->phase_on) {
+    h->phase_ms[TOBK_PHASE_EIGEN] = pm.ms(m_begin, m_eig);
+    h->phase_ms[TOBK_PHASE_PROLONG] = pm.ms(m_eig, m_prolong);
+    h->phase_ms[TOBK_PHASE_FINE_SOLVE] = pm.ms(m_prolong, m_solve);
+    h->phase_ms[TOBK_PHASE_RQ] = pm.ms(m_solve, m_end);
+  }
   for (int i = 0; i < q; ++i) h->lam_host[i] = h->hscal[i];
   if (lambda)
     for (int i = 0; i < q; ++i) lambda[i] = h->lam_host[i];

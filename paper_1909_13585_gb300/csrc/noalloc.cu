@@ -16,6 +16,7 @@
 
 #include "../../include/tobk.h"
 #include "device_common.cuh"
+#include "unit_element.h"
 
 namespace tobk {
 
@@ -39,6 +40,13 @@ struct FineOpFromDensity {
   __device__ __forceinline__ double entry(int64_t, int r, int c) const { return M[r * Dims<DIM>::ND + c]; }
 };
 
+// X read with its fixed DOFs taken as zero: the residual is that of the free-DOF system K_ff x_f
+struct LoadFree {
+  const double* v;
+  const uint8_t* fixed;
+  __device__ __forceinline__ double operator()(int64_t i) const { return fixed[i] ? 0.0 : __ldg(v + i); }
+};
+
 template <int DIM>
 __global__ void __launch_bounds__(256) k_residual_noalloc(const __grid_constant__ FineOpFromDensity<DIM> op,
                                                           const double* __restrict__ B,
@@ -56,7 +64,7 @@ __global__ void __launch_bounds__(256) k_residual_noalloc(const __grid_constant_
     double acc[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
-    gather_rows<DIM, double>(op, i, j, k, LoadVec<double>{X + off}, acc);
+    gather_rows<DIM, double>(op, i, j, k, LoadFree{X + off, op.fixed}, acc);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const int64_t idx = DIM * node + c;
@@ -74,82 +82,18 @@ __global__ void __launch_bounds__(256) k_residual_noalloc(const __grid_constant_
 
 namespace {
 
-// Unit-modulus element stiffness K_e0 = sum_gp w |J| B^T D B of the unit Q4 (plane stress) or H8
-// element, 2-point Gauss rule per axis, written into a caller-provided array (no heap use).
-template <int DIM>
-void element_stiffness_on_stack(double nu, double* Ke) {
-  constexpr int NN = Dims<DIM>::NN, ND = Dims<DIM>::ND, NV = Dims<DIM>::NV;
-  double D[NV * NV] = {0.0};
-  if (DIM == 2) {
-    const double c = 1.0 / (1.0 - nu * nu);
-    D[0] = c;
-    D[1] = c * nu;
-    D[NV] = c * nu;
-    D[NV + 1] = c;
-    D[2 * NV + 2] = c * (1.0 - nu) / 2.0;
-  } else {
-    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    const double mu = 1.0 / (2.0 * (1.0 + nu));
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) D[a * NV + b] = lam + (a == b ? 2.0 * mu : 0.0);
-    for (int a = 3; a < NV; ++a) D[a * NV + a] = mu;
-  }
-  for (int q = 0; q < ND * ND; ++q) Ke[q] = 0.0;
-  const double g = 1.0 / std::sqrt(3.0);
-  const double wdet = DIM == 2 ? 0.25 : 0.125;
-  for (int gp = 0; gp < NN; ++gp) {
-    double xg[3] = {((gp >> 0) & 1) ? g : -g, ((gp >> 1) & 1) ? g : -g, ((gp >> 2) & 1) ? g : -g};
-    double dN[DIM][NN];
-    for (int l = 0; l < NN; ++l) {
-      const double xl[3] = {corner_x(l) ? 1.0 : -1.0, corner_y(l) ? 1.0 : -1.0, corner_z(l) ? 1.0 : -1.0};
-      for (int a = 0; a < DIM; ++a) {
-        double v = xl[a] / (DIM == 2 ? 4.0 : 8.0);
-        for (int b = 0; b < DIM; ++b)
-          if (b != a) v *= 1.0 + xl[b] * xg[b];
-        dN[a][l] = 2.0 * v;
-      }
-    }
-    double B[NV][ND];
-    for (int a = 0; a < NV; ++a)
-      for (int r = 0; r < ND; ++r) B[a][r] = 0.0;
-    for (int l = 0; l < NN; ++l) {
-      if (DIM == 2) {
-        B[0][2 * l] = dN[0][l];
-        B[1][2 * l + 1] = dN[1][l];
-        B[2][2 * l] = dN[1][l];
-        B[2][2 * l + 1] = dN[0][l];
-      } else {
-        B[0][3 * l] = dN[0][l];
-        B[1][3 * l + 1] = dN[1][l];
-        B[2][3 * l + 2] = dN[DIM - 1][l];
-        B[3][3 * l] = dN[1][l];
-        B[3][3 * l + 1] = dN[0][l];
-        B[4][3 * l + 1] = dN[DIM - 1][l];
-        B[4][3 * l + 2] = dN[1][l];
-        B[5][3 * l] = dN[DIM - 1][l];
-        B[5][3 * l + 2] = dN[0][l];
-      }
-    }
-    for (int r = 0; r < ND; ++r)
-      for (int c = 0; c < ND; ++c) {
-        double s = 0.0;
-        for (int a = 0; a < NV; ++a)
-          for (int b = 0; b < NV; ++b) s += B[a][r] * D[a * NV + b] * B[b][c];
-        Ke[r * ND + c] += wdet * s;
-      }
-  }
-}
-
 std::mutex g_setup_mutex;
 constexpr int kMaxDevices = 64;
 double* g_partial_addr[kMaxDevices] = {nullptr};
 unsigned* g_counter_addr[kMaxDevices] = {nullptr};
 
-// Device addresses of the scratch arrays, looked up once per device (with that device current).
-int scratch_for_device(int dev, double** partial, unsigned** counters) {
+// Device addresses of the scratch arrays on device dev (current), looked up on the first call and
+// again whenever `refresh` is set (the caller's stream is not capturing), so that a module reloaded
+// after a device reset is seen.
+int scratch_for_device(int dev, bool refresh, double** partial, unsigned** counters) {
   if (dev < 0 || dev >= kMaxDevices) return TOBK_E_ARG;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partial_addr[dev]) {
+  if (!g_partial_addr[dev] || refresh) {
     void* p = nullptr;
     void* c = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_partial) != cudaSuccess ||
@@ -176,7 +120,7 @@ void launch_noalloc(const tobk_desc& d, const double* x, const uint8_t* fixed, c
   op.penal = d.penal;
   op.E0 = d.E0;
   op.Emin = d.Emin;
-  element_stiffness_on_stack<DIM>(d.nu, op.M);
+  unit_element::stiffness(DIM, d.nu, op.M);
   const int64_t want = (op.g.nnode + 255) / 256;
   const unsigned blocks = (unsigned)(want < kNoAllocBlocks ? want : kNoAllocBlocks);
   note_launch();
@@ -193,6 +137,10 @@ extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, con
   if (desc->dim != 2 && desc->dim != 3) return TOBK_E_ARG;
   for (int a = 0; a < desc->dim; ++a)
     if (desc->nel[a] < 1) return TOBK_E_ARG;
+  // the material checks of tobk_create: a Poisson ratio of 1/2 or more makes the 3D Lame constant
+  // infinite, a non-positive modulus or p < 1 leaves K(x) without meaning
+  if (!(desc->nu > -1.0 && desc->nu < 0.5) || !(desc->E0 > 0.0) || !(desc->Emin > 0.0) || !(desc->penal >= 1.0))
+    return TOBK_E_ARG;
   // the built-in scratch holds kNoAllocMaxRhs right-hand sides; larger blocks are rejected
   if (nrhs < 1 || nrhs > kNoAllocMaxRhs) return TOBK_E_ARG;
   int dev = 0;
@@ -200,12 +148,14 @@ extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, con
     cudaGetLastError();
     return TOBK_E_CUDA;
   }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
   double* partial = nullptr;
   unsigned* counters = nullptr;
-  if (scratch_for_device(dev, &partial, &counters) != TOBK_OK) {
+  if (scratch_for_device(dev, cs == cudaStreamCaptureStatusNone, &partial, &counters) != TOBK_OK) {
     return TOBK_E_CUDA;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // the arrival counters must start at zero (an interrupted earlier call could have left them set)
   cudaMemsetAsync(counters, 0, sizeof(unsigned) * kNoAllocMaxRhs, s);
   if (desc->dim == 2)

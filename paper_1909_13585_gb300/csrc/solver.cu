@@ -10,6 +10,7 @@
 #include <string>
 
 #include "handle.h"
+#include "unit_element.h"
 
 namespace tobk {
 
@@ -30,85 +31,22 @@ struct ActiveRhsScope {
 // element tables (Gauss-Legendre 2-point rule per axis; exact for Q4/H8 on unit elements)
 // ================================================================================================
 ElementTables make_element_tables(int dim, double nu) {
+  namespace ue = unit_element;
   ElementTables t;
   t.dim = dim;
-  t.nn = 1 << dim;
-  t.nd = dim * t.nn;
+  t.nn = ue::nodes(dim);
+  t.nd = ue::dofs(dim);
   t.ngp = t.nn;
-  t.nv = dim == 2 ? 3 : 6;
+  t.nv = ue::voigt(dim);
   const int nn = t.nn, nd = t.nd, nv = t.nv;
-  // natural coordinates (+-1) of the local nodes, Q4 order then the same on the upper face
-  auto xi_node = [&](int l, int a) -> double {
-    const int cx = ((l & 3) == 1 || (l & 3) == 2) ? 1 : 0;
-    const int cy = ((l & 3) >= 2) ? 1 : 0;
-    const int cz = l >> 2;
-    const int c = a == 0 ? cx : (a == 1 ? cy : cz);
-    return c ? 1.0 : -1.0;
-  };
-  const double g = 1.0 / std::sqrt(3.0);
-  t.wdet = std::pow(0.5, dim);  // weight 1 per point, |J| = (1/2)^dim on the unit element
+  auto xi_node = ue::xi_node;
+  t.wdet = ue::weight_det(dim);
   t.dN.assign((size_t)t.ngp * dim * nn, 0.0);
-  for (int q = 0; q < t.ngp; ++q) {
-    double gp[3];
-    for (int a = 0; a < dim; ++a) gp[a] = ((q >> a) & 1) ? g : -g;
-    for (int l = 0; l < nn; ++l)
-      for (int a = 0; a < dim; ++a) {
-        double v = xi_node(l, a) / std::pow(2.0, dim);
-        for (int b = 0; b < dim; ++b)
-          if (b != a) v *= 1.0 + xi_node(l, b) * gp[b];
-        t.dN[((size_t)q * dim + a) * nn + l] = 2.0 * v;  // d/dx = 2 d/dxi on the unit element
-      }
-  }
-  // unit-modulus constitutive matrix; Voigt order 2D [xx yy xy], 3D [xx yy zz xy yz zx]
+  for (int q = 0; q < t.ngp; ++q) ue::shape_gradients(dim, q, &t.dN[(size_t)q * dim * nn]);
   t.D.assign((size_t)nv * nv, 0.0);
-  if (dim == 2) {
-    const double c = 1.0 / (1.0 - nu * nu);
-    t.D[0] = c;
-    t.D[1] = c * nu;
-    t.D[3] = c * nu;
-    t.D[4] = c;
-    t.D[8] = c * (1.0 - nu) / 2.0;
-  } else {
-    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    const double mu = 1.0 / (2.0 * (1.0 + nu));
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) t.D[a * 6 + b] = lam + (a == b ? 2.0 * mu : 0.0);
-    for (int a = 3; a < 6; ++a) t.D[a * 6 + a] = mu;
-  }
-  // K_e0 = sum_gp wdet B^T D B
+  ue::constitutive(dim, nu, t.D.data());
   t.Ke0.assign((size_t)nd * nd, 0.0);
-  std::vector<double> B((size_t)nv * nd);
-  for (int q = 0; q < t.ngp; ++q) {
-    std::fill(B.begin(), B.end(), 0.0);
-    const double* dn = &t.dN[(size_t)q * dim * nn];
-    for (int l = 0; l < nn; ++l) {
-      const double dx = dn[0 * nn + l], dy = dn[1 * nn + l];
-      if (dim == 2) {
-        B[0 * nd + 2 * l] = dx;
-        B[1 * nd + 2 * l + 1] = dy;
-        B[2 * nd + 2 * l] = dy;
-        B[2 * nd + 2 * l + 1] = dx;
-      } else {
-        const double dz = dn[2 * nn + l];
-        B[0 * nd + 3 * l] = dx;
-        B[1 * nd + 3 * l + 1] = dy;
-        B[2 * nd + 3 * l + 2] = dz;
-        B[3 * nd + 3 * l] = dy;
-        B[3 * nd + 3 * l + 1] = dx;
-        B[4 * nd + 3 * l + 1] = dz;
-        B[4 * nd + 3 * l + 2] = dy;
-        B[5 * nd + 3 * l] = dz;
-        B[5 * nd + 3 * l + 2] = dx;
-      }
-    }
-    for (int r = 0; r < nd; ++r)
-      for (int c = 0; c < nd; ++c) {
-        double s = 0.0;
-        for (int a = 0; a < nv; ++a)
-          for (int b = 0; b < nv; ++b) s += B[a * nd + r] * t.D[a * nv + b] * B[b * nd + c];
-        t.Ke0[(size_t)r * nd + c] += t.wdet * s;
-      }
-  }
+  ue::stiffness(dim, nu, t.Ke0.data());
   // interpolation weights child node -> coarse element node, per child position
   t.W.assign((size_t)nn * nn * nn, 0.0);
   for (int kc = 0; kc < nn; ++kc)

@@ -125,10 +125,43 @@ def save_weights(net, torch, path):
              out_scale=net.output_scale())
 
 
+WEIGHT_KEYS = ("nel", "levels", "channels", "params", "adam_m", "adam_v", "step", "out_scale")
+
+
+def read_weights(path):
+    """Reads a weights file written by save_weights and checks it on the host: a readable .npz
+    archive with every key, FP32 parameter and Adam-moment vectors of one common length, finite
+    values, a positive output scale.  Raises ValueError naming what is wrong."""
+    try:
+        with np.load(path) as z:
+            data = {k: z[k] for k in z.files}
+    except Exception as e:  # truncated or foreign files fail inside numpy / zipfile
+        raise ValueError(f"weights file {path!r} is not a readable .npz archive ({type(e).__name__}: {e})") from None
+    missing = [k for k in WEIGHT_KEYS if k not in data]
+    if missing:
+        raise ValueError(f"weights file {path!r} lacks {', '.join(missing)}")
+    params = data["params"]
+    if params.dtype != np.float32 or params.ndim != 1:
+        raise ValueError(f"weights file {path!r}: params must be a 1-D float32 vector, got {params.dtype} {params.shape}")
+    for k in ("adam_m", "adam_v"):
+        if data[k].dtype != np.float32 or data[k].shape != params.shape:
+            raise ValueError(f"weights file {path!r}: {k} does not match params ({data[k].dtype} {data[k].shape})")
+    if not (np.all(np.isfinite(params)) and np.isfinite(float(data["out_scale"])) and float(data["out_scale"]) > 0):
+        raise ValueError(f"weights file {path!r} holds non-finite parameters or a bad output scale")
+    return data
+
+
 def load_weights(pkg, torch, path, stream=None):
-    z = np.load(path)
+    """A network restored from a weights file; ValueError if the file is damaged or was written for
+    another architecture (its parameter count differs from the network it describes)."""
+    z = read_weights(path)
     net = pkg.UNet(tuple(int(v) for v in z["nel"]), int(z["levels"]), tuple(int(v) for v in z["channels"]),
                    stream=stream)
+    if net.num_params != z["params"].size:
+        n = net.num_params
+        net.close()
+        raise ValueError(f"weights file {path!r} holds {z['params'].size} parameters, the network it describes "
+                         f"needs {n}")
     net.set_state(torch.from_numpy(z["params"]), torch.from_numpy(z["adam_m"]), torch.from_numpy(z["adam_v"]),
                   int(z["step"]))
     net.set_output_scale(float(z["out_scale"]))

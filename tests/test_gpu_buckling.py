@@ -39,6 +39,14 @@ def _check_modes(op, Phi_gpu, Phi_or, lam, gap_tol=1e-4):
             assert Phi_or[op.free, i] @ (Kf @ P[:, i]) > 0
 
 
+def _gated(lam_coarse, q, gap_tol=1e-4):
+    """Indices whose coarse load factor is isolated (relative gap > gap_tol): their fine Rayleigh
+    quotients are unique.  At most two of the q may fall in clusters."""
+    ok = _gaps(lam_coarse) > gap_tol
+    assert ok.sum() >= q - 2, (ok.sum(), lam_coarse)
+    return ok
+
+
 def _run(p, **kw):
     torch, pkg = require_gpu()
     s = pkg.Solver(p, **kw)
@@ -59,7 +67,10 @@ EXACT_CASES = [
 @pytest.mark.parametrize("name,make", EXACT_CASES, ids=[c[0] for c in EXACT_CASES])
 def test_exact_lba_matches_oracle(name, make):
     p = make()
-    s, pkg, J, lam, Phi, info = _run(p)
+    # the library stops at its own residual <= eig_tol; evaluated again by the oracle in another
+    # summation order the residual can differ in its last digits, so the library is asked for
+    # 0.5e-8 and the oracle checks the Appendix A tolerance 1e-8
+    s, pkg, J, lam, Phi, info = _run(p, eig_tol=0.5e-8)
     op = lba.Problem(p)
     u, Jo = lba.linear_analysis(op)
     lam_o, Phi_o, Gf = lba.exact_lba(op, u, p.num_modes)
@@ -67,7 +78,7 @@ def test_exact_lba_matches_oracle(name, make):
     assert info["converged"] == 1
     _check_modes(op, Phi, Phi_o, lam_o)
     for i in range(p.num_modes):
-        assert lba.eig_residual(op.Kf, Gf, lam[i], Phi[op.free, i]) < 1e-7
+        assert lba.eig_residual(op.Kf, Gf, lam[i], Phi[op.free, i]) <= 1e-8
 
 
 ML_CASES = [
@@ -85,12 +96,9 @@ def test_multilevel_lba_matches_oracle(name, make):
     op = lba.Problem(p)
     u, _ = lba.linear_analysis(op)
     ml = lba.multilevel_lba(op, u, p.num_modes, p.eig_level)
-    g = _gaps(ml["lam_coarse"])
     # the fine Rayleigh quotients are unique only when the coarse eigenvectors are
-    if np.all(g > 1e-4):
-        assert np.allclose(lam, ml["lam"], rtol=1e-6), (lam, ml["lam"])
-    else:
-        assert lam[0] == pytest.approx(ml["lam"][0], rel=1e-3)
+    ok = _gated(ml["lam_coarse"], p.num_modes)
+    assert np.allclose(lam[ok], ml["lam"][ok], rtol=1e-6, atol=0), (lam, ml["lam"])
     assert np.all(np.diff(lam) >= 0)
     assert lam[0] >= lba.exact_lba(op, u, 1)[0][0] * (1 - 1e-9)   # Rayleigh bound
 
@@ -159,4 +167,30 @@ def test_fp32_vcycle_and_fused_load_adjoint_pipeline(dim):
     dlam_o, dJ_o, _ = sensitivity.sensitivities(op, u, lam, Phi)
     assert rel_err(dJ, dJ_o) < 1e-6
     for i in range(p.num_modes):
+        assert rel_err(dlam[i], dlam_o[i]) < 1e-5, i
+
+
+@pytest.mark.parametrize("name,make", [EXACT_CASES[2], ML_CASES[2]], ids=["cant8x4x4_exact", "cant16x8x8_l2"])
+def test_3d_sensitivities_full_chain_against_oracle_pairs(name, make):
+    """3D full chain: the GPU's load factors and sensitivities against the oracle's own linear
+    analysis, LBA (exact or multilevel) and sensitivities, nothing of the GPU fed to the oracle;
+    gated on isolated load factors."""
+    p = make()
+    s, pkg, J, lam, Phi, info = _run(p)
+    dlam, dJ, _ = s.compute_sensitivities()
+    op = lba.Problem(p)
+    u, Jo = lba.linear_analysis(op)
+    assert J == pytest.approx(Jo, rel=1e-7)
+    if p.eig_level == 1:
+        lam_o, Phi_o, _ = lba.exact_lba(op, u, p.num_modes)
+        ok = _gaps(lam_o) > 1e-4
+    else:
+        ml = lba.multilevel_lba(op, u, p.num_modes, p.eig_level)
+        lam_o, Phi_o = ml["lam"], ml["Phi"]
+        ok = _gated(ml["lam_coarse"], p.num_modes) & (_gaps(lam_o) > 1e-4)
+    assert ok.sum() >= p.num_modes - 2
+    assert np.allclose(lam[ok], lam_o[ok], rtol=1e-6, atol=0), (lam, lam_o)
+    dlam_o, dJ_o, _ = sensitivity.sensitivities(op, u, lam_o, Phi_o)
+    assert rel_err(dJ, dJ_o) < 1e-6
+    for i in np.flatnonzero(ok):
         assert rel_err(dlam[i], dlam_o[i]) < 1e-5, i

@@ -113,3 +113,91 @@ def test_invalid_densities_and_call_order_are_rejected():
     s.compute_buckling()
     s.compute_sensitivities()
     s.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# failure detection: host-side causes, library status codes (nothing here can fault the GPU; every
+# loop in the library is bounded by max_iter)
+# ------------------------------------------------------------------------------------------------
+def _raw_solve(s):
+    """tobk_solve_equilibrium through the C-ABI, returning its status instead of raising."""
+    import ctypes as C
+    from paper_1909_13585_gb300 import binding
+    J = C.c_double()
+    info = binding.tobk_solve_info()
+    rc = s.lib.tobk_solve_equilibrium(s.h, C.byref(J), C.byref(info))
+    msg = s.lib.tobk_last_error(s.h).decode()
+    return rc, J.value, info.as_dict(), msg
+
+
+def test_iteration_limit_returns_not_converged_with_the_last_iterate():
+    """max_iter too small: TOBK_E_NOT_CONVERGED, info filled (iterations, converged = 0, the true
+    relative residual of the returned iterate), and u holds that iterate (its residual, evaluated by
+    the oracle, is the one reported)."""
+    torch, pkg = require_gpu()
+    p = _column(48, 16)
+    s = pkg.Solver(p, max_iter=4)
+    rc, J, info, msg = _raw_solve(s)
+    assert rc == pkg.binding.TOBK_E_NOT_CONVERGED, (rc, msg)
+    assert "iteration limit" in msg
+    assert info["converged"] == 0 and 1 <= info["iterations"] <= 4
+    assert np.isfinite(info["rel_residual"]) and info["rel_residual"] > 1e-8
+    u = s.get_field(pkg.TOBK_FIELD_U)
+    op = lba.Problem(p)
+    res = np.linalg.norm(p.f[op.free] - op.Kf @ u[op.free]) / np.linalg.norm(p.f[op.free])
+    assert res == pytest.approx(info["rel_residual"], rel=1e-6)
+    # the same handle then converges with a sufficient limit
+    s2 = pkg.Solver(p)
+    J2, info2 = s2.solve_equilibrium()
+    assert info2["converged"] == 1
+    s.close(); s2.close()
+
+
+def test_no_dirichlet_dofs_ends_with_an_error_status():
+    """No fixed DOF: K is singular (rigid-body modes) and the load has a net force, so K u = f has no
+    solution.  The solve must come back with a failure status (breakdown, non-finite or not
+    converged), not hang and not report success."""
+    import time
+    torch, pkg = require_gpu()
+    p = _column(32, 16)
+    s = pkg.Solver(p, max_iter=100)
+    s.set_fixed(np.zeros(p.num_dofs, dtype=np.uint8))
+    s.set_load(p.f)
+    s.set_densities(p.x)
+    t0 = time.perf_counter()
+    rc, J, info, msg = _raw_solve(s)
+    assert time.perf_counter() - t0 < 60.0
+    assert rc in (pkg.binding.TOBK_E_BREAKDOWN, pkg.binding.TOBK_E_NONFINITE, pkg.binding.TOBK_E_NOT_CONVERGED), (rc, msg)
+    assert info["converged"] == 0
+    s.close()
+
+
+def test_nan_in_the_load_is_reported_as_non_finite():
+    """A NaN entry in f reaches the CG scalars; the solve stops with TOBK_E_NONFINITE."""
+    torch, pkg = require_gpu()
+    p = _column(32, 16)
+    s = pkg.Solver(p)
+    f = p.f.copy()
+    f[np.flatnonzero(p.fixed == 0)[5]] = np.nan
+    s.set_load(f)
+    rc, J, info, msg = _raw_solve(s)
+    assert rc == pkg.binding.TOBK_E_NONFINITE, (rc, msg)
+    assert "non-finite" in msg
+    s.close()
+
+
+def test_weights_for_another_architecture_are_rejected(tmp_path):
+    """A well-formed weights file whose parameter vector does not fit the network it names: a clean
+    ValueError before any parameter reaches the library."""
+    torch, pkg = require_gpu()
+    from paper_1909_13585_gb300 import learned
+    z = dict(learned.read_weights(learned.WEIGHTS))
+    z["channels"] = np.array([16, 32, 64, 128])
+    path = str(tmp_path / "other.npz")
+    np.savez(path, **z)
+    with pytest.raises(ValueError, match="parameters"):
+        learned.load_weights(pkg, torch, path)
+    net = pkg.UNet(tuple(int(v) for v in z["nel"]), int(z["levels"]), tuple(int(v) for v in z["channels"]))
+    with pytest.raises(ValueError, match="float32 of length"):
+        net.set_state(torch.zeros(10, dtype=torch.float32))
+    net.close()

@@ -2,8 +2,9 @@
 column480x160 in FP64 (the headline step) against the oracle's direct solves and multilevel LBA;
 cantilever96x48x48 with the FP32 V-cycle and the fused load + adjoint launch through properties that
 hold at any size, evaluated with the oracle's assembly-free K v and G v (true residuals of u and of
-the adjoint systems, the Rayleigh quotients and K-normalisation of the returned modes); sampled
-designs of the 64-design batch."""
+the adjoint systems, the Rayleigh quotients and K-normalisation of the returned modes), and the same
+recipe at 32 x 16 x 16 against the oracle output by output; sampled designs of the 64-design batch,
+their residuals allowed the rounding difference of two residual evaluations."""
 import numpy as np
 import pytest
 
@@ -23,6 +24,22 @@ def _gaps(lam):
         if i + 1 < lam.size:
             g[i] = min(g[i], abs(lam[i + 1] - lam[i]) / abs(lam[i]))
     return g
+
+
+def _residual_rounding_bound(p, U, B):
+    """How far two evaluations of ||b - K u|| / ||b|| in different summation orders can differ: each
+    computed residual entry is within gamma_k (|b| + |K| |u|) of the exact one (k = entries summed per
+    row, unit roundoff 2^-53), so two programs differ by at most twice that, relative to ||b||.  At a
+    residual of 1e-8 of a SIMP system with a modulus contrast of 1e6, |K| |u| is many times |b|, so this
+    is a visible part of the tolerance."""
+    K = assembly.assemble_K(p.nel, p.dim, p.x, p.nu, p.penal, p.E0, p.Emin)
+    free = p.fixed == 0
+    A = abs(K)
+    k = int(np.diff(K.tocsr().indptr).max()) + 1
+    gamma = k * 2.0 ** -53 / (1 - k * 2.0 ** -53)
+    U, B = np.atleast_2d(U), np.atleast_2d(B)
+    return max(2 * gamma * np.linalg.norm((np.abs(B[r]) + A @ np.abs(U[r]))[free]) / np.linalg.norm(B[r][free])
+               for r in range(B.shape[0]))
 
 
 def _relres(p, U, B):
@@ -47,6 +64,7 @@ def test_column480x160_fp64_step_matches_oracle():
     assert J == pytest.approx(Jo, rel=1e-7)
     ml = lba.multilevel_lba(op, uo, p.num_modes, p.eig_level)
     ok = _gaps(ml["lam_coarse"]) > 1e-4
+    assert ok.sum() >= p.num_modes - 2, ml["lam_coarse"]
     assert np.allclose(lam[ok], ml["lam"][ok], rtol=1e-6, atol=0), (lam, ml["lam"])
     # sensitivities of the well-separated pairs (same formula on the oracle's pairs)
     dlo, dJo, _ = sensitivity.sensitivities(op, uo, ml["lam"], ml["Phi"])
@@ -89,6 +107,44 @@ def test_cantilever96x48x48_fp32_fused_properties():
     s.close()
 
 
+def test_cantilever_recipe_32x16x16_fp32_fused_against_oracle():
+    """The cantilever96x48x48 recipe (seed 2, filter radius 3, volume fraction 0.3, clamped face
+    x = 0, top load) at a third of the linear size, where the oracle's sparse direct solves still
+    finish: the mixed-precision form (FP32 V-cycle in FP64 flexible CG, fused load + adjoint launch,
+    eigenproblem two levels down, q = 12) against the FP64 oracle, output by output.  At the full
+    size the oracle's direct factorisation does not fit (its 3D fill grows much faster than the
+    grid) and its CG does not reach a tight tolerance, so the test above checks properties there."""
+    torch, pkg = require_gpu()
+    p = synthetic.cantilever_3d(32, 16, 16, seed=2, radius=3, volfrac=0.3, mg_levels=4, eig_level=3,
+                                num_modes=12)
+    s = pkg.Solver(p, stream=torch.cuda.Stream(), precision=pkg.TOBK_FP32_VCYCLE, fuse_load_adjoint=1)
+    J, _ = s.solve_equilibrium()
+    lam, info = s.compute_buckling()
+    assert info["converged"] == 1
+    dlam, dJ, sinfo = s.compute_sensitivities()
+    assert sinfo["converged"] == 1
+    u = s.get_field(pkg.TOBK_FIELD_U)
+    op = lba.Problem(p)
+    uo, Jo = lba.linear_analysis(op)
+    ml = lba.multilevel_lba(op, uo, p.num_modes, p.eig_level)
+    dlo, dJo, _ = sensitivity.sensitivities(op, uo, ml["lam"], ml["Phi"])
+    # per-output errors against the FP64 oracle
+    e = (u - uo)[op.free]
+    err_u = np.sqrt(e @ (op.Kf @ e)) / np.sqrt(uo[op.free] @ (op.Kf @ uo[op.free]))
+    ok = (_gaps(ml["lam_coarse"]) > 1e-4) & (_gaps(ml["lam"]) > 1e-4)
+    assert ok.sum() >= p.num_modes - 2, ml["lam_coarse"]
+    err_lam = np.abs(lam[ok] / ml["lam"][ok] - 1).max()
+    err_dlam = max(np.abs(dlam[i] - dlo[i]).max() / np.abs(dlo[i]).max() for i in np.flatnonzero(ok))
+    err_dJ = np.abs(dJ - dJo).max() / np.abs(dJo).max()
+    print("cantilever32x16x16 fp32_vcycle vs FP64 oracle: u (energy) %.2e, lambda %.2e, dlambda %.2e, dJ %.2e"
+          % (err_u, err_lam, err_dlam, err_dJ))
+    assert _relres(p, u, p.f) <= 1e-8
+    assert err_u < 1e-6 and J == pytest.approx(Jo, rel=1e-7)
+    assert err_lam < 1e-6
+    assert err_dlam < 1e-5 and err_dJ < 1e-6
+    s.close()
+
+
 def test_batch64_sampled_designs_against_oracle():
     torch, pkg = require_gpu()
     problems = synthetic.batch_configs(64)
@@ -112,5 +168,5 @@ def test_batch64_sampled_designs_against_oracle():
     for d in (0, 17, 40, 63):
         p = problems[d]
         Xd = Xh[nrhs * off[d]: nrhs * off[d + 1]].reshape(nrhs, p.num_dofs)
-        assert _relres(p, Xd, blocks[d]) <= 1e-8 * 1.01, d
+        assert _relres(p, Xd, blocks[d]) <= 1e-8 + _residual_rounding_bound(p, Xd, blocks[d]), d
     bt.close()

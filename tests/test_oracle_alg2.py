@@ -48,3 +48,37 @@ def test_ritz_load_factors_bound_each_level_and_the_fine_grid():
     # the per-level smoothing does not make the first load factor worse than Sec. 2.1's
     plain = lba.multilevel_lba(op, u, 4, 3)
     assert r["lam"][0] <= plain["lam"][0] * (1 + 1e-3)
+
+
+def test_kaczmarz_single_row_is_the_orthogonal_projection():
+    """One row a: the update psi - (a . psi / |a|^2) a is the orthogonal projection onto a^perp, so
+    a . psi vanishes afterwards and the change is parallel to a with that exact coefficient (a row
+    scaled by |a| instead of |a|^2 fails the first check)."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(5)
+    n = 9
+    a = np.zeros(n)
+    a[[1, 4, 7]] = rng.standard_normal(3) * 3.0
+    A = sp.csr_matrix(a[None, :])
+    psi = rng.standard_normal((n, 2))
+    out = lba.kaczmarz(A, psi, 1)
+    assert np.abs(a @ out).max() <= 1e-13 * np.abs(a).max() * np.abs(psi).max()
+    coef = (a @ psi) / (a @ a)
+    assert np.allclose(out, psi - np.outer(a, coef), rtol=0, atol=1e-14)
+
+
+def test_kaczmarz_converges_to_the_null_space_projection():
+    """For A psi = 0 every Kaczmarz step is an orthogonal projection onto a hyperplane that contains
+    null(A), and the iterate stays in psi0 + range(A^T): the sweeps converge to the orthogonal
+    projection of psi0 onto null(A), (I - A^+ A) psi0 (A^+ from the SVD); a null vector is left
+    unchanged."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((4, 10))
+    psi0 = rng.standard_normal((10, 3))
+    U, S, Vt = np.linalg.svd(A)
+    Pnull = np.eye(10) - Vt[:4].T @ Vt[:4]
+    out = lba.kaczmarz(sp.csr_matrix(A), psi0, 400)
+    assert np.allclose(out, Pnull @ psi0, rtol=0, atol=1e-10)
+    v = Pnull @ rng.standard_normal(10)
+    assert np.allclose(lba.kaczmarz(sp.csr_matrix(A), v[:, None], 3)[:, 0], v, rtol=0, atol=1e-13)

@@ -277,3 +277,117 @@ def test_elementwise_apply_equals_assembled_operators():
         yg = assembly.apply_G(p.nel, p.dim, p.x, u, p.nu, p.penal, p.E0, p.Emin, V)
         assert np.allclose(yk, (K @ V.T).T, rtol=1e-12, atol=1e-12 * np.abs(yk).max())
         assert np.allclose(yg, (G @ V.T).T, rtol=1e-12, atol=1e-12 * np.abs(yg).max())
+
+
+# ------------------------------------------------------------------------------------------------
+# multilevel chain (Sec. 2.1 steps 1-4) pinned by an independent coarse-mesh analysis
+# ------------------------------------------------------------------------------------------------
+def _roller_column(nel, dim, load, x0=0.8, mg_levels=3, eig_level=2, q=4):
+    """Uniform column, long axis last (y in 2D, z in 3D): the base nodes ride on rollers (normal DOF
+    fixed), one base corner is pinned in-plane (and in 3D a second base corner in y, which removes
+    the rotation about z).  A compressive load of total magnitude `load` acts on the top as
+    consistent nodal loads.  The exact solution is linear (uniform uniaxial stress, free Poisson
+    expansion), so it lies in every coarse space of the hierarchy."""
+    nd = [v + 1 for v in nel[:dim]]
+    nn = int(np.prod(nd))
+    n = dim * nn
+    ids = np.arange(nn).reshape(nd[::-1])          # [z][y][x] or [y][x]
+    fixed = np.zeros(n, dtype=np.uint8)
+    f = np.zeros(n)
+    if dim == 2:
+        base, top = ids[0, :], ids[-1, :]
+        w = np.full(nd[0], 1.0 / nel[0]); w[0] *= 0.5; w[-1] *= 0.5
+        fixed[2 * base + 1] = 1
+        fixed[2 * ids[0, 0]] = 1
+        f[2 * top + 1] = -load * w
+    else:
+        base, top = ids[0].reshape(-1), ids[-1].reshape(-1)
+        wx = np.ones(nd[0]); wx[0] = wx[-1] = 0.5
+        wy = np.ones(nd[1]); wy[0] = wy[-1] = 0.5
+        w = np.outer(wy, wx).reshape(-1) / float(nel[0] * nel[1])
+        fixed[3 * base + 2] = 1
+        fixed[3 * ids[0, 0, 0]] = fixed[3 * ids[0, 0, 0] + 1] = 1
+        fixed[3 * ids[0, 0, -1] + 1] = 1
+        f[3 * top + 2] = -load * w
+    m = int(np.prod(nel[:dim]))
+    nel3 = tuple(nel[:dim]) + ((1,) if dim == 2 else ())
+    return synthetic.Problem(name="roller_column", dim=dim, nel=nel3, x=np.full(m, x0), f=f, fixed=fixed,
+                             mg_levels=mg_levels, eig_level=eig_level, num_modes=q)
+
+
+CHAIN_CASES = [(2, (8, 24), 2), (2, (8, 32), 3), (3, (4, 4, 8), 2)]
+
+
+@pytest.mark.parametrize("dim,nel,level", CHAIN_CASES)
+def test_multilevel_coarse_pencil_is_the_rediscretised_coarse_problem(dim, nel, level):
+    """Uniform density and uniform stress: the Galerkin pencil (K^l, G^l) that multilevel_lba builds
+    is the pencil of the same column re-meshed with elements 2^(l-1) times larger (Sec. 2.1 step 1;
+    nested conforming spaces, exact quadrature).  On unit elements the coarse column is 2^(l-1)
+    times smaller, so the load that keeps the stress is scaled by 2^-(l-1)(d-1); K and G then agree up
+    to the common factor 2^(l-1)(d-2), which leaves the load factors unchanged.  The coarse load
+    factors of multilevel_lba must equal those of an independent exact LBA of that coarse column."""
+    q = 4
+    p = _roller_column(nel, dim, 1.0, eig_level=level, mg_levels=level)
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    ml = lba.multilevel_lba(op, u, q, level)
+    s = 2 ** (level - 1)
+    pc = _roller_column(tuple(v // s for v in nel), dim, 1.0 / s ** (dim - 1), mg_levels=1, eig_level=1)
+    opc = lba.Problem(pc)
+    uc, _ = lba.linear_analysis(opc)
+    lam_c, Phi_c, Gfc = lba.exact_lba(opc, uc, q)
+    scale = float(s) ** (dim - 2)
+    assert np.allclose(ml["Kl"].toarray(), scale * opc.Kf.toarray(), rtol=0, atol=1e-12 * abs(opc.Kf).max())
+    assert np.allclose(ml["Gl"].toarray(), scale * Gfc.toarray(), rtol=0, atol=1e-12 * abs(Gfc).max())
+    assert np.allclose(ml["lam_coarse"], lam_c, rtol=1e-10, atol=0), (ml["lam_coarse"], lam_c)
+
+
+@pytest.mark.parametrize("dim,nel,level", CHAIN_CASES)
+def test_multilevel_prolongated_modes_interpolate_the_coarse_modes(dim, nel, level):
+    """Sec. 2.1 step 2 (Psi^j = I^j_{j+1} Psi^{j+1} down to Omega_1): at fine nodes that coincide
+    with nodes of Omega_l the prolongated modes take the coarse nodal values; at the midpoint of two
+    coinciding nodes along an axis they take their mean (bilinear / trilinear interpolation)."""
+    q = 3
+    p = _roller_column(nel, dim, 1.0, eig_level=level, mg_levels=level)
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    ml = lba.multilevel_lba(op, u, q, level)
+    s = 2 ** (level - 1)
+    ndf = [v + 1 for v in nel[:dim]]
+    ndc = [v // s + 1 for v in nel[:dim]]
+    fixed_c = ml["fixed_levels"][-1]
+    Pc = np.zeros((dim * int(np.prod(ndc)), q))
+    Pc[fixed_c == 0] = ml["Psi_coarse"]
+    Pf = ml["Psi"].reshape(ndf[::-1] + [dim, q])
+    Pc = Pc.reshape(ndc[::-1] + [dim, q])
+    sl = tuple(slice(None, None, s) for _ in range(dim))
+    assert np.allclose(Pf[sl], Pc, rtol=0, atol=1e-13 * np.abs(Pc).max())
+    # midpoints along the first axis (x): mean of the two coarse neighbours
+    if s >= 2:
+        mid = tuple([slice(None, None, s)] * (dim - 1) + [slice(s // 2, None, s)])
+        avg = 0.5 * (Pc[tuple([slice(None)] * (dim - 1) + [slice(0, -1)])]
+                     + Pc[tuple([slice(None)] * (dim - 1) + [slice(1, None)])])
+        assert np.allclose(Pf[mid], avg, rtol=0, atol=1e-13 * np.abs(Pc).max())
+
+
+@pytest.mark.parametrize("dim,nel,level", CHAIN_CASES)
+def test_multilevel_fine_step_brackets_the_load_factor(dim, nel, level):
+    """Sec. 2.1 steps 3-4 are one inverse-iteration step of K^{-1}(-G) from the prolongated modes.
+    Under pure compression -G is positive semi-definite, so the operator is positive semi-definite in
+    the K inner product and one step cannot lower its Rayleigh quotient mu = 1/lambda: the fine load
+    factor lies between the exact one (Rayleigh bound) and the coarse one (which is the fine Rayleigh
+    quotient of the prolongated mode, by the Galerkin construction)."""
+    q = 3
+    p = _roller_column(nel, dim, 1.0, eig_level=level, mg_levels=level)
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    Gf = lba.assembly.restrict_free(op.G(u), op.fixed)
+    assert np.linalg.eigvalsh(-Gf.toarray()).min() > -1e-12 * abs(Gf).max()   # -G is PSD here
+    ml = lba.multilevel_lba(op, u, q, level)
+    lam_exact, _, _ = lba.exact_lba(op, u, 1)
+    psi = ml["Psi"][op.free, 0]
+    rq_psi = -(psi @ (op.Kf @ psi)) / (psi @ (Gf @ psi))
+    assert rq_psi == pytest.approx(ml["lam_coarse"][0], rel=1e-10)
+    assert lam_exact[0] * (1 - 1e-10) <= ml["lam"][0] <= ml["lam_coarse"][0] * (1 + 1e-10)
+    # and the step really moves it (the coarse mode is not a fine eigenvector)
+    assert ml["lam"][0] < ml["lam_coarse"][0] * (1 - 1e-6)

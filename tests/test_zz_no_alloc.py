@@ -58,6 +58,77 @@ def test_noalloc_residual_matches_solver(dim):
     s.close()
 
 
+def _desc(binding, lib, p, **kw):
+    d = binding.tobk_desc()
+    lib.tobk_default_desc(C.byref(d))
+    d.dim, d.nel[0], d.nel[1] = p.dim, p.nel[0], p.nel[1]
+    d.nel[2] = p.nel[2] if p.dim == 3 else 1
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def test_noalloc_sixteen_rhs_on_a_grid_wider_than_its_block_cap():
+    """nrhs = 16 (the limit) on a 2D grid of 263,425 nodes, more than the 1024 blocks x 256 threads
+    of the fixed grid width (the grid-stride loop covers the rest), for arbitrary B and X: every
+    relres agrees with the oracle's element-by-element K X.  Entries of X at fixed DOFs are read as
+    zero, so setting them changes nothing."""
+    torch, pkg = require_gpu()
+    from paper_1909_13585_gb300 import binding
+    from oracle import assembly
+    lib = binding.load()
+    p = synthetic.column_2d(1024, 256, seed=33, radius=2, mg_levels=1)
+    assert p.num_nodes > 1024 * 256
+    nr = 16
+    rng = np.random.default_rng(8)
+    Bh = rng.standard_normal((nr, p.num_dofs))
+    Xh = rng.standard_normal((nr, p.num_dofs))
+    free = p.fixed == 0
+    Xf = Xh.copy()
+    Xf[:, ~free] = 0.0
+    KX = assembly.apply_K(p.nel, p.dim, p.x, p.nu, p.penal, p.E0, p.Emin, Xf)
+    ref = np.linalg.norm((Bh - KX)[:, free], axis=1) / np.linalg.norm(Bh[:, free], axis=1)
+    d = _desc(binding, lib, p)
+    x = to_dev(torch, p.x)
+    fixed = to_dev(torch, p.fixed.astype(np.uint8))
+    B, X = to_dev(torch, Bh), to_dev(torch, Xh)
+    for call in range(2):
+        relres = torch.full((nr,), -1.0, dtype=torch.float64, device="cuda")
+        rc = lib.tobk_residual_noalloc(C.byref(d), x.data_ptr(), fixed.data_ptr(), B.data_ptr(), X.data_ptr(), nr,
+                                       relres.data_ptr(), None)
+        assert rc == binding.TOBK_OK
+        torch.cuda.synchronize()
+        assert np.allclose(relres.cpu().numpy(), ref, rtol=1e-12, atol=0)
+
+
+def test_noalloc_rejects_bad_arguments():
+    """Null pointers, empty grids and the material checks of tobk_create are rejected with
+    TOBK_E_ARG before anything is launched."""
+    torch, pkg = require_gpu()
+    from paper_1909_13585_gb300 import binding
+    lib = binding.load()
+    p = synthetic.cantilever_3d(4, 2, 2, seed=1, radius=1.5, volfrac=0.5, mg_levels=1)
+    buf = torch.zeros(p.num_dofs, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    x = to_dev(torch, p.x)
+    fixed = to_dev(torch, p.fixed.astype(np.uint8))
+
+    def call(d, xp=x.data_ptr(), bp=buf.data_ptr(), op=out.data_ptr(), nr=1):
+        return lib.tobk_residual_noalloc(C.byref(d), xp, fixed.data_ptr(), bp, bp, nr, op, None)
+
+    assert call(_desc(binding, lib, p)) == binding.TOBK_OK
+    for kw in (dict(nu=0.5), dict(nu=-1.0), dict(E0=0.0), dict(Emin=-1e-6), dict(penal=0.5), dict(dim=4)):
+        assert call(_desc(binding, lib, p, **kw)) == binding.TOBK_E_ARG, kw
+    d = _desc(binding, lib, p)
+    d.nel[1] = 0
+    assert call(d) == binding.TOBK_E_ARG
+    assert call(_desc(binding, lib, p), xp=None) == binding.TOBK_E_ARG
+    assert call(_desc(binding, lib, p), bp=None) == binding.TOBK_E_ARG
+    assert call(_desc(binding, lib, p), op=None) == binding.TOBK_E_ARG
+    assert call(_desc(binding, lib, p), nr=0) == binding.TOBK_E_ARG
+    torch.cuda.synchronize()
+
+
 def test_noalloc_rejects_too_many_rhs():
     torch, pkg = require_gpu()
     from paper_1909_13585_gb300 import binding
