@@ -62,11 +62,12 @@ def rhs_per_step(p, fused=False):
     return 1 + (p.num_modes if p.eig_level > 1 else 0) + p.num_modes + (1 if fused else 0)
 
 
-def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush):
-    """The same step on another workload / precision, device-timed per step with an L2 flush."""
+def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush, outputs=None, **overrides):
+    """The same step on another workload / precision, device-timed per step with an L2 flush.  If
+    `outputs` is a dict, the last step's u, load factors and sensitivities are stored in it (host)."""
     p = synthetic.config(name)
     stream = torch.cuda.Stream(device=dev)
-    s = pkg.Solver(p, stream=stream, precision=precision, fuse_load_adjoint=1 if fused else 0)
+    s = pkg.Solver(p, stream=stream, precision=precision, fuse_load_adjoint=1 if fused else 0, **overrides)
     x_d = torch.from_numpy(p.x).to(dev)
     q, m = p.num_modes, p.num_elements
     dlam_d = torch.zeros((q, m), dtype=torch.float64, device=dev)
@@ -76,9 +77,10 @@ def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush):
     def step():
         s.set_densities(x_d)
         _, i1 = s.solve_equilibrium()
-        _, i2 = s.compute_buckling()
+        lam, i2 = s.compute_buckling()
         _, _, i3 = s.compute_sensitivities(dlam_d, dJ_d)
         info.update(la_iters=i1["iterations"], buckling_iters=i2["iterations"], adjoint_iters=i3["iterations"])
+        info["_lam"] = lam
 
     for _ in range(warmup):
         step()
@@ -92,10 +94,71 @@ def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     units = p.num_dofs * rhs_per_step(p, fused)
+    lam = info.pop("_lam")
+    if outputs is not None:
+        outputs.update(u=s.get_field(pkg.TOBK_FIELD_U), lam=np.array(lam), dlam=dlam_d.cpu().numpy(),
+                       dJ=dJ_d.cpu().numpy())
     s.close()
     return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "dofs": p.num_dofs,
             "rhs_per_step": rhs_per_step(p, fused), "precision": "fp64" if precision == 0 else "fp32_vcycle",
-            "fused_load_adjoint": bool(fused), "steps": steps, "warmup": warmup, **info}
+            "fused_load_adjoint": bool(fused), "steps": steps, "warmup": warmup,
+            **({"smoother": "damped_jacobi", "omega": overrides.get("omega", 0.6)} if overrides.get("smoother") == 0
+               else {}), **info}
+
+
+def output_errors(test, ref):
+    """Per-output differences of one form's results from another's (same design): relative 2-norm
+    of u, largest relative load-factor difference, and the sensitivities' largest difference scaled
+    by their largest magnitude (per mode, worst mode)."""
+    du = float(np.linalg.norm(test["u"] - ref["u"]) / np.linalg.norm(ref["u"]))
+    dl = float(np.abs(test["lam"] / ref["lam"] - 1).max())
+    dd = float(max(np.abs(test["dlam"][i] - ref["dlam"][i]).max() / np.abs(ref["dlam"][i]).max()
+                   for i in range(ref["dlam"].shape[0])))
+    dj = float(np.abs(test["dJ"] - ref["dJ"]).max() / np.abs(ref["dJ"]).max())
+    return {"u_rel_l2": du, "lambda_rel_max": dl, "dlambda_rel_max": dd, "dJ_rel_max": dj}
+
+
+def measure_batch_sequential_fp64(pkg, torch, steps, warmup, dev, flush, count=64, nadj=6):
+    """The batch's designs and right-hand sides solved one design at a time by the plain FP64 mgPCG
+    (one handle per design, its 1 + nadj right-hand sides in one multi-RHS solve): the baseline of the
+    batched form.  One step = set every design's densities + solve every design."""
+    problems = synthetic.batch_configs(count)
+    stream = torch.cuda.Stream(device=dev)
+    B = batch_rhs(pkg, torch, problems, nadj, dev, stream)
+    nr = 1 + nadj
+    solvers, views, xs = [], [], []
+    off = 0
+    for p in problems:
+        s = pkg.Solver(p, stream=stream, max_rhs=nr)
+        solvers.append(s)
+        views.append((B[off: off + nr * p.num_dofs], torch.zeros(nr * p.num_dofs, dtype=torch.float64, device=dev)))
+        xs.append(torch.from_numpy(p.x).to(dev))
+        off += nr * p.num_dofs
+    its = []
+
+    def step():
+        its.clear()
+        for s, (b, xo), x in zip(solvers, views, xs):
+            s.set_densities(x)
+            xo.zero_()
+            its.append(s.solve(1, b, xo, nr)["iterations"])
+
+    for _ in range(warmup):
+        step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    dofs = int(sum(p.num_dofs for p in problems))
+    for s in solvers:
+        s.close()
+    return {"value": dofs * nr / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "designs": count, "dofs_total": dofs,
+            "rhs_per_design": nr, "precision": "fp64", "iterations_max": max(its), "steps": steps, "warmup": warmup}
 
 
 def batch_rhs(pkg, torch, problems, nadj, dev, stream):
@@ -519,9 +582,20 @@ def ours(args):
         fs, fw = args.steps, max(3, args.warmup)
         forms["column480x160_fp32_vcycle"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP32_VCYCLE, False,
                                                           fs, fw, dev, flush)
+        forms["column480x160_fp64_damped_jacobi"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP64, False,
+                                                                 fs, fw, dev, flush, smoother=0, omega=0.6)
+        forms["column60x20_fp64_exact_lba"] = measure_form(pkg, torch, "column60x20", pkg.TOBK_FP64, False,
+                                                           fs, fw, dev, flush)
+        o64, o32 = {}, {}
+        forms["cantilever96x48x48_fp64"] = measure_form(pkg, torch, "cantilever96x48x48", pkg.TOBK_FP64, False,
+                                                        fs, fw, dev, flush, outputs=o64)
         forms["cantilever96x48x48_fp32_vcycle_fused"] = measure_form(pkg, torch, "cantilever96x48x48",
-                                                                     pkg.TOBK_FP32_VCYCLE, True, fs, fw, dev, flush)
+                                                                     pkg.TOBK_FP32_VCYCLE, True, fs, fw, dev, flush,
+                                                                     outputs=o32)
+        forms["cantilever96x48x48_fp32_vcycle_fused"]["error_vs_fp64_path"] = output_errors(o32, o64)
+        del o64, o32
         forms["batch64_column2d_fp32_vcycle"] = measure_batch(pkg, torch, fs, fw, dev, flush)
+        forms["batch64_column2d_fp64_one_at_a_time"] = measure_batch_sequential_fp64(pkg, torch, fs, fw, dev, flush)
         forms["cantilever128x64x64_learned_warm_start"] = measure_learned(pkg, torch, dev, flush)
 
     cpu = None

@@ -102,6 +102,17 @@ typedef struct {
                         nu_post in D^{-1} K over [lambda_max / cheb_ratio, lambda_max], lambda_max
                         measured per level and design by power iteration); nu_pre, nu_post <= 8 */
   double cheb_ratio; /* lambda_max / lambda_min of the Chebyshev interval (e.g. 10) */
+  /* Algorithm 2 (Appendix A) on the way from Omega_l to Omega_1, after each prolongation
+   * Psi^j = I^j_{j+1} Psi^{j+1} (levels l-1 down to 1; multilevel path only): */
+  int kaczmarz_sweeps; /* Kaczmarz sweeps on (K^j + sigma G^j) psi = 0 for every mode, sigma the smallest
+                          load factor known from the level above; rows in 3^d node-colour order (colour
+                          (i mod 3) + 3 (j mod 3) + 9 (k mod 3) ascending, the d rows of a node in turn);
+                          0 = none (Sec. 2.1 steps 1-4) */
+  int ritz_levels;   /* 1: Rayleigh-Ritz projection of (K^j, G^j) on span Psi^j after the smoothing */
+  int fine_steps;    /* inverse-iteration steps K phi_{k+1} = G phi_k on Omega_1 (eq.
+                        PInvIt-GeneralInteration with the preconditioner P = K, each solve by mgPCG to
+                        rtol), each followed by the Rayleigh quotients; 1 (or 0) = the single fine solve
+                        of Sec. 2.1 step 3 */
 } tobk_desc;
 
 typedef enum { TOBK_SMOOTHER_JACOBI = 0, TOBK_SMOOTHER_CHEBYSHEV = 1 } tobk_smoother;
@@ -120,7 +131,8 @@ typedef struct tobk_handle tobk_handle;
 
 /* Fills *desc with defaults: nu 0.3, E0 1, Emin 1e-6, p 3, 3 levels, eig_level 1, 6 modes, FP64,
  * rtol 1e-8, max_iter 500, omega 0.6, nu_pre = nu_post = 2, eig_tol 1e-8, eig_max_iter 200,
- * max_rhs = num_modes + 4.  Returns TOBK_OK. */
+ * max_rhs = num_modes + 4, no Kaczmarz sweeps, no per-level Ritz projection, one fine solve.
+ * Returns TOBK_OK. */
 int tobk_default_desc(tobk_desc* desc);
 
 /* Creates a handle on the current CUDA device and the given stream (cudaStream_t; NULL = legacy

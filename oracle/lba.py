@@ -21,7 +21,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import assembly, transfer
+from . import assembly, grid, transfer
 
 
 class Problem:
@@ -144,14 +144,41 @@ def eig_residual(Kf, Gf, lam, phi_free):
 # ------------------------------------------------------------------------------------------------
 # Algorithm 2 with its per-level steps (the optional refinement of Sec. 2.1, Appendix A)
 # ------------------------------------------------------------------------------------------------
-def kaczmarz(A: sp.spmatrix, Psi: np.ndarray, sweeps: int) -> np.ndarray:
+def multicolour_rows(nel, dim, fixed) -> np.ndarray:
+    """A row order for Kaczmarz sweeps on a level (the paper gives none): the free rows grouped by the
+    colour (i mod 3) + 3 (j mod 3) + 9 (k mod 3) of their node (i, j, k), colours ascending, nodes in
+    increasing index within a colour, the d rows of a node in turn.  Returned as indices into the
+    free-DOF numbering.  Rows of different nodes of one colour share no unknown (their nodes are
+    three or more apart along some axis, each row touches only the 3^d surrounding nodes), so their
+    relative order does not change the result."""
+    nd = grid.node_dims(nel, dim)
+    fixed = np.asarray(fixed, dtype=np.uint8)
+    free_index = np.full(fixed.size, -1, dtype=np.int64)
+    free_index[fixed == 0] = np.arange(int((fixed == 0).sum()))
+    nodes = np.arange(int(np.prod(nd[:dim])))
+    i = nodes % nd[0]
+    j = (nodes // nd[0]) % nd[1]
+    k = nodes // (nd[0] * nd[1]) if dim == 3 else np.zeros_like(nodes)
+    colour = i % 3 + 3 * (j % 3) + 9 * (k % 3)
+    order = []
+    for col in range(27 if dim == 3 else 9):
+        for a in nodes[colour == col]:
+            for c in range(dim):
+                r = free_index[dim * a + c]
+                if r >= 0:
+                    order.append(r)
+    return np.asarray(order, dtype=np.int64)
+
+
+def kaczmarz(A: sp.spmatrix, Psi: np.ndarray, sweeps: int, order=None) -> np.ndarray:
     """Kaczmarz sweeps for A psi = 0 on every column of Psi (Appendix A: Gauss-Seidel on A^T A):
-    for the rows i = 0, 1, ... in turn, psi <- psi - (a_i . psi / |a_i|^2) a_i."""
+    for the rows i in turn (`order`, default 0, 1, 2, ...), psi <- psi - (a_i . psi / |a_i|^2) a_i."""
     A = A.tocsr()
     rn = np.asarray(A.multiply(A).sum(axis=1)).ravel()
     Psi = np.array(Psi, dtype=np.float64, copy=True)
+    rows = range(A.shape[0]) if order is None else order
     for _ in range(sweeps):
-        for i in range(A.shape[0]):
+        for i in rows:
             if rn[i] == 0.0:
                 continue
             s, e = A.indptr[i], A.indptr[i + 1]
@@ -173,13 +200,18 @@ def ritz(Kl, Gl, Psi: np.ndarray):
 
 
 def multilevel_lba_refined(op: Problem, u: np.ndarray, q: int, eig_level: int, sweeps: int = 1,
-                           ritz_projection: bool = True, dense_limit: int = 4000):
+                           ritz_projection: bool = True, dense_limit: int = 4000, order: str = "natural",
+                           fine_steps: int = 1):
     """Algorithm 2: the coarse eigenpairs of level eig_level, then on every level j = eig_level-1 down
     to 1 (the fine grid; the printed loop index is garbled): prolongate Psi^j = I^j_{j+1} Psi^{j+1},
     shift by the smallest load factor of the level above, `sweeps` Kaczmarz sweeps on
-    (K^j + shift G^j) psi = 0 for every mode, Rayleigh-Ritz on span Psi^j; finally the fine solve
-    K Phi~ = G Psi and the per-column Rayleigh quotients (lines 15-16).  With sweeps = 0 and no
-    Ritz projection this is Sec. 2.1 steps 1-4 (multilevel_lba)."""
+    (K^j + shift G^j) psi = 0 for every mode (rows in increasing order, or order = "multicolour":
+    multicolour_rows), Rayleigh-Ritz on span Psi^j; finally the fine solve K Phi~ = G Psi and the
+    per-column Rayleigh quotients, normalised and sorted.  fine_steps > 1 repeats the fine solve
+    from the previous step's modes: inverse iteration on Omega_1, eq. PInvIt-GeneralInteration with
+    the preconditioner P = K (then phi - K^{-1}(K + s G) phi = -s K^{-1} G phi, a multiple of the
+    inverse-iteration step whatever the shift s).  With sweeps = 0, no Ritz projection and one fine
+    step this is Sec. 2.1 steps 1-4 (multilevel_lba)."""
     G = op.G(u)
     Gf = assembly.restrict_free(G, op.fixed)
     nels, fixeds, Ps = transfer.hierarchy(op.nel, op.dim, op.fixed, eig_level)
@@ -193,16 +225,18 @@ def multilevel_lba_refined(op: Problem, u: np.ndarray, q: int, eig_level: int, s
     for j in reversed(range(len(Ps))):                               # level j + 1 (1-based) = Omega_{j+1}
         Psi = Ps[j] @ Psi
         if sweeps > 0:
-            Psi = kaczmarz(Ks[j] + Lam.min() * Gs[j], Psi, sweeps)
+            rows = multicolour_rows(nels[j], op.dim, fixeds[j]) if order == "multicolour" else None
+            Psi = kaczmarz(Ks[j] + Lam.min() * Gs[j], Psi, sweeps, rows)
         if ritz_projection:
             Lam, Psi = ritz(Ks[j], Gs[j], Psi)
             if Lam.size < q:
                 raise RuntimeError("Rayleigh-Ritz lost a positive load factor on level %d" % (j + 1))
         levels.append(dict(level=j + 1, lam=Lam.copy(), K=Ks[j], G=Gs[j]))
-    Phi = op.solve(Gf @ Psi)
-    num = np.einsum("ij,ij->j", Phi, op.Kf @ Phi)
-    den = np.einsum("ij,ij->j", Phi, Gf @ Phi)
-    lam = -num / den
-    order = np.argsort(lam)
-    return dict(lam=lam[order], Phi=op.to_full(_normalise_modes(op.Kf, Phi[:, order])), lam_coarse=lam_c,
-                levels=levels, Gf=Gf)
+    for _ in range(max(1, fine_steps)):
+        Phi = op.solve(Gf @ Psi)
+        num = np.einsum("ij,ij->j", Phi, op.Kf @ Phi)
+        den = np.einsum("ij,ij->j", Phi, Gf @ Phi)
+        lam = -num / den
+        srt = np.argsort(lam)
+        lam, Psi = lam[srt], _normalise_modes(op.Kf, Phi[:, srt])
+    return dict(lam=lam, Phi=op.to_full(Psi), lam_coarse=lam_c, levels=levels, Gf=Gf)

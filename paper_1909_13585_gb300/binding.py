@@ -25,7 +25,8 @@ class tobk_desc(C.Structure):
                 ("rtol", C.c_double), ("max_iter", C.c_int), ("omega", C.c_double),
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("eig_tol", C.c_double),
                 ("eig_max_iter", C.c_int), ("max_rhs", C.c_int), ("eig_inner_iters", C.c_int),
-                ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double)]
+                ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double),
+                ("kaczmarz_sweeps", C.c_int), ("ritz_levels", C.c_int), ("fine_steps", C.c_int)]
 
 
 class tobk_solve_info(C.Structure):

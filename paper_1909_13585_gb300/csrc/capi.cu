@@ -46,6 +46,9 @@ int tobk_default_desc(tobk_desc* d) {
   d->fuse_load_adjoint = 0;
   d->smoother = TOBK_SMOOTHER_CHEBYSHEV;
   d->cheb_ratio = 10.0;
+  d->kaczmarz_sweeps = 0;
+  d->ritz_levels = 0;
+  d->fine_steps = 1;
   return TOBK_OK;
 }
 

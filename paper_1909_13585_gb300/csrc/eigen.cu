@@ -287,7 +287,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     if (rc) break;
     if (h->hscal[384] != 0.0) {  // the K-orthonormalised expansion lost rank
       rc = fail(h, TOBK_E_BREAKDOWN,
-                "eigensolver basis lost rank (the level has too few free DOFs for the block of q + 4 vectors)");
+                "eigensolver basis lost rank (the level has fewer free DOFs than the block of q vectors needs)");
       break;
     }
     for (int i = 0; i < kk; ++i) hth[i] = h->hscal[i];
@@ -384,6 +384,70 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   }
   if (rc == TOBK_OK && !converged) rc = fail(h, TOBK_E_NOT_CONVERGED, "eigensolver did not reach eig_tol");
   return rc;
+}
+
+// Rayleigh-Ritz of (K^j, G^j) on span Psi at level j (Algorithm 2, 'R[Psi]'): K-orthonormalise the
+// q columns (Cholesky QR, twice), project H = Psi^T (-G) Psi, decompose it with the dense
+// Rayleigh-Ritz kernels of the eigensolver (FP32 Jacobi + FP64 refinement), rotate Psi onto the
+// Ritz vectors.  Scratch: the level's V-cycle vectors z, t, r (each [rmax][n_j], rmax >= q).
+int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host) {
+  cudaStream_t st = h->stream;
+  const int64_t n = h->lv[j].g.n;
+  const int nb = h->eig_nb, mmax = h->eig_mmax;
+  if (q > nb || q > kRRMax) return fail(h, TOBK_E_ARG, "ritz_level: too many vectors");
+  double* KW = h->lv[j].z;
+  double* Tb = h->lv[j].t;
+  double* GW = h->lv[j].r;
+  double* theta = h->dscal;
+  double* sinfo = h->dscal + 384;
+  double* Cs = h->Cs;
+  double* M = h->Cs + (size_t)mmax * nb;
+  double* Rinv = M + (size_t)nb * nb;
+  double* rrX0 = h->tri;
+  double* rrX1 = rrX0 + (size_t)mmax * mmax;
+  double* rrS = rrX1 + (size_t)mmax * mmax;
+  double* rrR = rrS + (size_t)mmax * mmax;
+  double* rrXw = rrR + (size_t)mmax * mmax;
+  double* rrLam = rrXw + (size_t)mmax * mmax;
+  double* rrDelta = rrLam + mmax;
+  cudaFuncSetAttribute(k_rr_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)rr_finish_smem_bytes(kRRMax, kRRMax));
+  cudaMemsetAsync(sinfo, 0, sizeof(double), st);
+  for (int pass = 0; pass < 2; ++pass) {
+    apply_K_level(h, j, Psi, KW, q, n);
+    launch_gram(Psi, q, KW, q, n, n, M, h->gram_partial, st);
+    ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, q, Rinv, sinfo);
+    launch_combine(Psi, q, Rinv, q, q, 1.0, 0.0, Tb, n, n, st);
+    cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);
+  }
+  apply_G_level(h, j, Psi, GW, q, n);
+  launch_gram(Psi, q, GW, q, n, n, Cs, h->gram_partial, st);
+  ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)q * q), 256, 0, st>>>(Cs, q, q, 0, -1.0, h->Hs, mmax);
+  ::tobk::note_launch(), launch_rr_eig32(h->Hs, q, mmax, nullptr, 0, rrX0, sinfo + 2, st);
+  for (int step = 0; step < kRRRefineSteps; ++step) {
+    const bool last = step == kRRRefineSteps - 1;
+    double* xin = (step & 1) ? rrX1 : rrX0;
+    double* xout = last ? rrXw : ((step & 1) ? rrX0 : rrX1);
+    ::tobk::note_launch(), k_rr_oa_products<<<q, 64, 0, st>>>(h->Hs, mmax, xin, q, rrS, rrR);
+    ::tobk::note_launch(), k_rr_oa_update<<<q, 64, 0, st>>>(xin, rrS, rrR, q, xout, last ? mmax : q,
+                                                            last ? rrLam : nullptr, rrDelta, step == 0);
+  }
+  ::tobk::note_launch(), k_rr_finish<<<1, 256, rr_finish_smem_bytes(q, q), st>>>(h->Hs, mmax, q, q, rrXw, mmax, rrLam,
+                                                                                 rrDelta, theta, h->Ys, mmax);
+  launch_combine(Psi, q, h->Ys, mmax, q, 1.0, 0.0, Tb, n, n, st);
+  cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double) * 512, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  int rc = check_cuda(h, "ritz_level");
+  if (rc) return rc;
+  if (h->hscal[384] != 0.0) return fail(h, TOBK_E_BREAKDOWN, "Ritz projection: the prolongated modes lost rank");
+  for (int i = 0; i < q; ++i) {
+    const double th = h->hscal[i];
+    if (!(th > 0.0) || !std::isfinite(th))
+      return fail(h, TOBK_E_BREAKDOWN, "Ritz projection lost a positive load factor on level " + std::to_string(j + 1));
+    lam_host[i] = 1.0 / th;
+  }
+  return TOBK_OK;
 }
 
 }  // namespace tobk

@@ -56,6 +56,10 @@ struct tobk_handle {
   double *Hs = nullptr, *Bs = nullptr, *Ys = nullptr, *Cs = nullptr, *gram_partial = nullptr;
   double* small_host = nullptr;  // pinned
   double* tri = nullptr;         // scratch of the split small eigensolver (reflectors, T, vectors)
+  // Algorithm 2 smoothing: nodal stencil of K^j + sigma G^j and its squared row norms (sized for the
+  // finest level, allocated only when kaczmarz_sweeps > 0)
+  double* kz_S = nullptr;
+  double* kz_rn2 = nullptr;
   // small scalars
   double* dscal = nullptr;       // device scratch scalars [256]
   double* hscal = nullptr;       // pinned host scratch [256]
@@ -113,6 +117,9 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info);
 int compute_sensitivities(tobk_handle* h, double* dlam, double* dJ, bool out_on_device, tobk_solve_info* info);
 // eigensolver at level j: q lowest positive load factors, modes K_j-normalised -> out [q][n_j]
 int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info);
+// Rayleigh-Ritz projection of (K^j, G^j) on span Psi (q columns, stride n_j; Algorithm 2 'R[Psi]'):
+// Psi is replaced by the K-normalised Ritz vectors, lam_host [q] by their load factors, ascending.
+int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host);
 // G_j v at level j (fine: matrix-free from Gs; coarse: Galerkin Ge)
 void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);
 void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride);

@@ -158,4 +158,15 @@ void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, d
                     double* Y, int64_t n, int64_t stride, cudaStream_t s);
 int gram_partial_blocks(int64_t n);
 
+// ---- Kaczmarz smoothing of prolongated modes (kaczmarz.cu) -----------------------------------------
+// Nodal stencil S of A = K + sigma G at a level and its squared row norms rn2 [n].  K from E_kappa
+// [m] and the unit matrix Ke0 (fine level, Ek != nullptr) or stored element matrices Ke; G from the
+// fine scalar matrices Gs [m][nn*nn] (Gs != nullptr) or stored element matrices Ge.
+void launch_pencil_stencil(const Grid& g, const uint8_t* fixed, const double* Ek, const double* Ke0,
+                           const double* Ke, const double* Gs, const double* Ge, double sigma, double* S,
+                           double* rn2, cudaStream_t s);
+// `sweeps` multicolour Kaczmarz sweeps on A psi = 0 for q modes Psi [q][stride].
+void launch_kaczmarz_sweeps(const Grid& g, const uint8_t* fixed, const double* S, const double* rn2, double* Psi,
+                            int q, int64_t stride, int sweeps, cudaStream_t s);
+
 }  // namespace tobk

@@ -171,39 +171,68 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     rc = eigen_solve(h, l, q, Psi, lam_h, &ei);
     if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
     m_eig = pm.mark();
-    // step 2: Psi^j = I^j_{j+1} Psi^{j+1}
+    // step 2: Psi^j = I^j_{j+1} Psi^{j+1}, and on each finer level the optional steps of
+    // Algorithm 2: Kaczmarz smoothing on K^j + sigma G^j (sigma the smallest load factor known from
+    // the level above) and the Rayleigh-Ritz projection of (K^j, G^j) on span Psi^j
+    const int sweeps = h->desc.kaczmarz_sweeps;
+    const bool ritz = h->desc.ritz_levels != 0;
+    double shift = lam_h[0];
+    for (int i = 1; i < q; ++i) shift = std::min(shift, lam_h[i]);
     for (int j = l; j >= 1; --j) {
       Level& C = h->lv[j];
       Level& F = h->lv[j - 1];
       cudaMemsetAsync(F.b, 0, sizeof(double) * q * F.g.n, st);
       launch_prolong_add(F.g, C.g, F.fixed, C.b, F.b, q, F.g.n, C.g.n, st);
+      if (sweeps > 0) {
+        if (j - 1 == 0)
+          launch_pencil_stencil(F.g, F.fixed, h->Ek, h->d_Ke0, nullptr, h->Gs, nullptr, shift, h->kz_S, h->kz_rn2, st);
+        else
+          launch_pencil_stencil(F.g, F.fixed, nullptr, nullptr, F.Ke, nullptr, F.Ge, shift, h->kz_S, h->kz_rn2, st);
+        launch_kaczmarz_sweeps(F.g, F.fixed, h->kz_S, h->kz_rn2, F.b, q, F.g.n, sweeps, st);
+      }
+      if (ritz) {
+        const int rrc = ritz_level(h, j - 1, q, F.b, lam_h);
+        if (rrc) return rrc;
+        shift = lam_h[0];
+      }
     }
-    // step 3: K Phi = G Psi (one multi-RHS mgPCG solve on the fine grid).  Initial guess
-    // Phi_0 = -Psi / lambda_c: (K + lambda_c G) Psi is the fine residual of the prolongated coarse
-    // pair, and with Galerkin coarse operators its restriction to Omega_l is the coarse eigen
-    // residual (1e-8), so the starting error has no component the coarse space represents.
+    // steps 3-4, repeated fine_steps times (inverse iteration on Omega_1): K Phi = G Psi by one
+    // multi-RHS mgPCG solve, then the Rayleigh quotients lambda_i = -phi^T K phi / phi^T G phi.
+    // Initial guess Phi_0 = -Psi / lambda: for the first step (K + lambda_c G) Psi is the fine
+    // residual of the prolongated coarse pair, and with Galerkin coarse operators its restriction
+    // to Omega_l is the coarse eigen residual (1e-8), so the starting error has no component the
+    // coarse space represents.
+    const int steps = std::max(1, h->desc.fine_steps);
+    const double* src = h->lv[0].b;
     double* rhs = h->bwork;
-    apply_G_level(h, 0, h->lv[0].b, rhs, q, n);
     double* Phi = h->xwork;
-    double s_h[64];
-    for (int i = 0; i < q; ++i) s_h[i] = (lam_h[i] > 0.0 && std::isfinite(lam_h[i])) ? -1.0 / lam_h[i] : 0.0;
-    cudaMemcpyAsync(den, s_h, sizeof(double) * q, cudaMemcpyHostToDevice, st);
-    ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), q), 256, 0, st>>>(h->lv[0].b, den, Phi, n);
-    m_prolong = pm.mark();
-    tobk_solve_info si{};
-    int src = pcg_solve(h, 0, rhs, Phi, q, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &si);
-    if (src && src != TOBK_E_NOT_CONVERGED) return src;
-    m_solve = pm.mark();
-    // step 4: Rayleigh quotients lambda_i = -phi^T K phi / phi^T G phi
-    double* KP = h->lv[0].z;
-    double* GP = h->lv[0].t;
-    apply_K_level(h, 0, Phi, KP, q, n);
-    apply_G_level(h, 0, Phi, GP, q, n);
-    launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
-    launch_coldots(Phi, GP, q, n, n, den, h->gram_partial, st);
-    ::tobk::note_launch(), k_rq<<<1, 64, 0, st>>>(num, den, q, lraw);
-    finalize_modes(h, Phi, lraw, num, h->modes, h->lam);
-    ei.iterations += si.iterations;
+    for (int stp = 0; stp < steps; ++stp) {
+      if (stp > 0) {  // the previous step's normalised modes and load factors
+        src = h->modes;
+        cudaMemcpyAsync(h->hscal, h->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        for (int i = 0; i < q; ++i) lam_h[i] = h->hscal[i];
+      }
+      apply_G_level(h, 0, src, rhs, q, n);
+      double s_h[64];
+      for (int i = 0; i < q; ++i) s_h[i] = (lam_h[i] > 0.0 && std::isfinite(lam_h[i])) ? -1.0 / lam_h[i] : 0.0;
+      cudaMemcpyAsync(den, s_h, sizeof(double) * q, cudaMemcpyHostToDevice, st);
+      ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), q), 256, 0, st>>>(src, den, Phi, n);
+      if (stp == 0) m_prolong = pm.mark();
+      tobk_solve_info si{};
+      int src_rc = pcg_solve(h, 0, rhs, Phi, q, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &si);
+      if (src_rc && src_rc != TOBK_E_NOT_CONVERGED) return src_rc;
+      ei.iterations += si.iterations;
+      if (stp == steps - 1) m_solve = pm.mark();
+      double* KP = h->lv[0].z;
+      double* GP = h->lv[0].t;
+      apply_K_level(h, 0, Phi, KP, q, n);
+      apply_G_level(h, 0, Phi, GP, q, n);
+      launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
+      launch_coldots(Phi, GP, q, n, n, den, h->gram_partial, st);
+      ::tobk::note_launch(), k_rq<<<1, 64, 0, st>>>(num, den, q, lraw);
+      finalize_modes(h, Phi, lraw, num, h->modes, h->lam);
+    }
   }
   cudaMemcpyAsync(h->hscal, h->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
   const int m_end = pm.mark();

@@ -191,6 +191,11 @@ static void layout(tobk_handle* h, Arena& a) {
   const int64_t gp_rows = std::max<int64_t>(gram_partial_blocks(ne), gram_partial_blocks(nf));
   h->gram_partial = a.take<double>((size_t)gp_rows * mm * std::max(mm, nb));
   h->dscal = a.take<double>(1024);
+  if (h->desc.kaczmarz_sweeps > 0 && h->eig > 0) {
+    const int d = h->dim;
+    h->kz_S = a.take<double>((size_t)(d == 2 ? 9 : 27) * d * d * g.nnode);
+    h->kz_rn2 = a.take<double>((size_t)nf);
+  }
 }
 
 int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solve_only) {
@@ -206,6 +211,9 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   if (d->smoother == TOBK_SMOOTHER_CHEBYSHEV && !(d->cheb_ratio > 1.0)) return TOBK_E_ARG;
   if (!(d->nu > -1.0 && d->nu < 0.5) || !(d->E0 > 0.0) || !(d->Emin > 0.0) || !(d->penal >= 1.0)) return TOBK_E_ARG;
   if (d->precision != TOBK_FP64 && d->precision != TOBK_FP32_VCYCLE) return TOBK_E_ARG;
+  if (d->kaczmarz_sweeps < 0 || d->kaczmarz_sweeps > 64 || (d->ritz_levels != 0 && d->ritz_levels != 1) ||
+      d->fine_steps < 0 || d->fine_steps > 64)
+    return TOBK_E_ARG;
   for (int a = 0; a < d->dim; ++a) {
     if (d->nel[a] < 1) return TOBK_E_ARG;
     if (d->nel[a] % (1 << (d->mg_levels - 1)) != 0) return TOBK_E_ARG;
@@ -219,7 +227,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   h->L = d->mg_levels;
   h->eig = d->eig_level - 1;
   h->q = d->num_modes;
-  h->eig_nb = h->q + 4;
+  h->eig_nb = h->q;  // block = wanted pairs: as few iterations as q + 2 or q + 4 (measured), less work each
   h->eig_mmax = 64;
   h->rmax = std::max({d->max_rhs, h->eig_nb, h->q + 1, 1});
   if (h->rmax > kMaxRhs || h->eig_mmax < 2 * h->eig_nb) {

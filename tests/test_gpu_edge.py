@@ -76,16 +76,31 @@ def test_small_grid_single_level():
 
 
 def test_eigen_level_smaller_than_the_block_is_reported():
-    """Two elements up, one across: 8 free DOFs cannot hold the eigensolver's block of q + 4 = 6
-    K-orthonormal vectors and its first expansion; the call reports TOBK_E_BREAKDOWN instead of
-    returning load factors from a rank-deficient basis."""
+    """Two elements up, one across: 8 free DOFs cannot hold the eigensolver's block of q = 9
+    K-orthonormal vectors; the call reports TOBK_E_BREAKDOWN instead of returning load factors from a
+    rank-deficient basis."""
     torch, pkg = require_gpu()
-    p = synthetic.column_2d(2, 1, seed=3, radius=1.0, mg_levels=1, eig_level=1, num_modes=2)
+    p = synthetic.column_2d(2, 1, seed=3, radius=1.0, mg_levels=1, eig_level=1, num_modes=9)
     s = pkg.Solver(p)
     s.solve_equilibrium()
     with pytest.raises(pkg.TobkError) as e:
         s.compute_buckling()
     assert e.value.code == pkg.binding.TOBK_E_BREAKDOWN
+    s.close()
+
+
+def test_eigen_basis_spanning_the_whole_level_is_exact():
+    """Two elements up, one across, q = 2: the eigensolver's basis reaches all 8 free DOFs within a
+    few expansions, so its Ritz pairs are the exact ones (dense oracle)."""
+    torch, pkg = require_gpu()
+    p = synthetic.column_2d(2, 1, seed=3, radius=1.0, mg_levels=1, eig_level=1, num_modes=2)
+    s = pkg.Solver(p)
+    s.solve_equilibrium()
+    lam, info = s.compute_buckling()
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    lam_o, _, _ = lba.exact_lba(op, u, 2)
+    assert np.allclose(lam, lam_o, rtol=1e-8, atol=0), (lam, lam_o)
     s.close()
 
 

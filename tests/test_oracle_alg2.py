@@ -4,6 +4,7 @@ Kaczmarz smoothing and Rayleigh-Ritz, Appendix A): Kaczmarz row projections neve
 (Courant-Fischer for the K-definite pencil), the refinement without smoothing and projection is
 Sec. 2.1 steps 1-4, and the fine load factor keeps its Rayleigh bound."""
 import numpy as np
+import pytest
 import scipy.linalg as sla
 
 import synthetic
@@ -82,3 +83,55 @@ def test_kaczmarz_converges_to_the_null_space_projection():
     assert np.allclose(out, Pnull @ psi0, rtol=0, atol=1e-10)
     v = Pnull @ rng.standard_normal(10)
     assert np.allclose(lba.kaczmarz(sp.csr_matrix(A), v[:, None], 3)[:, 0], v, rtol=0, atol=1e-13)
+
+
+def test_multicolour_order_is_a_permutation_with_disjoint_same_colour_supports():
+    """The multicolour row order visits every free row once, and two rows of different nodes of one
+    colour share no column of the level's pencil, so the rows of one colour commute: reversing the
+    node order inside every colour gives bit-identical sweeps."""
+    p, op, u = _case()
+    nels, fixeds, Ps = lba.transfer.hierarchy(p.nel, p.dim, p.fixed, 3)
+    Gf = lba.assembly.restrict_free(op.G(u), op.fixed)
+    Kl, Gl = (Ps[0].T @ op.Kf @ Ps[0]).tocsr(), (Ps[0].T @ Gf @ Ps[0]).tocsr()
+    A = (Kl + 0.7 * Gl).tocsr()
+    order = lba.multicolour_rows(nels[1], p.dim, fixeds[1])
+    assert np.array_equal(np.sort(order), np.arange(A.shape[0]))
+    nd = lba.grid.node_dims(nels[1], p.dim)
+    free = np.flatnonzero(fixeds[1] == 0)
+    node_of = free // p.dim
+    colour = (node_of % nd[0]) % 3 + 3 * ((node_of // nd[0]) % 3)
+    for col in range(9):
+        rows = order[colour[order] == col]
+        seen = {}
+        for r in rows:
+            for cidx in A.indices[A.indptr[r]:A.indptr[r + 1]]:
+                owner = seen.setdefault(cidx, node_of[r])
+                assert owner == node_of[r], (col, r, cidx)
+    # reversed node order within each colour (rows of one node kept in turn)
+    rev = []
+    for col in range(9):
+        rows = order[colour[order] == col]
+        for node in sorted(set(node_of[rows]), reverse=True):
+            rev.extend(rows[node_of[rows] == node])
+    psi = np.random.default_rng(2).standard_normal((A.shape[0], 3))
+    a = lba.kaczmarz(A, psi, 2, order)
+    b = lba.kaczmarz(A, psi, 2, np.asarray(rev))
+    assert np.array_equal(a, b)
+
+
+def test_inverse_iteration_steps_descend_to_the_exact_load_factor():
+    """fine_steps > 1 repeats the fine solve K Phi = G Phi_prev (eq. PInvIt-GeneralInteration with
+    P = K).  Under pure compression -G is positive semi-definite and every step lowers the smallest
+    Rayleigh quotient (it is an inverse-iteration step of a positive semi-definite operator), never
+    below the exact lambda_1; with the gap of this column the iteration converges to it."""
+    from tests.test_oracle_lba import _roller_column
+    p = _roller_column((8, 32), 2, 1.0, eig_level=3, mg_levels=3)
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    exact, _, _ = lba.exact_lba(op, u, 2)
+    prev = np.inf
+    for k in (1, 2, 3, 6, 30):
+        r = lba.multilevel_lba_refined(op, u, 2, 3, sweeps=0, ritz_projection=False, fine_steps=k)
+        assert exact[0] * (1 - 1e-12) <= r["lam"][0] <= prev * (1 + 1e-12), (k, r["lam"][0], prev)
+        prev = r["lam"][0]
+    assert prev == pytest.approx(exact[0], rel=1e-8)
