@@ -113,7 +113,15 @@ typedef struct {
                         PInvIt-GeneralInteration with the preconditioner P = K, each solve by mgPCG to
                         rtol), each followed by the Rayleigh quotients; 1 (or 0) = the single fine solve
                         of Sec. 2.1 step 3 */
+  int element;       /* tobk_element: the element of the fine grid */
 } tobk_desc;
+
+/* Elements (Sec. 2).  TOBK_ELEMENT_INCOMPATIBLE: Wilson's quadrilateral (2D) and the hexahedron with
+ * 11 interpolation functions per component (3D): the bilinear / trilinear nodal functions plus d
+ * internal modes 1 - xi_k^2 per component, condensed out element by element (the stress stiffness
+ * uses the same condensation, its Gauss-point stresses from the enhanced strain).  Batches and the
+ * learned warm start take TOBK_ELEMENT_PLAIN only. */
+typedef enum { TOBK_ELEMENT_PLAIN = 0, TOBK_ELEMENT_INCOMPATIBLE = 1 } tobk_element;
 
 typedef enum { TOBK_SMOOTHER_JACOBI = 0, TOBK_SMOOTHER_CHEBYSHEV = 1 } tobk_smoother;
 
@@ -131,7 +139,8 @@ typedef struct tobk_handle tobk_handle;
 
 /* Fills *desc with defaults: nu 0.3, E0 1, Emin 1e-6, p 3, 3 levels, eig_level 1, 6 modes, FP64,
  * rtol 1e-8, max_iter 500, omega 0.6, nu_pre = nu_post = 2, eig_tol 1e-8, eig_max_iter 200,
- * max_rhs = num_modes + 4, no Kaczmarz sweeps, no per-level Ritz projection, one fine solve.
+ * max_rhs = num_modes + 4, no Kaczmarz sweeps, no per-level Ritz projection, one fine solve, plain
+ * Q4 / H8 elements.
  * Returns TOBK_OK. */
 int tobk_default_desc(tobk_desc* desc);
 
@@ -358,8 +367,8 @@ int tobk_unet_train_step(tobk_unet* net, const float* x, const double* f, const 
  * cudaMalloc's implicit synchronisation.  It needs no handle and allocates nothing.
  *
  * For r = 0..nrhs-1 writes relres[r] = ||B_r - K(x) X_r||_2 / ||B_r||_2 over the free DOFs of the
- * fine grid described by desc (dim, nel, nu, E0, Emin, penal; other fields ignored), K(x) being the
- * SIMP stiffness of tobk_apply_K at level 1.  Entries of X at fixed DOFs are read as zero (the
+ * fine grid described by desc (dim, nel, nu, E0, Emin, penal, element; other fields ignored), K(x)
+ * being the SIMP stiffness of tobk_apply_K at level 1.  Entries of X at fixed DOFs are read as zero (the
  * residual of the free-DOF system), and when B_r is zero on the free DOFs relres[r] is the absolute
  * residual norm ||K(x) X_r||_2.  x [m], fixed [n] (uint8, 1 = fixed), B and X
  * [nrhs][n] and relres [nrhs] are DEVICE pointers on the current device; the caller owns them.

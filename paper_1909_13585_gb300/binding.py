@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libtobk.so")
 TOBK_OK, TOBK_E_ARG, TOBK_E_STATE, TOBK_E_NOMEM, TOBK_E_CUDA, TOBK_E_NOT_CONVERGED, \
     TOBK_E_BREAKDOWN, TOBK_E_TIMEOUT, TOBK_E_NONFINITE = range(9)
 TOBK_FP64, TOBK_FP32_VCYCLE = 0, 1
+TOBK_ELEMENT_PLAIN, TOBK_ELEMENT_INCOMPATIBLE = 0, 1
 TOBK_FIELD_U, TOBK_FIELD_MODES, TOBK_FIELD_ADJOINT, TOBK_FIELD_ADJOINT_RHS = range(4)
 
 
@@ -26,7 +27,8 @@ class tobk_desc(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("eig_tol", C.c_double),
                 ("eig_max_iter", C.c_int), ("max_rhs", C.c_int), ("eig_inner_iters", C.c_int),
                 ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double),
-                ("kaczmarz_sweeps", C.c_int), ("ritz_levels", C.c_int), ("fine_steps", C.c_int)]
+                ("kaczmarz_sweeps", C.c_int), ("ritz_levels", C.c_int), ("fine_steps", C.c_int),
+                ("element", C.c_int)]
 
 
 class tobk_solve_info(C.Structure):

@@ -201,7 +201,7 @@ int h8_zc(const Grid& g, int nr) {
 }
 
 template <typename T, int MODE>
-void h8_launch(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, const H8Args<T>& a, int nr, int64_t stride,
+void h8_launch(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int element, const H8Args<T>& a, int nr, int64_t stride,
                cudaStream_t s) {
   static bool configured = false;
   const size_t smem = sizeof(H8Smem<T>);
@@ -212,7 +212,7 @@ void h8_launch(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, cons
   const int zc = h8_zc(g, nr), nzc = (g.nn[2] + zc - 1) / zc;
   dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)(nzc * nr));
   note_launch();
-  k_fine_h8<T, MODE><<<grid, kThreads3, smem, s>>>(g, Ek, fixed, h8_consts<T>(nu), a, zc, nzc, stride);
+  k_fine_h8<T, MODE><<<grid, kThreads3, smem, s>>>(g, Ek, fixed, h8_consts<T>(nu, element), a, zc, nzc, stride);
 }
 
 }  // namespace
@@ -224,7 +224,7 @@ int64_t fine_h8_blocks(const Grid& g) {
 }
 
 template <typename T>
-void launch_fine_h8(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int mode, const T* v, const T* b,
+void launch_fine_h8(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int element, int mode, const T* v, const T* b,
                     const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
   H8Args<T> a{};
   a.v = v;
@@ -234,20 +234,20 @@ void launch_fine_h8(const Grid& g, const T* Ek, const uint8_t* fixed, double nu,
   a.sm = sm;
   a.act = active_rhs();
   if (mode == APPLY_KV)
-    h8_launch<T, APPLY_KV>(g, Ek, fixed, nu, a, nr, stride, s);
+    h8_launch<T, APPLY_KV>(g, Ek, fixed, nu, element, a, nr, stride, s);
   else if (mode == APPLY_RES)
-    h8_launch<T, APPLY_RES>(g, Ek, fixed, nu, a, nr, stride, s);
+    h8_launch<T, APPLY_RES>(g, Ek, fixed, nu, element, a, nr, stride, s);
   else
-    h8_launch<T, APPLY_JAC>(g, Ek, fixed, nu, a, nr, stride, s);
+    h8_launch<T, APPLY_JAC>(g, Ek, fixed, nu, element, a, nr, stride, s);
 }
 
-template void launch_fine_h8<double>(const Grid&, const double*, const uint8_t*, double, int, const double*,
+template void launch_fine_h8<double>(const Grid&, const double*, const uint8_t*, double, int, int, const double*,
                                      const double*, const double*, double*, SmoothArgs<double>, int, int64_t,
                                      cudaStream_t);
-template void launch_fine_h8<float>(const Grid&, const float*, const uint8_t*, double, int, const float*, const float*,
+template void launch_fine_h8<float>(const Grid&, const float*, const uint8_t*, double, int, int, const float*, const float*,
                                     const float*, float*, SmoothArgs<float>, int, int64_t, cudaStream_t);
 
-void launch_fine_h8_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, double nu, const double* z,
+void launch_fine_h8_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, double nu, int element, const double* z,
                                  const double* p_old, double* p_new, double* q, int nr, int64_t stride, double* sc,
                                  double* partial, unsigned* counters, int64_t pstride, cudaStream_t s) {
   H8Args<double> a{};
@@ -259,7 +259,7 @@ void launch_fine_h8_cg_direction(const Grid& g, const double* Ek, const uint8_t*
   a.partial = partial;
   a.counters = counters;
   a.pstride = pstride;
-  h8_launch<double, APPLY_CGDIR>(g, Ek, fixed, nu, a, nr, stride, s);
+  h8_launch<double, APPLY_CGDIR>(g, Ek, fixed, nu, element, a, nr, stride, s);
 }
 
 }  // namespace tobk

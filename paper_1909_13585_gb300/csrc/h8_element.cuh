@@ -15,6 +15,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "unit_element.h"
+
 namespace tobk {
 
 template <typename T>
@@ -22,10 +24,26 @@ struct H8Consts {
   T l1, m1;   // mean gradient: lambda/16, mu/16
   T l2, m2;   // linear monomials: lambda/48, mu/48
   T hx;       // xi eta zeta mode: (lambda + 4 mu)/144
+  T icd, ico; // incompatible-mode correction (0 for the plain element), see h8_forces
 };
 
+// Walsh sign s_S(l) of local node l for the mode S given as a bit set over the axes (1 x, 2 y, 4 z)
+inline double h8_walsh_sign(int l, int S) {
+  const int bx = ((l & 3) == 1 || (l & 3) == 2) ? 1 : 0, by = ((l & 3) >= 2) ? 1 : 0, bz = l >> 2;
+  double s = 1.0;
+  if (S & 1) s *= bx ? 1.0 : -1.0;
+  if (S & 2) s *= by ? 1.0 : -1.0;
+  if (S & 4) s *= bz ? 1.0 : -1.0;
+  return s;
+}
+
+// Constants of the factored operator.  For the incompatible-mode hexahedron (Sec. 2) the condensed
+// stiffness K_c differs from the trilinear one only in six bilinear Walsh modes, coupled in three
+// pairs (u.xy, w.yz), (u.zx, v.yz), (v.xy, w.zx): per 64 of the Walsh sums, a diagonal entry icd and a
+// pair coupling ico, here projected out of K_c - K_e0 on the host (their closed forms are
+// -(4/3)(mu + lambda^2 / (lambda + 2 mu)) / 64 and -(4/3) lambda^2 / (lambda + 2 mu) / 64).
 template <typename T>
-inline H8Consts<T> h8_consts(double nu) {
+inline H8Consts<T> h8_consts(double nu, int element = 0) {
   const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   const double mu = 1.0 / (2.0 * (1.0 + nu));
   H8Consts<T> c;
@@ -34,6 +52,26 @@ inline H8Consts<T> h8_consts(double nu) {
   c.l2 = (T)(lam / 48.0);
   c.m2 = (T)(mu / 48.0);
   c.hx = (T)((lam + 4.0 * mu) / 144.0);
+  c.icd = c.ico = (T)0;
+  if (element == 1) {
+    double K0[24 * 24], Kc[24 * 24], A[9 * 24];
+    unit_element::stiffness(3, nu, K0);
+    unit_element::incompatible_tables(3, nu, Kc, A);
+    double gux[24] = {0.0}, gwy[24] = {0.0};  // Walsh vectors of (u, xy) and (w, yz)
+    for (int l = 0; l < 8; ++l) {
+      gux[3 * l + 0] = h8_walsh_sign(l, 1 | 2);
+      gwy[3 * l + 2] = h8_walsh_sign(l, 2 | 4);
+    }
+    double d = 0.0, o = 0.0;
+    for (int a = 0; a < 24; ++a)
+      for (int b = 0; b < 24; ++b) {
+        const double cab = Kc[a * 24 + b] - K0[a * 24 + b];
+        d += gux[a] * cab * gux[b];
+        o += gux[a] * cab * gwy[b];
+      }
+    c.icd = (T)(d / 64.0);  // W^T W = 8 I for the 24 x 24 Walsh matrix W: C = W^T (W C W^T / 64) W
+    c.ico = (T)(o / 64.0);
+  }
   return c;
 }
 
@@ -159,6 +197,15 @@ __device__ __forceinline__ void h8_forces(const T (&v)[3][2][2][2], T E, const H
     D[c][3] = Dxy[c];
     D[c][4] = Dyz[c];
     D[c][5] = Dzx[c];
+  }
+  if (k.icd != T(0)) {  // incompatible modes: the three coupled pairs of bilinear Walsh modes
+    const T a03 = W[0][3], a24 = W[2][4], a05 = W[0][5], a14 = W[1][4], a13 = W[1][3], a25 = W[2][5];
+    D[0][3] += k.icd * a03 + k.ico * a24;
+    D[2][4] += k.icd * a24 + k.ico * a03;
+    D[0][5] += k.icd * a05 + k.ico * a14;
+    D[1][4] += k.icd * a14 + k.ico * a05;
+    D[1][3] += k.icd * a13 + k.ico * a25;
+    D[2][5] += k.icd * a25 + k.ico * a13;
   }
   // the three bilinear monomials act only on W_xyz: D_xyz = (lambda + 4 mu)/144 W_xyz per component
   D[0][6] = k.hx * W[0][6];

@@ -34,6 +34,9 @@ struct tobk_handle {
   float* Ek32 = nullptr;
   double *f = nullptr, *u = nullptr, *u0 = nullptr;
   double *Gs0 = nullptr, *Gs = nullptr;  // [m][nn*nn] stress stiffness (unit modulus / with E_sigma)
+  // incompatible-mode elements: condensation map [d*d][nd], per-element G over the 2^d + d functions
+  // [m][nf*nf] and the condensed unit-modulus stress stiffness [m][nd*nd] (times E_sigma in use)
+  double *d_A = nullptr, *Gfull = nullptr, *Gc0 = nullptr;
   // coarsest dense inverse
   double *Adense = nullptr, *Awork = nullptr, *Ainv = nullptr;
   // multi-RHS CG work (sized for the fine level)

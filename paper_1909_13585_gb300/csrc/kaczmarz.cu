@@ -31,13 +31,15 @@ struct PencilDims {
 // S[((nbr * d + c) * d + c') * nnode + node] = A[d node + c][d nb + c'], nbr = (dx+1) + 3 (dy+1) [+ 9
 // (dz+1)], for A = K + sigma G.  K: fine level from E_kappa [m] and the unit matrix Ke0 [nd*nd]
 // (Ek != nullptr), else stored element matrices Ke [m][nd*nd].  G: fine level from the stored
-// scalar matrices Gs [m][nn*nn] (the operator Gs (x) I_d; Gs != nullptr), else stored Ge [m][nd*nd].
+// scalar matrices Gs [m][nn*nn] (the operator Gs (x) I_d; Gs != nullptr), else stored Ge [m][nd*nd],
+// times Gscale[e] when Gscale != nullptr (the condensed stress stiffness of incompatible modes).
 // rn2 [n] = squared norms of the rows (0 at fixed DOFs).
 template <int DIM>
 __global__ void k_pencil_stencil(Grid g, const uint8_t* __restrict__ fixed, const double* __restrict__ Ek,
                                  const double* __restrict__ Ke0, const double* __restrict__ Ke,
-                                 const double* __restrict__ Gs, const double* __restrict__ Ge, double sigma,
-                                 double* __restrict__ S, double* __restrict__ rn2) {
+                                 const double* __restrict__ Gs, const double* __restrict__ Ge,
+                                 const double* __restrict__ Gscale, double sigma, double* __restrict__ S,
+                                 double* __restrict__ rn2) {
   constexpr int NN = Dims<DIM>::NN, ND = Dims<DIM>::ND, NE = PencilDims<DIM>::NE;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
@@ -53,6 +55,7 @@ __global__ void k_pencil_stencil(Grid g, const uint8_t* __restrict__ fixed, cons
         const int64_t e = ei + (int64_t)g.nel[0] * (ej + (int64_t)g.nel[1] * ek);
         const int ln = local_node(cx, cy, cz);
         const double sk = Ek ? Ek[e] : 1.0;
+        const double sg = Gscale ? Gscale[e] : 1.0;
         for (int lb = 0; lb < NN; ++lb) {
           const int dx = corner_x(lb) - cx, dy = corner_y(lb) - cy, dz = corner_z(lb) - cz;
           const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
@@ -62,7 +65,7 @@ __global__ void k_pencil_stencil(Grid g, const uint8_t* __restrict__ fixed, cons
               if (fixed[DIM * node + c] || fixed[DIM * nb + cc]) continue;
               const int r = ln * DIM + c, col = lb * DIM + cc;
               const double kv = Ek ? sk * Ke0[r * ND + col] : Ke[e * ND * ND + r * ND + col];
-              const double gv = Gs ? (c == cc ? Gs[e * NN * NN + ln * NN + lb] : 0.0) : Ge[e * ND * ND + r * ND + col];
+              const double gv = Gs ? (c == cc ? Gs[e * NN * NN + ln * NN + lb] : 0.0) : sg * Ge[e * ND * ND + r * ND + col];
               S[(int64_t)((nbr * DIM + c) * DIM + cc) * nn + node] += kv + sigma * gv;
             }
         }
@@ -119,14 +122,14 @@ __global__ void __launch_bounds__(128) k_kaczmarz_colour(Grid g, const uint8_t* 
 }
 
 void launch_pencil_stencil(const Grid& g, const uint8_t* fixed, const double* Ek, const double* Ke0,
-                           const double* Ke, const double* Gs, const double* Ge, double sigma, double* S,
-                           double* rn2, cudaStream_t s) {
+                           const double* Ke, const double* Gs, const double* Ge, const double* Gscale, double sigma,
+                           double* S, double* rn2, cudaStream_t s) {
   const unsigned grid = (unsigned)((g.nnode + 127) / 128);
   note_launch();
   if (g.dim == 2)
-    k_pencil_stencil<2><<<grid, 128, 0, s>>>(g, fixed, Ek, Ke0, Ke, Gs, Ge, sigma, S, rn2);
+    k_pencil_stencil<2><<<grid, 128, 0, s>>>(g, fixed, Ek, Ke0, Ke, Gs, Ge, Gscale, sigma, S, rn2);
   else
-    k_pencil_stencil<3><<<grid, 128, 0, s>>>(g, fixed, Ek, Ke0, Ke, Gs, Ge, sigma, S, rn2);
+    k_pencil_stencil<3><<<grid, 128, 0, s>>>(g, fixed, Ek, Ke0, Ke, Gs, Ge, Gscale, sigma, S, rn2);
 }
 
 void launch_kaczmarz_sweeps(const Grid& g, const uint8_t* fixed, const double* S, const double* rn2, double* Psi,

@@ -136,7 +136,7 @@ void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double
     return;
   }
   if (!op.stored && op.g.dim == 3) {
-    launch_fine_h8<double>(op.g, op.scale64, op.fixed, op.nu, mode, v, b, dinv, y, sm, nr, stride, s);
+    launch_fine_h8<double>(op.g, op.scale64, op.fixed, op.nu, op.element, mode, v, b, dinv, y, sm, nr, stride, s);
     return;
   }
   if (op.g.dim == 2)
@@ -156,7 +156,7 @@ void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float
     return;
   }
   if (!op.stored && op.g.dim == 3) {
-    launch_fine_h8<float>(op.g, op.scale32, op.fixed, op.nu, mode, v, b, dinv, y, sm, nr, stride, s);
+    launch_fine_h8<float>(op.g, op.scale32, op.fixed, op.nu, op.element, mode, v, b, dinv, y, sm, nr, stride, s);
     return;
   }
   if (op.g.dim == 2)
@@ -531,7 +531,7 @@ double* launch_dense_invert(double* A, double* work, int64_t n, double* rcp2, cu
 // ================================================================================================
 // Galerkin coarse element matrices: K_c = sum_children W_k^T (masked child K) W_k
 // ================================================================================================
-enum { GAL_FINE_K = 0, GAL_FINE_G = 1, GAL_STORED = 2 };
+enum { GAL_FINE_K = 0, GAL_FINE_G = 1, GAL_STORED = 2, GAL_SCALED_STORED = 3 };
 
 template <int DIM, int SRC>
 __global__ void k_galerkin(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_f, const double* __restrict__ src,
@@ -563,6 +563,8 @@ __global__ void k_galerkin(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_f
       val = src[ef] * T0[row * ND + col];
     else if (SRC == GAL_FINE_G)
       val = (cr == cc) ? src[ef * NN * NN + lr * NN + lc] : 0.0;
+    else if (SRC == GAL_SCALED_STORED)
+      val = T0[ef] * src[ef * ND * ND + row * ND + col];
     else
       val = src[ef * ND * ND + row * ND + col];
     if (fixed_f[DIM * nr_ + cr] || fixed_f[DIM * nc_ + cc]) val = 0.0;
@@ -602,6 +604,10 @@ void launch_galerkin_fine_K(const Grid& gf, const Grid& gc, const uint8_t* fixed
 void launch_galerkin_fine_G(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Gs,
                             const double* W, double* Gc, cudaStream_t s) {
   galerkin_impl<GAL_FINE_G>(gf, gc, fixed_f, Gs, nullptr, W, Gc, s);
+}
+void launch_galerkin_scaled_stored(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Kf,
+                                   const double* scale, const double* W, double* Kc, cudaStream_t s) {
+  galerkin_impl<GAL_SCALED_STORED>(gf, gc, fixed_f, Kf, scale, W, Kc, s);
 }
 void launch_galerkin_stored(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Kf,
                             const double* W, double* Kc, cudaStream_t s) {
@@ -1027,7 +1033,7 @@ void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_
     return;
   }
   if (d.g.dim == 3 && !d.stored) {
-    launch_fine_h8_cg_direction(d.g, d.scale64, d.fixed, d.nu, z, p_old, p_new, q, nr, stride, sc, partial,
+    launch_fine_h8_cg_direction(d.g, d.scale64, d.fixed, d.nu, d.element, z, p_old, p_new, q, nr, stride, sc, partial,
                                 counters + 2 * kMaxRhs, cg_partial_stride(d.g), s);
     return;
   }

@@ -33,6 +33,7 @@ struct LevelOpDesc {
   const double* S64 = nullptr;
   const float* S32 = nullptr;
   double nu = 0.3;  // Poisson ratio (the factored fine H8 operator builds its constants from it)
+  int element = 0;  // tobk_element of the fine level (the factored H8 operator's correction)
 };
 
 // Assembles the per-node stencil of a stored-element-matrix level (rows/columns of fixed DOFs
@@ -112,10 +113,10 @@ int64_t fine_q4_tiles(const Grid& g);
 int64_t fine_h8_blocks(const Grid& g);
 // Factored fine H8 operator: y = K v | b - K v | smoothing step (same contract as launch_apply).
 template <typename T>
-void launch_fine_h8(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int mode, const T* v, const T* b,
+void launch_fine_h8(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int element, int mode, const T* v, const T* b,
                     const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s);
 // CG direction on the fine H8 level in factored form (same contract as launch_cg_direction).
-void launch_fine_h8_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, double nu, const double* z,
+void launch_fine_h8_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, double nu, int element, const double* z,
                                  const double* p_old, double* p_new, double* q, int nr, int64_t stride, double* sc,
                                  double* partial, unsigned* counters, int64_t pstride, cudaStream_t s);
 // CG direction on the fine Q4 level in factored form: p_new = z + beta p_old, q = K p_new,
@@ -158,13 +159,28 @@ void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, d
                     double* Y, int64_t n, int64_t stride, cudaStream_t s);
 int gram_partial_blocks(int64_t n);
 
+// ---- incompatible-mode elements (incompatible.cu) ---------------------------------------------------
+// Gfull [m][nf*nf] and the condensed unit-modulus stress stiffness Gc0 [m][nd*nd] from u.
+void launch_inc_stress(const Grid& g, const double* u, const double* A, const double* dN, const double* D,
+                       double wdet, double* Gfull, double* Gc0, cudaStream_t s);
+// y = sum_e Es[e] Gc0[e] v_e for nr vectors (rows of fixed DOFs zero)
+void launch_inc_apply_g(const Grid& g, const uint8_t* fixed, const double* Gc0, const double* Es, const double* v,
+                        double* y, int nr, int64_t stride, cudaStream_t s);
+// adjoint right-hand side b = phi^T (grad_u G) phi via element vectors ev [m][nd] (masked)
+void launch_inc_adjoint(const Grid& g, const uint8_t* fixed, const double* phi, const double* Es, const double* A,
+                        const double* dN, const double* D, double wdet, double* ev, double* b, cudaStream_t s);
+// Galerkin coarse element matrices from stored fine element matrices times a per-element scale
+void launch_galerkin_scaled_stored(const Grid& gf, const Grid& gc, const uint8_t* fixed_f, const double* Kf,
+                                   const double* scale, const double* W, double* Kc, cudaStream_t s);
+
 // ---- Kaczmarz smoothing of prolongated modes (kaczmarz.cu) -----------------------------------------
 // Nodal stencil S of A = K + sigma G at a level and its squared row norms rn2 [n].  K from E_kappa
 // [m] and the unit matrix Ke0 (fine level, Ek != nullptr) or stored element matrices Ke; G from the
-// fine scalar matrices Gs [m][nn*nn] (Gs != nullptr) or stored element matrices Ge.
+// fine scalar matrices Gs [m][nn*nn] (Gs != nullptr) or stored element matrices Ge, times Gscale[e]
+// when Gscale != nullptr.
 void launch_pencil_stencil(const Grid& g, const uint8_t* fixed, const double* Ek, const double* Ke0,
-                           const double* Ke, const double* Gs, const double* Ge, double sigma, double* S,
-                           double* rn2, cudaStream_t s);
+                           const double* Ke, const double* Gs, const double* Ge, const double* Gscale, double sigma,
+                           double* S, double* rn2, cudaStream_t s);
 // `sweeps` multicolour Kaczmarz sweeps on A psi = 0 for q modes Psi [q][stride].
 void launch_kaczmarz_sweeps(const Grid& g, const uint8_t* fixed, const double* S, const double* rn2, double* Psi,
                             int q, int64_t stride, int sweeps, cudaStream_t s);

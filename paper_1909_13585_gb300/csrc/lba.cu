@@ -184,10 +184,15 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
       cudaMemsetAsync(F.b, 0, sizeof(double) * q * F.g.n, st);
       launch_prolong_add(F.g, C.g, F.fixed, C.b, F.b, q, F.g.n, C.g.n, st);
       if (sweeps > 0) {
-        if (j - 1 == 0)
-          launch_pencil_stencil(F.g, F.fixed, h->Ek, h->d_Ke0, nullptr, h->Gs, nullptr, shift, h->kz_S, h->kz_rn2, st);
+        if (j - 1 == 0 && h->Gc0)
+          launch_pencil_stencil(F.g, F.fixed, h->Ek, h->d_Ke0, nullptr, nullptr, h->Gc0, h->Es, shift, h->kz_S,
+                                h->kz_rn2, st);
+        else if (j - 1 == 0)
+          launch_pencil_stencil(F.g, F.fixed, h->Ek, h->d_Ke0, nullptr, h->Gs, nullptr, nullptr, shift, h->kz_S,
+                                h->kz_rn2, st);
         else
-          launch_pencil_stencil(F.g, F.fixed, nullptr, nullptr, F.Ke, nullptr, F.Ge, shift, h->kz_S, h->kz_rn2, st);
+          launch_pencil_stencil(F.g, F.fixed, nullptr, nullptr, F.Ke, nullptr, F.Ge, nullptr, shift, h->kz_S,
+                                h->kz_rn2, st);
         launch_kaczmarz_sweeps(F.g, F.fixed, h->kz_S, h->kz_rn2, F.b, q, F.g.n, sweeps, st);
       }
       if (ritz) {
@@ -379,7 +384,8 @@ __global__ void k_adjoint_gather(Grid g, const uint8_t* __restrict__ fixed, cons
 template <int DIM>
 __global__ void k_sensitivities(Grid g, int q, const double* __restrict__ u, const double* __restrict__ modes,
                                 const double* __restrict__ adj, const double* __restrict__ Gs0,
-                                const double* __restrict__ Ke0, const double* __restrict__ dEk,
+                                const double* __restrict__ Gc0, const double* __restrict__ Ke0,
+                                const double* __restrict__ dEk,
                                 const double* __restrict__ dEs, const double* __restrict__ lam,
                                 const double* __restrict__ pGp_glob, double* __restrict__ dlam,
                                 double* __restrict__ dJ) {
@@ -428,13 +434,22 @@ __global__ void k_sensitivities(Grid g, int q, const double* __restrict__ u, con
       pKp += pe[a] * s;
     }
     double pGp = 0.0;
-    for (int a = 0; a < NN; ++a)
-      for (int b = 0; b < NN; ++b) {
+    if (Gc0) {  // condensed stress stiffness of the incompatible-mode element (dense, unit modulus)
+      const double* Gc = Gc0 + e * ND * ND;
+      for (int a = 0; a < ND; ++a) {
         double s = 0.0;
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) s += pe[a * DIM + c] * pe[b * DIM + c];
-        pGp += G0[a * NN + b] * s;
+        for (int b = 0; b < ND; ++b) s += Gc[a * ND + b] * pe[b];
+        pGp += pe[a] * s;
       }
+    } else {
+      for (int a = 0; a < NN; ++a)
+        for (int b = 0; b < NN; ++b) {
+          double s = 0.0;
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) s += pe[a * DIM + c] * pe[b * DIM + c];
+          pGp += G0[a * NN + b] * s;
+        }
+    }
     double zKu = 0.0;
 #pragma unroll
     for (int a = 0; a < ND; ++a) zKu += adj[(int64_t)i * n + dof[a]] * Ku[a];
@@ -458,7 +473,9 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
   for (int i = 0; i < q; ++i) {
     const double* phi = h->modes + (size_t)i * n;
     double* b = h->adj_rhs + (size_t)i * n;
-    if (g.dim == 2) {
+    if (h->Gc0) {
+      launch_inc_adjoint(g, h->lv[0].fixed, phi, h->Es, h->d_A, h->d_dN, h->d_D, h->tab.wdet, h->esens, b, st);
+    } else if (g.dim == 2) {
       ::tobk::note_launch(), k_adjoint_gp<2><<<nblk(g.m, 128), 128, 0, st>>>(g, phi, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->esens);
       ::tobk::note_launch(), k_adjoint_gather<2><<<nblk(g.nnode), 256, 0, st>>>(g, h->lv[0].fixed, h->esens, h->d_dN, b);
     } else {
@@ -486,10 +503,10 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
   double* pGp = h->dscal + 960;
   launch_coldots(h->modes, GP, q, n, n, pGp, h->gram_partial, st);
   if (g.dim == 2)
-    ::tobk::note_launch(), k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk,
+    ::tobk::note_launch(), k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->Gc0, h->d_Ke0, h->dEk,
                                                        h->dEs, h->lam, pGp, h->dlam, h->dJ);
   else
-    ::tobk::note_launch(), k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->d_Ke0, h->dEk, h->dEs,
+    ::tobk::note_launch(), k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->Gc0, h->d_Ke0, h->dEk, h->dEs,
                                                      h->lam, pGp, h->dlam, h->dJ);
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (dlam_out) cudaMemcpyAsync(dlam_out, h->dlam, sizeof(double) * q * g.m, kind, st);

@@ -120,7 +120,12 @@ void launch_noalloc(const tobk_desc& d, const double* x, const uint8_t* fixed, c
   op.penal = d.penal;
   op.E0 = d.E0;
   op.Emin = d.Emin;
-  unit_element::stiffness(DIM, d.nu, op.M);
+  if (d.element == TOBK_ELEMENT_INCOMPATIBLE) {
+    double A[unit_element::kMaxInternal * unit_element::kMaxDofs];
+    unit_element::incompatible_tables(DIM, d.nu, op.M, A);
+  } else {
+    unit_element::stiffness(DIM, d.nu, op.M);
+  }
   const int64_t want = (op.g.nnode + 255) / 256;
   const unsigned blocks = (unsigned)(want < kNoAllocBlocks ? want : kNoAllocBlocks);
   note_launch();
@@ -141,6 +146,7 @@ extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, con
   // infinite, a non-positive modulus or p < 1 leaves K(x) without meaning
   if (!(desc->nu > -1.0 && desc->nu < 0.5) || !(desc->E0 > 0.0) || !(desc->Emin > 0.0) || !(desc->penal >= 1.0))
     return TOBK_E_ARG;
+  if (desc->element != TOBK_ELEMENT_PLAIN && desc->element != TOBK_ELEMENT_INCOMPATIBLE) return TOBK_E_ARG;
   // the built-in scratch holds kNoAllocMaxRhs right-hand sides; larger blocks are rejected
   if (nrhs < 1 || nrhs > kNoAllocMaxRhs) return TOBK_E_ARG;
   int dev = 0;

@@ -22,21 +22,33 @@ struct Q4Consts {
   T hu, hv;              // (D11 + D33)/12, (D22 + D33)/12
 };
 
-// Recovers the constitutive entries from the unit element matrix K_e0 (row-major 8 x 8) through
-// three of its entries: K[0][0] = D11/3 + D33/3, K[0][2] = -D11/3 + D33/6, K[0][1] = D12/4 + D33/4.
+// Recovers the constants from the unit element matrix K_e0 (row-major 8 x 8).  The hourglass
+// coefficients from the hourglass vectors g = (+1, -1, +1, -1) on the x (resp. y) DOFs:
+// g^T K g = 16 hu.  The mean-gradient part from entries with the hourglass part removed:
+// K[0][0] - hu = (D11 + D33)/4, K[0][2] + hu = (D33 - D11)/4, K[0][1] = (D12 + D33)/4.  For the plain
+// Q4 element hu = hv = (D11 + D33)/12; Wilson's incompatible-mode element (Sec. 2) condenses to the
+// same matrix with hu = hv = (D11 - D12^2/D22)/12, the bending modulus, so both come out of K_e0.
 template <typename T>
 inline Q4Consts<T> q4_consts(const double* Ke0) {
-  const double k00 = Ke0[0], k02 = Ke0[2], k01 = Ke0[1];
-  const double d33 = 2.0 * (k00 + k02);  // (k00 + k02) = D33/2
-  const double d11 = 3.0 * k00 - d33;
-  const double d12 = 4.0 * k01 - d33;
+  const double g[4] = {1.0, -1.0, 1.0, -1.0};
+  double gKg = 0.0, hKh = 0.0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      gKg += g[a] * Ke0[(2 * a) * 8 + 2 * b] * g[b];
+      hKh += g[a] * Ke0[(2 * a + 1) * 8 + 2 * b + 1] * g[b];
+    }
+  const double hu = gKg / 16.0, hv = hKh / 16.0;
+  const double mean_xx = Ke0[0] - hu, mean_x01 = Ke0[2] + hu;
+  const double d11 = 2.0 * (mean_xx - mean_x01);
+  const double d33 = 2.0 * (mean_xx + mean_x01);
+  const double d12 = 4.0 * Ke0[1] - d33;
   Q4Consts<T> c;
   c.d11 = (T)d11;
   c.d22 = (T)d11;
   c.d12 = (T)d12;
   c.d33 = (T)d33;
-  c.hu = (T)((d11 + d33) / 12.0);
-  c.hv = (T)((d11 + d33) / 12.0);
+  c.hu = (T)hu;
+  c.hv = (T)hv;
   return c;
 }
 

@@ -30,10 +30,11 @@ struct ActiveRhsScope {
 // ================================================================================================
 // element tables (Gauss-Legendre 2-point rule per axis; exact for Q4/H8 on unit elements)
 // ================================================================================================
-ElementTables make_element_tables(int dim, double nu) {
+ElementTables make_element_tables(int dim, double nu, int element) {
   namespace ue = unit_element;
   ElementTables t;
   t.dim = dim;
+  t.element = element;
   t.nn = ue::nodes(dim);
   t.nd = ue::dofs(dim);
   t.ngp = t.nn;
@@ -46,7 +47,12 @@ ElementTables make_element_tables(int dim, double nu) {
   t.D.assign((size_t)nv * nv, 0.0);
   ue::constitutive(dim, nu, t.D.data());
   t.Ke0.assign((size_t)nd * nd, 0.0);
-  ue::stiffness(dim, nu, t.Ke0.data());
+  if (element == TOBK_ELEMENT_INCOMPATIBLE) {
+    t.A.assign((size_t)ue::internal_dofs(dim) * nd, 0.0);
+    ue::incompatible_tables(dim, nu, t.Ke0.data(), t.A.data());
+  } else {
+    ue::stiffness(dim, nu, t.Ke0.data());
+  }
   // interpolation weights child node -> coarse element node, per child position
   t.W.assign((size_t)nn * nn * nn, 0.0);
   for (int kc = 0; kc < nn; ++kc)
@@ -139,6 +145,12 @@ static void layout(tobk_handle* h, Arena& a) {
   if (!h->solve_only) {
     h->Gs0 = a.take<double>(g.m * nn * nn);
     h->Gs = a.take<double>(g.m * nn * nn);
+    if (h->tab.element == TOBK_ELEMENT_INCOMPATIBLE) {
+      const int nf = nn + h->dim;
+      h->d_A = a.take<double>(h->tab.A.size());
+      h->Gfull = a.take<double>(g.m * nf * nf);
+      h->Gc0 = a.take<double>(g.m * nd * nd);
+    }
   }
   const int64_t nc = h->lv[h->L - 1].g.n;
   h->Adense = a.take<double>(nc * nc);
@@ -214,6 +226,8 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   if (d->kaczmarz_sweeps < 0 || d->kaczmarz_sweeps > 64 || (d->ritz_levels != 0 && d->ritz_levels != 1) ||
       d->fine_steps < 0 || d->fine_steps > 64)
     return TOBK_E_ARG;
+  if (d->element != TOBK_ELEMENT_PLAIN && d->element != TOBK_ELEMENT_INCOMPATIBLE) return TOBK_E_ARG;
+  if (d->element != TOBK_ELEMENT_PLAIN && solve_only) return TOBK_E_ARG;  // batches: plain elements only
   for (int a = 0; a < d->dim; ++a) {
     if (d->nel[a] < 1) return TOBK_E_ARG;
     if (d->nel[a] % (1 << (d->mg_levels - 1)) != 0) return TOBK_E_ARG;
@@ -234,7 +248,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
     delete h;
     return TOBK_E_ARG;
   }
-  h->tab = make_element_tables(d->dim, d->nu);
+  h->tab = make_element_tables(d->dim, d->nu, d->element);
   int nel[3] = {d->nel[0], d->nel[1], d->dim == 3 ? d->nel[2] : 1};
   for (int j = 0; j < h->L; ++j) {
     h->lv[j].g = make_grid(d->dim, nel);
@@ -272,6 +286,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   cudaMemcpyAsync(h->d_W, h->tab.W.data(), sizeof(double) * h->tab.W.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->d_dN, h->tab.dN.data(), sizeof(double) * h->tab.dN.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->d_D, h->tab.D.data(), sizeof(double) * h->tab.D.size(), cudaMemcpyHostToDevice, s);
+  if (h->d_A) cudaMemcpyAsync(h->d_A, h->tab.A.data(), sizeof(double) * h->tab.A.size(), cudaMemcpyHostToDevice, s);
   cudaStreamSynchronize(s);
   if (check_cuda(h, "tobk_create") != TOBK_OK) {
     destroy_handle(h);
@@ -369,6 +384,7 @@ LevelOpDesc level_op(tobk_handle* h, int j) {
   d.g = h->lv[j].g;
   d.fixed = h->lv[j].fixed;
   d.nu = h->desc.nu;
+  d.element = h->tab.element;
   if (j == 0) {
     d.stored = false;
     d.scale64 = h->Ek;
@@ -733,7 +749,9 @@ void apply_K_level(tobk_handle* h, int j, const double* v, double* y, int nr, in
 }
 
 void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, int64_t stride) {
-  if (j == 0) {
+  if (j == 0 && h->Gc0) {
+    launch_inc_apply_g(h->lv[0].g, h->lv[0].fixed, h->Gc0, h->Es, v, y, nr, stride, h->stream);
+  } else if (j == 0) {
     launch_apply_kron(h->lv[0].g, h->lv[0].fixed, h->Gs, v, y, nr, stride, h->stream);
   } else {
     LevelOpDesc d{};
@@ -751,11 +769,16 @@ void apply_G_level(tobk_handle* h, int j, const double* v, double* y, int nr, in
 int setup_stress(tobk_handle* h) {
   cudaStream_t s = h->stream;
   const Grid& g = h->lv[0].g;
-  launch_stress_gs_dev(g, h->u, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->Gs0, h->Gs, s);
+  if (h->Gc0)
+    launch_inc_stress(g, h->u, h->d_A, h->d_dN, h->d_D, h->tab.wdet, h->Gfull, h->Gc0, s);
+  else
+    launch_stress_gs_dev(g, h->u, h->Es, h->d_dN, h->d_D, h->tab.wdet, h->Gs0, h->Gs, s);
   for (int j = 1; j <= h->eig; ++j) {
     Level& Lc = h->lv[j];
     const Level& Lf = h->lv[j - 1];
-    if (j == 1)
+    if (j == 1 && h->Gc0)
+      launch_galerkin_scaled_stored(Lf.g, Lc.g, Lf.fixed, h->Gc0, h->Es, h->d_W, Lc.Ge, s);
+    else if (j == 1)
       launch_galerkin_fine_G(Lf.g, Lc.g, Lf.fixed, h->Gs, h->d_W, Lc.Ge, s);
     else
       launch_galerkin_stored(Lf.g, Lc.g, Lf.fixed, Lf.Ge, h->d_W, Lc.Ge, s);

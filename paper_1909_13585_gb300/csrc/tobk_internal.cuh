@@ -71,13 +71,15 @@ inline Grid make_grid(int dim, const int nel[3]) {
 // ------------------------------------------------------------------------------------------------
 struct ElementTables {
   int dim, nn, nd, ngp, nv;
-  std::vector<double> Ke0;  // [nd*nd] unit-modulus stiffness
+  int element = 0;          // tobk_element
+  std::vector<double> Ke0;  // [nd*nd] unit-modulus stiffness (condensed for incompatible modes)
+  std::vector<double> A;    // [d*d][nd] condensation map of the incompatible modes (empty otherwise)
   std::vector<double> dN;   // [ngp][dim][nn] shape-function gradients in physical coordinates
   std::vector<double> D;    // [nv*nv] unit-modulus constitutive matrix
   double wdet;              // Gauss weight x |J| (same at every Gauss point)
   std::vector<double> W;    // [2^dim children][nn child nodes][nn coarse nodes] interpolation weights
 };
-ElementTables make_element_tables(int dim, double nu);
+ElementTables make_element_tables(int dim, double nu, int element = 0);
 
 // ------------------------------------------------------------------------------------------------
 // device memory arena (one cudaMalloc per handle)

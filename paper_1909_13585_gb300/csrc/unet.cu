@@ -793,7 +793,7 @@ void sample_grad(tobk_unet* u, const float* x, const double* f, const float* tar
   const int energy = u->desc.loss == TOBK_UNET_LOSS_ENERGY;
   if (energy) {  // K t with the library's factored H8 operator (FP32, moduli E_kappa of the features)
     const int nel[3] = {d0.W, d0.H, d0.D};
-    launch_fine_h8<float>(make_grid(3, nel), u->Ek, fixed, u->desc.nu, APPLY_KV, u->tn, nullptr, nullptr, u->Kt,
+    launch_fine_h8<float>(make_grid(3, nel), u->Ek, fixed, u->desc.nu, 0, APPLY_KV, u->tn, nullptr, nullptr, u->Kt,
                           SmoothArgs<float>{}, 1, n, u->stream);
   }
   const unsigned blocks = nb(n);

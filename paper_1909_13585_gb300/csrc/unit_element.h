@@ -115,5 +115,106 @@ inline void stiffness(int dim, double nu, double* Ke) {
   }
 }
 
+// ---- incompatible-mode elements (Sec. 2: Wilson's quadrilateral, the hexahedron with 11
+// interpolation functions per component) --------------------------------------------------------
+// Each component is interpolated by the 2^d nodal functions plus d internal modes P_k = 1 - xi_k^2
+// (natural coordinates xi in [-1, 1]^d), whose amplitudes alpha (d per component, ordered
+// [mode][component] after the nodal DOFs) are condensed out element by element:
+//   alpha = A u_e,  A = -K_aa^{-1} K_au,  K_c = K_uu + K_ua A.
+// A does not depend on the modulus, so one table serves every element of a unit-square / unit-cube
+// grid.
+
+constexpr int kMaxInternal = 9;  // d * d internal DOFs
+constexpr int kMaxFunctions = 11;  // 2^d + d interpolation functions per component
+
+inline int functions(int dim) { return nodes(dim) + dim; }
+inline int internal_dofs(int dim) { return dim * dim; }
+
+// dF [dim][nf]: gradients of the 2^d nodal functions then of the d internal modes at Gauss point q
+inline void full_gradients(int dim, int q, double* dF) {
+  const int nn = nodes(dim), nf = functions(dim);
+  double dN[3 * kMaxNodes];
+  shape_gradients(dim, q, dN);
+  const double g = 1.0 / std::sqrt(3.0);
+  for (int a = 0; a < dim; ++a) {
+    for (int l = 0; l < nn; ++l) dF[a * nf + l] = dN[a * nn + l];
+    for (int k = 0; k < dim; ++k) {
+      const double xk = ((q >> k) & 1) ? g : -g;
+      dF[a * nf + nn + k] = a == k ? 2.0 * (-2.0 * xk) : 0.0;  // d/dx = 2 d/dxi
+    }
+  }
+}
+
+// Kc [nd][nd] (condensed unit-modulus stiffness) and A [dd][nd] (condensation map)
+inline void incompatible_tables(int dim, double nu, double* Kc, double* A) {
+  const int nd = dofs(dim), dd = internal_dofs(dim), nf = functions(dim), nt = nd + dd, nv = voigt(dim);
+  constexpr int kT = kMaxDofs + kMaxInternal;
+  double D[kMaxVoigt * kMaxVoigt], dF[3 * kMaxFunctions], B[kMaxVoigt * kT], K[kT * kT];
+  constitutive(dim, nu, D);
+  const double wdet = weight_det(dim);
+  for (int q = 0; q < nt * nt; ++q) K[q] = 0.0;
+  for (int q = 0; q < nodes(dim); ++q) {
+    full_gradients(dim, q, dF);
+    for (int r = 0; r < nv * nt; ++r) B[r] = 0.0;
+    for (int f = 0; f < nf; ++f) {  // the strain matrix over all functions, DOF f * dim + c
+      const double dx = dF[0 * nf + f], dy = dF[1 * nf + f];
+      if (dim == 2) {
+        B[0 * nt + 2 * f] = dx;
+        B[1 * nt + 2 * f + 1] = dy;
+        B[2 * nt + 2 * f] = dy;
+        B[2 * nt + 2 * f + 1] = dx;
+      } else {
+        const double dz = dF[2 * nf + f];
+        B[0 * nt + 3 * f] = dx;
+        B[1 * nt + 3 * f + 1] = dy;
+        B[2 * nt + 3 * f + 2] = dz;
+        B[3 * nt + 3 * f] = dy;
+        B[3 * nt + 3 * f + 1] = dx;
+        B[4 * nt + 3 * f + 1] = dz;
+        B[4 * nt + 3 * f + 2] = dy;
+        B[5 * nt + 3 * f] = dz;
+        B[5 * nt + 3 * f + 2] = dx;
+      }
+    }
+    for (int r = 0; r < nt; ++r)
+      for (int c = 0; c < nt; ++c) {
+        double s = 0.0;
+        for (int a = 0; a < nv; ++a)
+          for (int b = 0; b < nv; ++b) s += B[a * nt + r] * D[a * nv + b] * B[b * nt + c];
+        K[r * nt + c] += wdet * s;
+      }
+  }
+  // A = -K_aa^{-1} K_au by Gauss-Jordan on [K_aa | -K_au] (K_aa is symmetric positive definite)
+  double M[kMaxInternal * (kMaxInternal + kMaxDofs)];
+  const int w = dd + nd;
+  for (int i = 0; i < dd; ++i) {
+    for (int j = 0; j < dd; ++j) M[i * w + j] = K[(nd + i) * nt + nd + j];
+    for (int j = 0; j < nd; ++j) M[i * w + dd + j] = -K[(nd + i) * nt + j];
+  }
+  for (int p = 0; p < dd; ++p) {
+    const double piv = M[p * w + p];
+    for (int j = 0; j < w; ++j) M[p * w + j] /= piv;
+    for (int i = 0; i < dd; ++i) {
+      if (i == p) continue;
+      const double f = M[i * w + p];
+      for (int j = 0; j < w; ++j) M[i * w + j] -= f * M[p * w + j];
+    }
+  }
+  for (int i = 0; i < dd; ++i)
+    for (int j = 0; j < nd; ++j) A[i * nd + j] = M[i * w + dd + j];
+  // K_c = K_uu + K_ua A, symmetrised
+  for (int r = 0; r < nd; ++r)
+    for (int c = 0; c < nd; ++c) {
+      double s = K[r * nt + c];
+      for (int i = 0; i < dd; ++i) s += K[r * nt + nd + i] * A[i * nd + c];
+      Kc[r * nd + c] = s;
+    }
+  for (int r = 0; r < nd; ++r)
+    for (int c = r + 1; c < nd; ++c) {
+      const double v = 0.5 * (Kc[r * nd + c] + Kc[c * nd + r]);
+      Kc[r * nd + c] = Kc[c * nd + r] = v;
+    }
+}
+
 }  // namespace unit_element
 }  // namespace tobk
