@@ -517,15 +517,120 @@ __global__ void k_gj_step(const double* __restrict__ A, double* __restrict__ B, 
 
 __global__ void k_first_pivot(const double* A, double* rcp) { rcp[0] = 1.0 / A[0]; }
 
-double* launch_dense_invert(double* A, double* work, int64_t n, double* rcp2, cudaStream_t s) {
-  double* src = A;
-  double* dst = work;
-  ::tobk::note_launch(), k_first_pivot<<<1, 1, 0, s>>>(A, rcp2);
-  for (int64_t k = 0; k < n; ++k) {
-    ::tobk::note_launch(), k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k, rcp2);
-    std::swap(src, dst);
+// Blocked in-place Gauss-Jordan (the same elimination as k_gj_step, kGJB pivots at a time): for the
+// pivot block K = [k0, k0 + bs),
+//   P = A_KK^{-1};  R_K = P A_K,j (j outside K);  A_ij -= A_iK R_Kj (i, j outside K);
+//   A_iK <- -A_iK P (i outside K);  A_KK <- P;  A_Kj <- R_Kj.
+// After the last block A holds its inverse.  Five launches per block instead of one per pivot.
+constexpr int kGJB = 32;
+
+__global__ void __launch_bounds__(kGJB * kGJB) k_bgj_diag(const double* __restrict__ A, int64_t n, int64_t k0, int bs,
+                                                          double* __restrict__ P) {
+  __shared__ double M[kGJB][kGJB + 1];
+  const int i = threadIdx.y, j = threadIdx.x;
+  if (i < bs && j < bs) M[i][j] = A[(k0 + i) * n + k0 + j];
+  __syncthreads();
+  for (int p = 0; p < bs; ++p) {
+    double v = 0.0;
+    if (i < bs && j < bs) {
+      const double r = 1.0 / M[p][p];
+      if (i == p && j == p)
+        v = r;
+      else if (i == p)
+        v = M[p][j] * r;
+      else if (j == p)
+        v = -M[i][p] * r;
+      else
+        v = M[i][j] - M[i][p] * (M[p][j] * r);
+    }
+    __syncthreads();
+    if (i < bs && j < bs) M[i][j] = v;
+    __syncthreads();
   }
-  return src;
+  if (i < bs && j < bs) P[i * kGJB + j] = M[i][j];
+}
+
+// R[r][j] = sum_q P[r][q] A[k0 + q][j] for columns j outside the block (R [bs][n])
+__global__ void k_bgj_row(const double* __restrict__ A, int64_t n, int64_t k0, int bs, const double* __restrict__ P,
+                          double* __restrict__ R) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= n || (j >= k0 && j < k0 + bs)) return;
+  double s = 0.0;
+  for (int q = 0; q < bs; ++q) s += P[r * kGJB + q] * A[(k0 + q) * n + j];
+  R[(int64_t)r * n + j] = s;
+}
+
+// A_ij -= sum_q A[i][k0 + q] R[q][j] for i, j outside the block; 32 x 32 tiles, 4 rows per thread
+__global__ void __launch_bounds__(256) k_bgj_update(double* __restrict__ A, int64_t n, int64_t k0, int bs,
+                                                    const double* __restrict__ R) {
+  __shared__ double Ai[32][kGJB + 1];
+  __shared__ double Rk[kGJB][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t i = i0 + rr;
+    Ai[rr][tx] = (i < n && tx < bs) ? A[i * n + k0 + tx] : 0.0;
+  }
+  for (int q = ty; q < kGJB; q += 8) {
+    const int64_t j = j0 + tx;
+    Rk[q][tx] = (q < bs && j < n) ? R[(int64_t)q * n + j] : 0.0;
+  }
+  __syncthreads();
+  const int64_t j = j0 + tx;
+  if (j >= n || (j >= k0 && j < k0 + bs)) return;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t i = i0 + rr;
+    if (i >= n || (i >= k0 && i < k0 + bs)) continue;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < kGJB; ++q) acc += Ai[rr][q] * Rk[q][tx];
+    A[i * n + j] -= acc;
+  }
+}
+
+// A_iK <- -A_iK P for i outside the block (one warp per row), then A_KK <- P and A_Kj <- R_Kj
+__global__ void k_bgj_col(double* __restrict__ A, int64_t n, int64_t k0, int bs, const double* __restrict__ P) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int c = threadIdx.x & 31;
+  if (i >= n || (i >= k0 && i < k0 + bs)) return;
+  const double old = c < bs ? A[i * n + k0 + c] : 0.0;
+  double s = 0.0;
+  for (int q = 0; q < bs; ++q) s += __shfl_sync(0xffffffffu, old, q) * (c < bs ? P[q * kGJB + c] : 0.0);
+  if (c < bs) A[i * n + k0 + c] = -s;
+}
+__global__ void k_bgj_rows_back(double* __restrict__ A, int64_t n, int64_t k0, int bs, const double* __restrict__ P,
+                                const double* __restrict__ R) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= n) return;
+  A[(k0 + r) * n + j] = (j >= k0 && j < k0 + bs) ? P[r * kGJB + (j - k0)] : R[(int64_t)r * n + j];
+}
+
+double* launch_dense_invert(double* A, double* work, int64_t n, double* rcp2, cudaStream_t s) {
+  if (n <= 2 * kGJB) {  // small matrices: one launch per pivot
+    double* src = A;
+    double* dst = work;
+    ::tobk::note_launch(), k_first_pivot<<<1, 1, 0, s>>>(A, rcp2);
+    for (int64_t k = 0; k < n; ++k) {
+      ::tobk::note_launch(), k_gj_step<<<blocks_for(n * n), kThreads, 0, s>>>(src, dst, n, k, rcp2);
+      std::swap(src, dst);
+    }
+    return src;
+  }
+  // work (n x n, n > 2 kGJB) holds R [kGJB][n] and P [kGJB][kGJB]
+  double* R = work;
+  double* P = work + (size_t)kGJB * n;
+  const unsigned tiles = (unsigned)((n + 31) / 32);
+  for (int64_t k0 = 0; k0 < n; k0 += kGJB) {
+    const int bs = (int)std::min<int64_t>(kGJB, n - k0);
+    ::tobk::note_launch(), k_bgj_diag<<<1, dim3(kGJB, kGJB), 0, s>>>(A, n, k0, bs, P);
+    ::tobk::note_launch(), k_bgj_row<<<dim3(blocks_for(n, 128), bs), 128, 0, s>>>(A, n, k0, bs, P, R);
+    ::tobk::note_launch(), k_bgj_update<<<dim3(tiles, tiles), dim3(32, 8), 0, s>>>(A, n, k0, bs, R);
+    ::tobk::note_launch(), k_bgj_col<<<blocks_for(n * 32, 256), 256, 0, s>>>(A, n, k0, bs, P);
+    ::tobk::note_launch(), k_bgj_rows_back<<<dim3(blocks_for(n, 128), bs), 128, 0, s>>>(A, n, k0, bs, P, R);
+  }
+  return A;
 }
 
 // ================================================================================================
