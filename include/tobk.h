@@ -114,6 +114,9 @@ typedef struct {
                         rtol), each followed by the Rayleigh quotients; 1 (or 0) = the single fine solve
                         of Sec. 2.1 step 3 */
   int element;       /* tobk_element: the element of the fine grid */
+  int eig_gram_tc;   /* 1: the eigensolver's Gram products V^T W run on the tensor cores with FP64
+                        accuracy (error-free splitting, see tobk_gram_tc); 0 (default): FP64 CUDA-core
+                        products, faster for the eigen levels of the configured workloads */
 } tobk_desc;
 
 /* Elements (Sec. 2).  TOBK_ELEMENT_INCOMPATIBLE: Wilson's quadrilateral (2D) and the hexahedron with
@@ -140,7 +143,7 @@ typedef struct tobk_handle tobk_handle;
 /* Fills *desc with defaults: nu 0.3, E0 1, Emin 1e-6, p 3, 3 levels, eig_level 1, 6 modes, FP64,
  * rtol 1e-8, max_iter 500, omega 0.6, nu_pre = nu_post = 2, eig_tol 1e-8, eig_max_iter 200,
  * max_rhs = num_modes + 4, no Kaczmarz sweeps, no per-level Ritz projection, one fine solve, plain
- * Q4 / H8 elements.
+ * Q4 / H8 elements, FP64 CUDA-core Gram products in the eigensolver.
  * Returns TOBK_OK. */
 int tobk_default_desc(tobk_desc* desc);
 
@@ -248,6 +251,18 @@ int tobk_solve(tobk_handle* h, int level, const double* B, double* X, int nrhs, 
 /* Copies the stored Galerkin element matrices of a coarse level (which: 0 = K, 1 = G) to out
  * [m_level][nd*nd] (device pointer), nd = dim * 2^dim. */
 int tobk_get_element_matrices(tobk_handle* h, int level, int which, double* out, int64_t len);
+
+/* C [na][nb] = A B^T for na, nb <= 64 FP64 vectors of length n (rows of A and B stride doubles
+ * apart; device pointers): the Gram product of the eigensolver (eq. eigenvalueProblemCoarseScale,
+ * solved to a residual of 1e-8, Appendix A) on the tensor cores.  Every vector is scaled by a power of
+ * two and cut into eight 7-bit digit planes held exactly in bfloat16; the plane products are summed
+ * exactly (FP32 tensor-core accumulators over chunks of 64 entries, then int64) and combined in FP64,
+ * so the result is within about n 2^-53 max|A_i| max|B_j| of the exact product (error-free
+ * splitting, Ozaki et al. 2012).  For unit tests; synchronised on cuda_stream before return.
+ * TOBK_E_ARG for bad sizes, TOBK_E_NONFINITE for a NaN / infinity in the input, TOBK_E_TIMEOUT if a
+ * bounded device wait gave up. */
+int tobk_gram_tc(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
+                 void* cuda_stream);
 
 /* ---- many designs solved together ------------------------------------------------------------
  * A batch holds nd independent 2D designs (each its own grid, densities, Dirichlet set and multigrid

@@ -28,7 +28,7 @@ class tobk_desc(C.Structure):
                 ("eig_max_iter", C.c_int), ("max_rhs", C.c_int), ("eig_inner_iters", C.c_int),
                 ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double),
                 ("kaczmarz_sweeps", C.c_int), ("ritz_levels", C.c_int), ("fine_steps", C.c_int),
-                ("element", C.c_int)]
+                ("element", C.c_int), ("eig_gram_tc", C.c_int)]
 
 
 class tobk_solve_info(C.Structure):
@@ -60,6 +60,7 @@ _SIGS = {
     "tobk_solve": (C.c_int, [_H, C.c_int, _P, _P, C.c_int, C.POINTER(tobk_solve_info)]),
     "tobk_get_element_matrices": (C.c_int, [_H, C.c_int, C.c_int, _P, C.c_int64]),
     "tobk_residual_noalloc": (C.c_int, [C.POINTER(tobk_desc), _P, _P, _P, _P, C.c_int, _P, C.c_void_p]),
+    "tobk_gram_tc": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int64, C.c_int64, _P, C.c_void_p]),
     "tobk_batch_create": (C.c_int, [C.POINTER(tobk_desc), C.c_int, C.c_int, C.c_void_p, C.POINTER(_H)]),
     "tobk_batch_destroy": (None, [_H]),
     "tobk_batch_last_error": (C.c_char_p, [_H]),

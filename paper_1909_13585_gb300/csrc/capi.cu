@@ -49,6 +49,8 @@ int tobk_default_desc(tobk_desc* d) {
   d->kaczmarz_sweeps = 0;
   d->ritz_levels = 0;
   d->fine_steps = 1;
+  d->element = TOBK_ELEMENT_PLAIN;
+  d->eig_gram_tc = 0;
   return TOBK_OK;
 }
 
@@ -256,3 +258,26 @@ int tobk_get_element_matrices(tobk_handle* h, int level, int which, double* out,
 }
 
 }  // extern "C"
+
+extern "C" int tobk_gram_tc(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
+                            void* cuda_stream) {
+  using namespace tobk;
+  if (!A || !B || !C || na < 1 || na > 64 || nb < 1 || nb > 64 || n < 1 || stride < n) return TOBK_E_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const size_t doubles = (size_t)gram_tc_chunks(n) * na * nb + 1;  // partials, then the two flags
+  double* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, sizeof(double) * doubles, s) != cudaSuccess) {
+    cudaGetLastError();
+    return TOBK_E_NOMEM;
+  }
+  unsigned* err = reinterpret_cast<unsigned*>(buf + doubles - 1);
+  cudaMemsetAsync(err, 0, 2 * sizeof(unsigned), s);
+  launch_gram_tc(A, na, B, nb, n, stride, C, buf, err, s);
+  unsigned herr[2] = {0, 0};
+  cudaMemcpyAsync(herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return TOBK_E_CUDA;
+  if (herr[0]) return TOBK_E_TIMEOUT;
+  if (herr[1]) return TOBK_E_NONFINITE;
+  return TOBK_OK;
+}

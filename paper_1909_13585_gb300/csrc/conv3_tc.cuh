@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "tcgen05_common.cuh"
+
 namespace tobk {
 namespace tc {
 
@@ -28,24 +30,6 @@ struct Dim3 {
   int D, H, W;
   __host__ __device__ int64_t vox() const { return (int64_t)D * H * W; }
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance between the 8-element
-// column blocks along K, sbo = byte distance between 8-row groups along M / N
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version
-  return d;                // base offset 0, layout type 0 (no swizzle)
-}
-
-// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N
-__host__ __device__ constexpr uint32_t idesc_bf16(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -66,23 +50,6 @@ struct ConvTcArgs {
   int relu;
   unsigned* err;              // set to 1 when a wait gave up
 };
-
-constexpr long long kSpinLimit = 1ll << 22;
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
 
 template <int N>
 __global__ void __launch_bounds__(128) k_conv3_tc(ConvTcArgs a) {

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "handle.h"
@@ -159,6 +160,27 @@ __global__ void k_gather_residual(const double* GX, const double* KX, const doub
   W[(int64_t)c * stride + k] = -GX[(int64_t)s * stride + k] - theta[s] * KX[(int64_t)s * stride + k];
 }
 
+// Gram product of the eigensolver: tensor cores (FP64-accurate splitting, gram_tc.cu) for vectors of
+// the eigen level, FP64 CUDA cores otherwise.
+static void eig_gram(tobk_handle* h, const double* A, int na, const double* B, int nb, int64_t n, int64_t stride,
+                     double* C) {
+  if (h->gtc_err && na <= 64 && nb <= 64 && n <= h->gtc_nmax)
+    launch_gram_tc(A, na, B, nb, n, stride, C, h->gram_partial, h->gtc_err, h->stream);
+  else
+    launch_gram(A, na, B, nb, n, stride, C, h->gram_partial, h->stream);
+}
+
+// TOBK_OK, or the status of a failed tensor-core Gram product (flags copied to the host at byte offset
+// 8000 of hscal by the last synchronised step)
+static int gram_tc_status(tobk_handle* h) {
+  if (!h->gtc_err) return TOBK_OK;
+  unsigned f[2];
+  std::memcpy(f, reinterpret_cast<const char*>(h->hscal) + 8000, sizeof(f));
+  if (f[0]) return fail(h, TOBK_E_TIMEOUT, "tensor-core Gram product: a bounded wait gave up");
+  if (f[1]) return fail(h, TOBK_E_NONFINITE, "non-finite value in the eigensolver basis");
+  return TOBK_OK;
+}
+
 // ------------------------------------------------------------------------------------------------
 // driver
 // ------------------------------------------------------------------------------------------------
@@ -212,6 +234,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   double* rrDelta = rrLam + mmax;
   int rr_prev = 0;  // size of the previous projected problem whose eigenvectors are in rrX1 (0: none)
   cudaMemsetAsync(sinfo, 0, sizeof(double), st);  // Cholesky breakdown flag (sticky)
+  if (h->gtc_err) cudaMemsetAsync(h->gtc_err, 0, 2 * sizeof(unsigned), st);
   const bool trace = std::getenv("TOBK_EIG_TRACE") != nullptr;
   int rc = TOBK_OK;
   PhaseMarks pm(h);
@@ -220,7 +243,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     // ---- K-orthogonalise the new block against the basis (classical Gram-Schmidt, twice)
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
     for (int pass = 0; pass < 2 && m > 0; ++pass) {
-      launch_gram(h->KV, m, W, nadd, n, sd, Cs, h->gram_partial, st);
+      eig_gram(h, h->KV, m, W, nadd, n, sd, Cs);
       launch_combine(h->V, m, Cs, nadd, nadd, -1.0, 1.0, W, n, sd, st);
     }
     prof_end(h);
@@ -228,7 +251,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     for (int pass = 0; pass < 2; ++pass) {
       apply_K_level(h, j, W, KW, nadd, sd);
       prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
-      launch_gram(W, nadd, KW, nadd, n, sd, M, h->gram_partial, st);
+      eig_gram(h, W, nadd, KW, nadd, n, sd, M);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)nadd);
       ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, nadd, Rinv, sinfo);
@@ -246,7 +269,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     cudaMemcpyAsync(h->GV + (size_t)m * n, GW, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
     const int mn = m + nadd;
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)mn * n);
-    launch_gram(h->V, mn, GW, nadd, n, sd, Cs, h->gram_partial, st);
+    eig_gram(h, h->V, mn, GW, nadd, n, sd, Cs);
     ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, -1.0, h->Hs, mmax);
     prof_end(h);
     m = mn;
@@ -282,8 +305,13 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     launch_coldots(KX, KX, q, n, sd, kxn, h->gram_partial, st);
     prof_end(h);
     cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double) * 512, cudaMemcpyDeviceToHost, st);
+    if (h->gtc_err)
+      cudaMemcpyAsync(reinterpret_cast<char*>(h->hscal) + 8000, h->gtc_err, 2 * sizeof(unsigned),
+                      cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     rc = check_cuda(h, "eigen_solve");
+    if (rc) break;
+    rc = gram_tc_status(h);
     if (rc) break;
     if (h->hscal[384] != 0.0) {  // the K-orthonormalised expansion lost rank
       rc = fail(h, TOBK_E_BREAKDOWN,
@@ -343,7 +371,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
         launch_combine(bsp, m, h->Ys, mmax, keep, 1.0, 0.0, tmp, n, sd, st);
         cudaMemcpyAsync(bsp, tmp, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st);
       }
-      launch_gram(h->V, keep, h->GV, keep, n, sd, Cs, h->gram_partial, st);
+      eig_gram(h, h->V, keep, h->GV, keep, n, sd, Cs);
       ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)keep * keep), 256, 0, st>>>(Cs, keep, keep, 0, -1.0, h->Hs,
                                                                                        mmax);
       m = keep;
@@ -415,13 +443,13 @@ int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host) {
   cudaMemsetAsync(sinfo, 0, sizeof(double), st);
   for (int pass = 0; pass < 2; ++pass) {
     apply_K_level(h, j, Psi, KW, q, n);
-    launch_gram(Psi, q, KW, q, n, n, M, h->gram_partial, st);
+    eig_gram(h, Psi, q, KW, q, n, n, M);
     ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, q, Rinv, sinfo);
     launch_combine(Psi, q, Rinv, q, q, 1.0, 0.0, Tb, n, n, st);
     cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);
   }
   apply_G_level(h, j, Psi, GW, q, n);
-  launch_gram(Psi, q, GW, q, n, n, Cs, h->gram_partial, st);
+  eig_gram(h, Psi, q, GW, q, n, n, Cs);
   ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)q * q), 256, 0, st>>>(Cs, q, q, 0, -1.0, h->Hs, mmax);
   ::tobk::note_launch(), launch_rr_eig32(h->Hs, q, mmax, nullptr, 0, rrX0, sinfo + 2, st);
   for (int step = 0; step < kRRRefineSteps; ++step) {
@@ -437,8 +465,13 @@ int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host) {
   launch_combine(Psi, q, h->Ys, mmax, q, 1.0, 0.0, Tb, n, n, st);
   cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double) * 512, cudaMemcpyDeviceToHost, st);
+  if (h->gtc_err)
+    cudaMemcpyAsync(reinterpret_cast<char*>(h->hscal) + 8000, h->gtc_err, 2 * sizeof(unsigned),
+                    cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   int rc = check_cuda(h, "ritz_level");
+  if (rc) return rc;
+  rc = gram_tc_status(h);
   if (rc) return rc;
   if (h->hscal[384] != 0.0) return fail(h, TOBK_E_BREAKDOWN, "Ritz projection: the prolongated modes lost rank");
   for (int i = 0; i < q; ++i) {

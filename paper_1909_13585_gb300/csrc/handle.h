@@ -63,6 +63,10 @@ struct tobk_handle {
   // finest level, allocated only when kaczmarz_sweeps > 0)
   double* kz_S = nullptr;
   double* kz_rn2 = nullptr;
+  // tensor-core Gram products of the eigensolver (partials in gram_partial): error flags [2]
+  // (timed-out wait, non-finite input); used for vectors up to gtc_nmax long
+  unsigned* gtc_err = nullptr;
+  int64_t gtc_nmax = 0;
   // small scalars
   double* dscal = nullptr;       // device scratch scalars [256]
   double* hscal = nullptr;       // pinned host scratch [256]

@@ -1238,6 +1238,10 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ p
 
 int gram_partial_blocks(int64_t n) { return (int)((n + kGramChunk - 1) / kGramChunk); }
 
+void launch_gram_final(const double* partial, int nchunks, int nout, double* C, cudaStream_t s) {
+  ::tobk::note_launch(), k_gram_final<<<(nout + 31) / 32, 256, 0, s>>>(partial, nchunks, nout, C);
+}
+
 void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
                  double* partial, cudaStream_t s) {
   const int chunks = gram_partial_blocks(n);

@@ -158,6 +158,14 @@ void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, in
 void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta,
                     double* Y, int64_t n, int64_t stride, cudaStream_t s);
 int gram_partial_blocks(int64_t n);
+// C[o] = sum over chunks of partial[c][o] in a fixed order (the second stage of launch_gram)
+void launch_gram_final(const double* partial, int nchunks, int nout, double* C, cudaStream_t s);
+// The same Gram product on the tensor cores with FP64 accuracy (gram_tc.cu); partial
+// [gram_tc_chunks(n)][na][nb] is FP64 scratch (at most the launch_gram partials), err [2] is set on a
+// timed-out wait / a non-finite input.  na, nb <= 64.
+void launch_gram_tc(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
+                    double* partial, unsigned* err, cudaStream_t s);
+int gram_tc_chunks(int64_t n);
 
 // ---- incompatible-mode elements (incompatible.cu) ---------------------------------------------------
 // Gfull [m][nf*nf] and the condensed unit-modulus stress stiffness Gc0 [m][nd*nd] from u.

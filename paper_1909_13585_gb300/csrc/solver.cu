@@ -203,6 +203,10 @@ static void layout(tobk_handle* h, Arena& a) {
   const int64_t gp_rows = std::max<int64_t>(gram_partial_blocks(ne), gram_partial_blocks(nf));
   h->gram_partial = a.take<double>((size_t)gp_rows * mm * std::max(mm, nb));
   h->dscal = a.take<double>(1024);
+  if (h->desc.eig_gram_tc) {  // partials of at most n / 128 chunks fit in gram_partial
+    h->gtc_nmax = std::max(ne, nf);
+    h->gtc_err = a.take<unsigned>(2);
+  }
   if (h->desc.kaczmarz_sweeps > 0 && h->eig > 0) {
     const int d = h->dim;
     h->kz_S = a.take<double>((size_t)(d == 2 ? 9 : 27) * d * d * g.nnode);
@@ -228,6 +232,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
     return TOBK_E_ARG;
   if (d->element != TOBK_ELEMENT_PLAIN && d->element != TOBK_ELEMENT_INCOMPATIBLE) return TOBK_E_ARG;
   if (d->element != TOBK_ELEMENT_PLAIN && solve_only) return TOBK_E_ARG;  // batches: plain elements only
+  if (d->eig_gram_tc != 0 && d->eig_gram_tc != 1) return TOBK_E_ARG;
   for (int a = 0; a < d->dim; ++a) {
     if (d->nel[a] < 1) return TOBK_E_ARG;
     if (d->nel[a] % (1 << (d->mg_levels - 1)) != 0) return TOBK_E_ARG;
