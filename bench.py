@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision / 3D form measurements")
     ap.add_argument("--profile-run", action="store_true",
                     help="one untimed step only (for an external profiler's launch list)")
+    ap.add_argument("--eig-gram-tc", type=int, default=0, choices=[0, 1],
+                    help="eigensolver Gram products on the tensor cores (FP64-accurate splitting)")
     return ap.parse_args()
 
 
@@ -74,10 +76,13 @@ def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush, 
     dJ_d = torch.zeros(m, dtype=torch.float64, device=dev)
     info = {}
 
+    s.phase_timing(True)
+
     def step():
         s.set_densities(x_d)
         _, i1 = s.solve_equilibrium()
         lam, i2 = s.compute_buckling()
+        info["eigen_ms"] = s.phase_read()["eigen"]
         _, _, i3 = s.compute_sensitivities(dlam_d, dJ_d)
         info.update(la_iters=i1["iterations"], buckling_iters=i2["iterations"], adjoint_iters=i3["iterations"])
         info["_lam"] = lam
@@ -473,7 +478,7 @@ def ours(args):
     p = synthetic.config(args.workload)
     precision = pkg.TOBK_FP64 if args.precision == "fp64" else pkg.TOBK_FP32_VCYCLE
     stream = torch.cuda.Stream(device=dev)
-    s = pkg.Solver(p, stream=stream, precision=precision)
+    s = pkg.Solver(p, stream=stream, precision=precision, eig_gram_tc=args.eig_gram_tc)
     q, m, n = p.num_modes, p.num_elements, p.num_dofs
     units = n * rhs_per_step(p)
 
@@ -584,6 +589,8 @@ def ours(args):
                                                           fs, fw, dev, flush)
         forms["column480x160_fp64_damped_jacobi"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP64, False,
                                                                  fs, fw, dev, flush, smoother=0, omega=0.6)
+        forms["column480x160_fp64_tensor_core_gram"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP64, False,
+                                                                    fs, fw, dev, flush, eig_gram_tc=1)
         forms["column60x20_fp64_exact_lba"] = measure_form(pkg, torch, "column60x20", pkg.TOBK_FP64, False,
                                                            fs, fw, dev, flush)
         o64, o32 = {}, {}

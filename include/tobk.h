@@ -164,7 +164,9 @@ int tobk_set_load(tobk_handle* h, const double* f, int64_t n, int on_device);
 /* Dirichlet mask [n] (uint8, 1 = fixed).  Coarse levels fix a DOF when the fine DOF at the
  * coinciding node is fixed. */
 int tobk_set_fixed(tobk_handle* h, const uint8_t* fixed, int64_t n, int on_device);
-/* Optional initial guess for the next solve_equilibrium (length n; NULL clears it). */
+/* Optional initial guess u0 for the next solve_equilibrium (length n; NULL clears it).  The solve
+ * starts from alpha u0 with alpha = u0^T f / u0^T K u0, the multiple of u0 closest to the solution in
+ * the energy norm (so never farther from it than the zero guess). */
 int tobk_set_initial_guess(tobk_handle* h, const double* u0, int64_t n, int on_device);
 
 /* LA (Algorithm 1 step 2): u = K^{-1} f by mgPCG to desc.rtol; *compliance = f^T u (may be NULL).

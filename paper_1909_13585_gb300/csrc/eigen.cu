@@ -353,7 +353,8 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       // a few mgPCG iterations on K w = r (a better approximation of K^{-1} r than one V-cycle;
       // the iteration limit is the point, so "not converged" is the expected status)
       tobk_solve_info si{};
-      const int src = pcg_solve(h, j, Tb, W, nadd, 1e-300, h->desc.eig_inner_iters, false, h->desc.precision, &si);
+      const int src =
+          pcg_solve(h, j, Tb, W, nadd, 1e-300, h->desc.eig_inner_iters, false, h->desc.precision, &si, true);
       if (src && src != TOBK_E_NOT_CONVERGED) {
         rc = src;
         break;

@@ -116,8 +116,10 @@ int setup_hierarchy(tobk_handle* h);
 void setup_smoothers(tobk_handle* h);
 LevelOpDesc level_op(tobk_handle* h, int j);
 // Multi-RHS MGCG solve at level s (0-based): K_s X = B, nr RHS (device, [nr][n_s]).
+// fixed_iters: exactly max_iter iterations (rounded up to pairs) as an approximate inverse, without
+// host synchronisation or exit check (a preconditioner)
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
-              int precision, tobk_solve_info* info);
+              int precision, tobk_solve_info* info, bool fixed_iters = false);
 int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info);
 int setup_stress(tobk_handle* h);  // Gs from u, Galerkin G down to the eigen level
 int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info);

@@ -25,8 +25,9 @@ namespace tobk {
 
 constexpr int kRRMax = 64;  // largest projected problem (the FP32 stage pads to it)
 // FP32 stage stopping rule: off-diagonal mass below this fraction of the total (off-diagonal entries
-// about 3e-6 of the norm); each of the kRRRefineSteps FP64 refinement steps then squares the error.
-constexpr double kRRJacobiTol2 = 1e-11;
+// about 3e-5 of the norm); each of the kRRRefineSteps FP64 refinement steps then squares the error
+// (3e-5 -> 1e-9 -> 1e-18).
+constexpr double kRRJacobiTol2 = 1e-9;
 constexpr int kRRRefineSteps = 2;
 static_assert(kRRRefineSteps >= 2, "the eigensolver's warm start reads the first refined X");
 

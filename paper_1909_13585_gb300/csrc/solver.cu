@@ -665,7 +665,7 @@ static int run_cg_pair(tobk_handle* h, int s, int nr, int precision) {
 }
 
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
-              int precision, tobk_solve_info* info) {
+              int precision, tobk_solve_info* info, bool fixed_iters) {
   if (nr < 1 || nr > h->rmax) return fail(h, TOBK_E_ARG, "bad RHS count");
   if (!h->setup_done) {
     int rc = setup_hierarchy(h);
@@ -686,6 +686,28 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
   double worst = 0.0;
   int iters = 0;
   bool all_conv = true;
+  if (fixed_iters) {
+    // a fixed number of iterations as an approximate inverse (a preconditioner): no host
+    // synchronisation, no exit check; breakdown shows in the caller's own residuals
+    launch_cg_init(op, B, w.x, w.r, use_x0, rtol, nr, n, w.sc, w.partial, w.counters, st);
+    cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
+    cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+    while (2 * pairs < max_iter) {
+      rc = run_cg_pair(h, s, nr, precision);
+      if (rc) break;
+      ++pairs;
+    }
+    cudaMemcpyAsync(X, w.x, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+      *info = tobk_solve_info{};
+      info->iterations = 2 * pairs;
+      info->num_rhs = nr;
+      info->status_detail = 2 * pairs;
+    }
+    return rc ? rc : check_cuda(h, "pcg_solve");
+  }
   for (int attempt = 0; attempt < 4; ++attempt) {
     launch_cg_init(op, B, w.x, w.r, use_x0 || attempt > 0, rtol, nr, n, w.sc, w.partial, w.counters, st);
     cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
@@ -794,6 +816,15 @@ int setup_stress(tobk_handle* h) {
   return TOBK_OK;
 }
 
+// u <- (d[0] / d[1]) u with d = (u^T f, u^T K u): the multiple of an initial guess closest to the
+// solution in the energy norm (never farther than the zero guess); zero if u^T K u is not positive
+__global__ void k_energy_scale(double* u, int64_t n, const double* d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double den = d[1];
+  u[i] *= (den > 0.0 && isfinite(d[0] / den)) ? d[0] / den : 0.0;
+}
+
 int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info) {
   if (!h->have_x || !h->have_f || !h->have_fixed) return fail(h, TOBK_E_STATE, "densities, load and fixed DOFs must be set");
   if (!h->setup_done) {
@@ -803,7 +834,14 @@ int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info)
   cudaStream_t s = h->stream;
   const int64_t n = h->lv[0].g.n;
   launch_mask_copy(h->f, h->lv[0].fixed, h->bwork, n, 1, n, s);
-  if (h->have_u0) cudaMemcpyAsync(h->u, h->u0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (h->have_u0) {
+    // the caller's guess (e.g. the learned warm start), scaled to minimise its energy-norm error
+    cudaMemcpyAsync(h->u, h->u0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    apply_K_level(h, 0, h->u, h->xwork, 1, n);
+    launch_gram(h->bwork, 1, h->u, 1, n, n, h->dscal + 960, h->gram_partial, s);
+    launch_gram(h->u, 1, h->xwork, 1, n, n, h->dscal + 961, h->gram_partial, s);
+    ::tobk::note_launch(), k_energy_scale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->u, n, h->dscal + 960);
+  }
   int rc = pcg_solve(h, 0, h->bwork, h->u, 1, h->desc.rtol, h->desc.max_iter, h->have_u0, h->desc.precision, info);
   if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
   launch_gram(h->bwork, 1, h->u, 1, n, n, h->dscal, h->gram_partial, s);
