@@ -138,15 +138,58 @@ void launch_coldots(const double* A, const double* B, int ncols, int64_t n, int6
   ::tobk::note_launch(), k_coldots_final<<<(ncols + 63) / 64, 64, 0, s>>>(partial, chunks, ncols, out);
 }
 
-// R_i = KX_i + (1/theta_i) GX_i written to R (i < q)
-__global__ void k_eig_residual_vec(const double* KX, const double* GX, const double* theta, double* R, int64_t n,
-                                   int64_t stride) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int i = blockIdx.y;
-  const double th = theta[i];
+// Squared norms of the pencil residuals and of K x for the Ritz pairs i < ncols (two stages,
+// deterministic): resn[i] = ||KX_i + (1/theta_i) GX_i||^2, kxn[i] = ||KX_i||^2.
+__global__ void k_resnorm_partial(const double* KX, const double* GX, const double* theta, int64_t n, int64_t stride,
+                                  double* partial) {
+  __shared__ double red[2][32];
+  const int col = blockIdx.y;
+  const double th = theta[col];
   const double lam = th != 0.0 ? 1.0 / th : 0.0;
-  R[(int64_t)i * stride + k] = KX[(int64_t)i * stride + k] + lam * GX[(int64_t)i * stride + k];
+  const int64_t k0 = (int64_t)blockIdx.x * kColChunk;
+  double sr = 0.0, sk = 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < n && k < k0 + kColChunk; k += blockDim.x) {
+    const double kx = KX[(int64_t)col * stride + k];
+    const double r = kx + lam * GX[(int64_t)col * stride + k];
+    sr += r * r;
+    sk += kx * kx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    sk += __shfl_xor_sync(0xffffffffu, sk, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = sk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partial[2 * ((size_t)col * gridDim.x + blockIdx.x)] = a;
+    partial[2 * ((size_t)col * gridDim.x + blockIdx.x) + 1] = b;
+  }
+}
+__global__ void k_resnorm_final(const double* partial, int chunks, int ncols, double* resn, double* kxn) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < chunks; ++k) {
+    a += partial[2 * ((size_t)c * chunks + k)];
+    b += partial[2 * ((size_t)c * chunks + k) + 1];
+  }
+  resn[c] = a;
+  kxn[c] = b;
+}
+
+static void launch_resnorms(const double* KX, const double* GX, const double* theta, int ncols, int64_t n,
+                            int64_t stride, double* resn, double* kxn, double* partial, cudaStream_t s) {
+  const int chunks = (int)((n + kColChunk - 1) / kColChunk);
+  ::tobk::note_launch(), k_resnorm_partial<<<dim3(chunks, ncols), 256, 0, s>>>(KX, GX, theta, n, stride, partial);
+  ::tobk::note_launch(), k_resnorm_final<<<(ncols + 63) / 64, 64, 0, s>>>(partial, chunks, ncols, resn, kxn);
 }
 
 // W_c = -GX_{s} - theta_s KX_{s}, s = sel[c]: the residual of the pencil -G x = mu K x at the Ritz
@@ -198,7 +241,6 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
   double* W = h->EW + (size_t)3 * nb * n;
   double* KW = h->EKW;
   double* Tb = h->EKW + (size_t)nb * n;
-  double* GW = h->EGW;
   double* theta = h->dscal;          // [mmax]
   double* resn = h->dscal + 128;     // [q]  ||r_i||^2
   double* kxn = h->dscal + 256;      // [q]  ||K x_i||^2
@@ -247,29 +289,30 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       launch_combine(h->V, m, Cs, nadd, nadd, -1.0, 1.0, W, n, sd, st);
     }
     prof_end(h);
-    // ---- K-orthonormalise within the block (Cholesky QR, twice)
+    // ---- K-orthonormalise within the block (Cholesky QR, twice: W -> Tb -> the basis columns
+    // m .. m + nadd - 1, which the block's K and G images join)
+    double* Vn = h->V + (size_t)m * n;
+    double* KVn = h->KV + (size_t)m * n;
+    double* GVn = h->GV + (size_t)m * n;
     for (int pass = 0; pass < 2; ++pass) {
-      apply_K_level(h, j, W, KW, nadd, sd);
+      const double* src = pass == 0 ? W : Tb;
+      double* dst = pass == 0 ? Tb : Vn;
+      apply_K_level(h, j, src, KW, nadd, sd);
       prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
-      eig_gram(h, W, nadd, KW, nadd, n, sd, M);
+      eig_gram(h, src, nadd, KW, nadd, n, sd, M);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)nadd);
       ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, nadd, Rinv, sinfo);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
-      launch_combine(W, nadd, Rinv, nadd, nadd, 1.0, 0.0, Tb, n, sd, st);
-      cudaMemcpyAsync(W, Tb, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
+      launch_combine(src, nadd, Rinv, nadd, nadd, 1.0, 0.0, dst, n, sd, st);
       prof_end(h);
     }
-    apply_K_level(h, j, W, KW, nadd, sd);
-    apply_G_level(h, j, W, GW, nadd, sd);
-    // ---- append to the basis
-    cudaMemcpyAsync(h->V + (size_t)m * n, W, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(h->KV + (size_t)m * n, KW, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(h->GV + (size_t)m * n, GW, sizeof(double) * nadd * n, cudaMemcpyDeviceToDevice, st);
+    apply_K_level(h, j, Vn, KVn, nadd, sd);
+    apply_G_level(h, j, Vn, GVn, nadd, sd);
     const int mn = m + nadd;
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)mn * n);
-    eig_gram(h, h->V, mn, GW, nadd, n, sd, Cs);
+    eig_gram(h, h->V, mn, GVn, nadd, n, sd, Cs);
     ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, -1.0, h->Hs, mmax);
     prof_end(h);
     m = mn;
@@ -297,12 +340,8 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     rr_prev = m;
     const int kk = std::min(nb, m);
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)m * n);
-    launch_combine(h->V, m, h->Ys, mmax, kk, 1.0, 0.0, X, n, sd, st);
-    launch_combine(h->KV, m, h->Ys, mmax, kk, 1.0, 0.0, KX, n, sd, st);
-    launch_combine(h->GV, m, h->Ys, mmax, kk, 1.0, 0.0, GX, n, sd, st);
-    ::tobk::note_launch(), k_eig_residual_vec<<<dim3(nblk(n), q), 256, 0, st>>>(KX, GX, theta, Tb, n, sd);
-    launch_coldots(Tb, Tb, q, n, sd, resn, h->gram_partial, st);
-    launch_coldots(KX, KX, q, n, sd, kxn, h->gram_partial, st);
+    launch_combine3(h->V, h->KV, h->GV, m, h->Ys, mmax, kk, X, KX, GX, n, sd, st);
+    launch_resnorms(KX, GX, theta, q, n, sd, resn, kxn, h->gram_partial, st);
     prof_end(h);
     cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double) * 512, cudaMemcpyDeviceToHost, st);
     if (h->gtc_err)

@@ -55,7 +55,7 @@ struct tobk_handle {
   double* esens = nullptr;   // [m][...] element scratch for adjoint RHS (Gauss-point vectors)
   // eigen workspace at the eigen level
   int eig_nb = 0, eig_mmax = 0;
-  double *V = nullptr, *KV = nullptr, *GV = nullptr, *EW = nullptr, *EKW = nullptr, *EGW = nullptr;
+  double *V = nullptr, *KV = nullptr, *GV = nullptr, *EW = nullptr, *EKW = nullptr;
   double *Hs = nullptr, *Bs = nullptr, *Ys = nullptr, *Cs = nullptr, *gram_partial = nullptr;
   double* small_host = nullptr;  // pinned
   double* tri = nullptr;         // scratch of the split small eigensolver (reflectors, T, vectors)

@@ -527,13 +527,18 @@ constexpr int kGJB = 32;
 __global__ void __launch_bounds__(kGJB * kGJB) k_bgj_diag(const double* __restrict__ A, int64_t n, int64_t k0, int bs,
                                                           double* __restrict__ P) {
   __shared__ double M[kGJB][kGJB + 1];
+  __shared__ double rp_s;
   const int i = threadIdx.y, j = threadIdx.x;
   if (i < bs && j < bs) M[i][j] = A[(k0 + i) * n + k0 + j];
   __syncthreads();
   for (int p = 0; p < bs; ++p) {
+    // one reciprocal per pivot (FP64 division is a long instruction sequence at 2 FP64 operations
+    // per clock per SM: 1024 threads dividing each would dominate the block)
+    if (i == 0 && j == 0) rp_s = 1.0 / M[p][p];
+    __syncthreads();
     double v = 0.0;
     if (i < bs && j < bs) {
-      const double r = 1.0 / M[p][p];
+      const double r = rp_s;
       if (i == p && j == p)
         v = r;
       else if (i == p)
@@ -953,7 +958,21 @@ __global__ void __launch_bounds__(kThreads) k_cg_dots(int64_t n, const double* _
   if (s[SC_ACTIVE] == 0.0) return;
   const int64_t off = (int64_t)rhs * stride;
   double v[3] = {0.0, 0.0, 0.0};  // z.r, z.q_old, p_old.r
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  // two grid-stride elements per trip, loads first (twice the loads in flight), summed in the order
+  // of the plain grid-stride loop
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
+    const double z0 = z[off + i], r0 = r[off + i], q0 = q[off + i], p0 = p[off + i];
+    const double z1 = z[off + i + step], r1 = r[off + i + step], q1 = q[off + i + step], p1 = p[off + i + step];
+    v[0] += z0 * r0;
+    v[1] += z0 * q0;
+    v[2] += p0 * r0;
+    v[0] += z1 * r1;
+    v[1] += z1 * q1;
+    v[2] += p1 * r1;
+  }
+  if (i < n) {
     const double zi = z[off + i], ri = r[off + i];
     v[0] += zi * ri;
     v[1] += zi * q[off + i];
@@ -1031,7 +1050,20 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* __res
   const int64_t off = (int64_t)rhs * stride;
   const double alpha = s[SC_ALPHA];
   double v[1] = {0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {  // as in k_cg_dots: two elements per trip, plain order
+    const double x0 = x[off + i], p0 = p[off + i], r0 = r[off + i], q0 = q[off + i];
+    const double x1 = x[off + i + step], p1 = p[off + i + step], r1 = r[off + i + step], q1 = q[off + i + step];
+    x[off + i] = x0 + alpha * p0;
+    x[off + i + step] = x1 + alpha * p1;
+    const double ra = r0 - alpha * q0, rb = r1 - alpha * q1;
+    r[off + i] = ra;
+    r[off + i + step] = rb;
+    v[0] += ra * ra;
+    v[0] += rb * rb;
+  }
+  if (i < n) {
     x[off + i] += alpha * p[off + i];
     const double ri = r[off + i] - alpha * q[off + i];
     r[off + i] = ri;
@@ -1188,30 +1220,58 @@ void launch_true_residual(const LevelOpDesc& d, const double* b, const double* x
 // ================================================================================================
 // tall-skinny block products for the block eigensolver
 // ================================================================================================
-constexpr int kGramChunk = 64;
+constexpr int kGramChunk = 32;  // smallest chunk of rows per block
 
-// partial[chunk][i][j] = sum_{k in chunk} A[i][k] B[j][k]
-__global__ void k_gram_partial(const double* __restrict__ A, int na, const double* __restrict__ B, int nb, int64_t n,
-                               int64_t stride, double* __restrict__ partial) {
-  extern __shared__ double sm[];
-  double* sA = sm;                       // [na][chunk]
-  double* sB = sm + na * kGramChunk;     // [nb][chunk]
-  const int64_t k0 = (int64_t)blockIdx.x * kGramChunk;
-  const int len = (n - k0) < kGramChunk ? (int)(n - k0) : kGramChunk;
-  for (int t = threadIdx.x; t < na * kGramChunk; t += blockDim.x) {
-    const int i = t / kGramChunk, kk = t % kGramChunk;
-    sA[t] = kk < len ? A[(int64_t)i * stride + k0 + kk] : 0.0;
+// SMs of the current device (queried once per device).
+static int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int c = 0;
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = c > 0 ? c : 152;
   }
-  for (int t = threadIdx.x; t < nb * kGramChunk; t += blockDim.x) {
-    const int j = t / kGramChunk, kk = t % kGramChunk;
-    sB[t] = kk < len ? B[(int64_t)j * stride + k0 + kk] : 0.0;
+  return cached[dev];
+}
+
+// Rows per block of the Gram product: the n rows are split into two chunks per SM (the product runs
+// at GB300's FP64 rate of 2 FMA per clock per SM, so an SM with one chunk more than the others sets
+// the time of the launch; two resident blocks per SM overlap one block's loads with the other's
+// multiply-adds), at least kGramChunk rows and no more than the shared memory holds.
+static int gram_chunk_rows(int na, int nb, int64_t n) {
+  const int64_t per_sm = (n + 2 * device_sm_count() - 1) / (2 * device_sm_count());
+  const int chunk = (int)std::min<int64_t>(std::max<int64_t>(per_sm, kGramChunk), 1 << 20);
+  const int cap = std::max(kGramChunk, (int)((200 * 1024) / (sizeof(double) * (size_t)(na + nb))) - 1);
+  return std::min(chunk, cap);
+}
+
+// partial[chunk][i][j] = sum_{k in chunk} A[i][k] B[j][k]; shared rows of odd stride len + 1.
+__global__ void k_gram_partial(const double* __restrict__ A, int na, const double* __restrict__ B, int nb, int64_t n,
+                               int64_t stride, int chunk, double* __restrict__ partial) {
+  extern __shared__ double sm[];
+  const int ldc = chunk + 1;
+  double* sA = sm;              // [na][ldc]
+  double* sB = sm + na * ldc;   // [nb][ldc]
+  const int64_t k0 = (int64_t)blockIdx.x * chunk;
+  const int len = (n - k0) < chunk ? (int)(n - k0) : chunk;
+  for (int t = threadIdx.x; t < na * chunk; t += blockDim.x) {
+    const int i = t / chunk, kk = t % chunk;
+    sA[i * ldc + kk] = kk < len ? A[(int64_t)i * stride + k0 + kk] : 0.0;
+  }
+  for (int t = threadIdx.x; t < nb * chunk; t += blockDim.x) {
+    const int j = t / chunk, kk = t % chunk;
+    sB[j * ldc + kk] = kk < len ? B[(int64_t)j * stride + k0 + kk] : 0.0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
     const int i = t / nb, j = t % nb;
+    const double* a = sA + i * ldc;
+    const double* b = sB + j * ldc;
     double s = 0.0;
 #pragma unroll 8
-    for (int kk = 0; kk < kGramChunk; ++kk) s += sA[i * kGramChunk + kk] * sB[j * kGramChunk + kk];
+    for (int kk = 0; kk < len; ++kk) s += a[kk] * b[kk];
     partial[(size_t)blockIdx.x * na * nb + t] = s;
   }
 }
@@ -1236,7 +1296,14 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ p
   }
 }
 
-int gram_partial_blocks(int64_t n) { return (int)((n + kGramChunk - 1) / kGramChunk); }
+// Upper bound of the chunks of any Gram product over n rows with na, nb <= 64 (sizes the partial
+// buffer): a chunk holds at least min(max(n / (2 SMs), kGramChunk), 199) rows, since the shared-memory
+// cap of gram_chunk_rows is at least 199 rows for na + nb <= 128.
+int gram_partial_blocks(int64_t n) {
+  const int64_t per_sm = (n + 2 * device_sm_count() - 1) / (2 * device_sm_count());
+  const int64_t cmin = std::min<int64_t>(std::max<int64_t>(per_sm, kGramChunk), 199);
+  return (int)((n + cmin - 1) / cmin);
+}
 
 void launch_gram_final(const double* partial, int nchunks, int nout, double* C, cudaStream_t s) {
   ::tobk::note_launch(), k_gram_final<<<(nout + 31) / 32, 256, 0, s>>>(partial, nchunks, nout, C);
@@ -1244,51 +1311,111 @@ void launch_gram_final(const double* partial, int nchunks, int nout, double* C, 
 
 void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
                  double* partial, cudaStream_t s) {
-  const int chunks = gram_partial_blocks(n);
-  const size_t smem = sizeof(double) * (size_t)(na + nb) * kGramChunk;
+  const int chunk = gram_chunk_rows(na, nb, n);
+  const int chunks = (int)((n + chunk - 1) / chunk);
+  const size_t smem = sizeof(double) * (size_t)(na + nb) * (chunk + 1);
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
     configured = true;
   }
-  ::tobk::note_launch(), k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, partial);
+  ::tobk::note_launch(), k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, chunk, partial);
   ::tobk::note_launch(), k_gram_final<<<(na * nb + 31) / 32, 256, 0, s>>>(partial, chunks, na * nb, C);
 }
 
-// Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j]; one thread per row index, up to 32 outputs per
-// pass over blockIdx.y tiles of columns.
-// Each thread owns one row index k and kCombineJ consecutive output columns, so that the grid has
-// enough blocks to cover the SMs even for the short vectors of the coarse eigen level.
-constexpr int kCombineJ = 4;
-__global__ void k_combine(const double* __restrict__ X, int nx, const double* __restrict__ C, int ldc, int ny,
-                          double alpha, double beta, double* __restrict__ Y, int64_t n, int64_t stride) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = blockIdx.y * kCombineJ;
-  const int nj = min(kCombineJ, ny - j0);
-  if (k >= n) return;
-  double acc[kCombineJ];
+// Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j].  A work item is one row index k and kCombineJ
+// consecutive output columns (items ordered row-fastest, so loads of X and stores of Y coalesce).
+// The items are cut into equal contiguous ranges, one per block, and the grid is a fixed number of
+// blocks per SM, so that every SM gets the same share of the FP64 multiply-adds even when the
+// vectors are short (GB300 runs FP64 at 2 FMA per clock per SM: an SM with one extra block sets the
+// time of the launch).
+constexpr int kCombineJ = 2;
+constexpr int kCombineThreads = 128;
+__global__ void __launch_bounds__(kCombineThreads) k_combine(const double* __restrict__ X, int nx,
+                                                             const double* __restrict__ C, int ldc, int ny,
+                                                             double alpha, double beta, double* __restrict__ Y,
+                                                             int64_t n, int64_t stride, int64_t per_block) {
+  const int groups = (ny + kCombineJ - 1) / kCombineJ;
+  const int64_t items = n * groups;
+  const int64_t end = min(items, ((int64_t)blockIdx.x + 1) * per_block);
+  for (int64_t it = (int64_t)blockIdx.x * per_block + threadIdx.x; it < end; it += blockDim.x) {
+    const int64_t k = it % n;
+    const int j0 = (int)(it / n) * kCombineJ;
+    const int nj = min(kCombineJ, ny - j0);
+    double acc[kCombineJ];
 #pragma unroll
-  for (int j = 0; j < kCombineJ; ++j) acc[j] = 0.0;
-  for (int i = 0; i < nx; ++i) {
-    const double xi = __ldg(X + (int64_t)i * stride + k);
-    const double* ci = C + (size_t)i * ldc + j0;
+    for (int j = 0; j < kCombineJ; ++j) acc[j] = 0.0;
+    for (int i = 0; i < nx; ++i) {
+      const double xi = __ldg(X + (int64_t)i * stride + k);
+      const double* ci = C + (size_t)i * ldc + j0;
 #pragma unroll
-    for (int j = 0; j < kCombineJ; ++j)
-      if (j < nj) acc[j] += xi * __ldg(ci + j);
-  }
+      for (int j = 0; j < kCombineJ; ++j)
+        if (j < nj) acc[j] += xi * __ldg(ci + j);
+    }
 #pragma unroll
-  for (int j = 0; j < kCombineJ; ++j) {
-    if (j < nj) {
-      double* y = Y + (int64_t)(j0 + j) * stride + k;
-      *y = (beta == 0.0 ? 0.0 : beta * *y) + alpha * acc[j];
+    for (int j = 0; j < kCombineJ; ++j) {
+      if (j < nj) {
+        double* y = Y + (int64_t)(j0 + j) * stride + k;
+        *y = (beta == 0.0 ? 0.0 : beta * *y) + alpha * acc[j];
+      }
     }
   }
 }
 
+// Y_s[j] = sum_i X_s[i] C[i][j] for nsrc <= 3 pairs (X_s, Y_s) sharing the coefficients C: a block
+// of basis vectors and its K and G images in one launch.  Items as in k_combine, source slowest.
+struct CombineSet {
+  const double* X[3];
+  double* Y[3];
+};
+__global__ void __launch_bounds__(kCombineThreads) k_combine_set(CombineSet cs, int nsrc, int nx,
+                                                                 const double* __restrict__ C, int ldc, int ny,
+                                                                 int64_t n, int64_t stride, int64_t per_block) {
+  const int groups = (ny + kCombineJ - 1) / kCombineJ;
+  const int64_t per_src = n * groups;
+  const int64_t items = per_src * nsrc;
+  const int64_t end = min(items, ((int64_t)blockIdx.x + 1) * per_block);
+  for (int64_t it = (int64_t)blockIdx.x * per_block + threadIdx.x; it < end; it += blockDim.x) {
+    const int src = (int)(it / per_src);
+    const int64_t rem = it - (int64_t)src * per_src;
+    const int64_t k = rem % n;
+    const int j0 = (int)(rem / n) * kCombineJ;
+    const int nj = min(kCombineJ, ny - j0);
+    const double* X = src == 0 ? cs.X[0] : (src == 1 ? cs.X[1] : cs.X[2]);
+    double* Y = src == 0 ? cs.Y[0] : (src == 1 ? cs.Y[1] : cs.Y[2]);
+    double acc[kCombineJ];
+#pragma unroll
+    for (int j = 0; j < kCombineJ; ++j) acc[j] = 0.0;
+    for (int i = 0; i < nx; ++i) {
+      const double xi = __ldg(X + (int64_t)i * stride + k);
+      const double* ci = C + (size_t)i * ldc + j0;
+#pragma unroll
+      for (int j = 0; j < kCombineJ; ++j)
+        if (j < nj) acc[j] += xi * __ldg(ci + j);
+    }
+#pragma unroll
+    for (int j = 0; j < kCombineJ; ++j)
+      if (j < nj) Y[(int64_t)(j0 + j) * stride + k] = acc[j];
+  }
+}
+
+void launch_combine3(const double* X0, const double* X1, const double* X2, int nx, const double* C, int ldc, int ny,
+                     double* Y0, double* Y1, double* Y2, int64_t n, int64_t stride, cudaStream_t s) {
+  CombineSet cs{{X0, X1, X2}, {Y0, Y1, Y2}};
+  const int64_t items = 3 * n * ((ny + kCombineJ - 1) / kCombineJ);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 31) / 32, 4 * (int64_t)device_sm_count()));
+  const int64_t per_block = (items + grid - 1) / grid;
+  ::tobk::note_launch(), k_combine_set<<<(unsigned)grid, kCombineThreads, 0, s>>>(cs, 3, nx, C, ldc, ny, n, stride,
+                                                                                 per_block);
+}
+
 void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta, double* Y,
                     int64_t n, int64_t stride, cudaStream_t s) {
-  dim3 grid(blocks_for(n), (ny + kCombineJ - 1) / kCombineJ);
-  ::tobk::note_launch(), k_combine<<<grid, kThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n, stride);
+  const int64_t items = n * ((ny + kCombineJ - 1) / kCombineJ);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 31) / 32, 4 * (int64_t)device_sm_count()));
+  const int64_t per_block = (items + grid - 1) / grid;
+  ::tobk::note_launch(), k_combine<<<(unsigned)grid, kCombineThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n,
+                                                                             stride, per_block);
 }
 
 }  // namespace tobk

@@ -59,6 +59,22 @@ void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double
                   double* y, SmoothArgs<double> sm, int nr, int64_t stride, cudaStream_t s);
 void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
                     float* y, SmoothArgs<float> sm, int nr, int64_t stride, cudaStream_t s);
+
+// 2D stencil levels, transfers fused into the sweeps (stencil.cu):
+// y = v + d with v = z + P zc (the prolongated coarse correction added on the fly, not at fixed
+// DOFs) and d = coef[0] d_in + coef[1] dinv (b - K v) -- the prolongation and the first
+// post-smoothing step of a V-cycle level in one launch (zc [nr][cstride] on the coarse grid gc).
+template <typename T>
+void launch_stencil_jac_prolong_2d(const Grid& g, const Grid& gc, const T* S, const uint8_t* fixed, const T* z,
+                                   const T* zc, const T* b, const T* dinv, T* y, SmoothArgs<T> sm, int nr,
+                                   int64_t stride, int64_t cstride, cudaStream_t s);
+// bc = P^T (b - K z) on the coarse grid gc (0 at its fixed DOFs), and when zc != nullptr the coarse
+// level's first damped step zc = coef_c[1] dinv_c bc (also into dc when dc != nullptr) -- the
+// residual, the restriction and the coarse pre-smoothing start in one launch.
+template <typename T>
+void launch_stencil_res_restrict_2d(const Grid& g, const Grid& gc, const T* S, const uint8_t* fixed, const T* z,
+                                    const T* b, int64_t stride, const uint8_t* fixed_c, T* bc, int64_t cstride,
+                                    const T* dinv_c, const T* coef_c, T* zc, T* dc, int nr, cudaStream_t s);
 // y = G v with G_e = Gs_e (x) I (Gs includes E_sigma), fine level.
 void launch_apply_kron(const Grid& g, const uint8_t* fixed, const double* Gs, const double* v, double* y,
                        int nr, int64_t stride, cudaStream_t s);
@@ -157,6 +173,9 @@ void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, in
 // for overwrite / accumulate; alpha scales the product.
 void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, double alpha, double beta,
                     double* Y, int64_t n, int64_t stride, cudaStream_t s);
+// Y_s = X_s C (s = 0, 1, 2; X_s [nx][stride], Y_s [ny][stride]) in one launch
+void launch_combine3(const double* X0, const double* X1, const double* X2, int nx, const double* C, int ldc, int ny,
+                     double* Y0, double* Y1, double* Y2, int64_t n, int64_t stride, cudaStream_t s);
 int gram_partial_blocks(int64_t n);
 // C[o] = sum over chunks of partial[c][o] in a fixed order (the second stage of launch_gram)
 void launch_gram_final(const double* partial, int nchunks, int nout, double* C, cudaStream_t s);

@@ -34,43 +34,99 @@ static_assert(kRRRefineSteps >= 2, "the eigensolver's warm start reads the first
 // Stage 1.  All m eigenvectors of H [m][ld] (symmetric part) in FP32 by cyclic Jacobi, written in
 // FP64 to X [m][m] (column c = eigenvector of the c-th largest eigenvalue).  The matrix is padded
 // to P (a multiple of 8, P >= m; padding rows are never rotated).  One round applies P/2 disjoint
-// rotations J_k (round-robin pairing) to C <- J C J^T as independent 2 x 2 blocks, one thread per
-// pair of pairs (warp A, lane B), so a round costs two barriers.  The rotations only steer the FP32
-// stage (the FP64 refinement below fixes the digits), so they use fast reciprocal / square-root
-// approximations.  Shared arrays have the odd row stride P + 1, so that row and column walks are
-// free of bank conflicts.  Warm start: when mprev > 0, Xp [mprev][mprev] (the previous eigenvectors
-// of the leading mprev x mprev block, FP64) starts the accumulated rotation V = diag(Xp, I), so that
-// the old block is already nearly diagonal.  info[0] = sweeps.
+// rotations J_k (round-robin pairing of the P indices) as C <- J C J^T, as independent 2 x 2
+// blocks.  Warp w owns the row slots A = w and A = w + P/4 of a round; lane B < P/2 owns column slot
+// B: the thread updates the blocks (A, B) of C and rows B and B + P/2 of the accumulated rotation's
+// columns p_A, q_A.  Lane k of every warp computes the rotation of slot k from the diagonal block of C
+// (the same arithmetic on the same values in every warp) and the warp's row rotations are broadcast
+// by shuffles.  C is double-buffered (a round reads one copy and writes the other), so a round costs
+// one barrier and no thread waits for another's rotation.  The rotations only steer the FP32 stage
+// (the FP64 refinement below fixes the digits), so they use fast reciprocal / square-root
+// approximations.  Shared arrays have the odd row stride P + 1.  Warm start: when mprev > 0, Xp
+// [mprev][mprev] (the previous eigenvectors of the leading mprev x mprev block, FP64) starts the
+// accumulated rotation V = diag(Xp, I), so that the old block is already nearly diagonal.
+// info[0] = sweeps.
+namespace rr_detail {
+// Round-robin (circle) pairing of P indices: in round r (0 <= r < P - 1), slot k pairs (p, q); every
+// index appears in exactly one slot of a round and every pair in exactly one round of a sweep.
 template <int P>
-__global__ void __launch_bounds__(16 * P) k_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev,
-                                                     double* X, double* info, double tol2) {
-  static_assert(P % 8 == 0 && P <= kRRMax, "padded size");  // P % 8 == 0: NP * P is a multiple of 32
-  constexpr int NP = P / 2;    // rotations per round
-  constexpr int NT = 32 * NP;  // threads: warp A, lane B < NP owns the 2 x 2 block (A, B)
+__device__ __forceinline__ void pair_of(int r, int k, int& p, int& q) {
+  if (k == 0) {
+    p = P - 1;
+    q = r;
+  } else {
+    p = r + k;
+    if (p >= P - 1) p -= P - 1;
+    q = r - k;
+    if (q < 0) q += P - 1;
+  }
+}
+
+// Rotation (c, s) that zeroes C[p][q] when rows and columns p, q are replaced by c p - s q and
+// s p + c q: t = s / c is the smaller root of t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq).
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float& c, float& s) {
+  c = 1.f;
+  s = 0.f;
+  if (apq != 0.f) {
+    const float tau = __fdividef(aqq - app, 2.f * apq);
+    const float at = fabsf(tau);
+    // tan of the rotation angle, 1 / (|tau| + sqrt(1 + tau^2)), signed like tau
+    float tt = at < 1e18f ? __fdividef(1.f, at + (1.f + at * at) * rsqrtf(1.f + at * at)) : __fdividef(0.5f, at);
+    tt = tau >= 0.f ? tt : -tt;
+    c = rsqrtf(1.f + tt * tt);
+    s = tt * c;
+  }
+}
+
+// The 2 x 2 block of C at rows (pa, qa), columns (pb, qb) rotated on both sides, Cc -> Cn.
+template <int LD>
+__device__ __forceinline__ void rotate_block(const float* Cc, float* Cn, int pa, int qa, float ca, float sa, int pb,
+                                             int qb, float cb, float sb) {
+  const float b00 = Cc[pa * LD + pb], b01 = Cc[pa * LD + qb], b10 = Cc[qa * LD + pb], b11 = Cc[qa * LD + qb];
+  const float l00 = ca * b00 - sa * b10, l01 = ca * b01 - sa * b11;
+  const float l10 = sa * b00 + ca * b10, l11 = sa * b01 + ca * b11;
+  Cn[pa * LD + pb] = cb * l00 - sb * l01;
+  Cn[pa * LD + qb] = sb * l00 + cb * l01;
+  Cn[qa * LD + pb] = cb * l10 - sb * l11;
+  Cn[qa * LD + qb] = sb * l10 + cb * l11;
+}
+
+// Accumulated rotation V <- V J^T on columns pa, qa (stored as rows of V), at rows r0 and r1.
+template <int LD>
+__device__ __forceinline__ void rotate_vcols(float* V, int pa, int qa, float ca, float sa, int r0, int r1) {
+  float* vp = V + pa * LD;
+  float* vq = V + qa * LD;
+  const float p0 = vp[r0], p1 = vp[r1], q0 = vq[r0], q1 = vq[r1];
+  vp[r0] = ca * p0 - sa * q0;
+  vp[r1] = ca * p1 - sa * q1;
+  vq[r0] = sa * p0 + ca * q0;
+  vq[r1] = sa * p1 + ca * q1;
+}
+}  // namespace rr_detail
+
+template <int P>
+__global__ void __launch_bounds__(8 * P) k_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev,
+                                                    double* X, double* info, double tol2) {
+  static_assert(P % 8 == 0 && P <= kRRMax, "padded size");
+  constexpr int NP = P / 2;    // rotations per round (column slots, one per lane)
+  constexpr int NW = NP / 2;   // warps; warp w owns row slots w and w + NW
+  constexpr int NT = 32 * NW;
   constexpr int LD = P + 1;
   constexpr int SZ = P * LD;
   extern __shared__ float sm32[];
-  float* C = sm32;           // rotated matrix
-  float* V = sm32 + SZ;      // accumulated rotations, transposed: V[col * LD + row]
-  float* T = sm32 + 2 * SZ;  // set-up scratch
-  __shared__ float4 rot[NP];                       // (c, s, p, q) of the round's slots
-  __shared__ unsigned char pair_tab[(P - 1) * P];  // round r, slot k -> (p, q)
-  __shared__ double red[2 * (NT / 32)];
+  float* Cc = sm32;          // current copy of the rotated matrix
+  float* Cn = sm32 + SZ;     // next copy (and the warm start's scratch)
+  float* V = sm32 + 2 * SZ;  // accumulated rotations, transposed: V[col * LD + row]
+  __shared__ unsigned short ptab[(P - 1) * NP];  // round r, slot k -> p | q << 8
+  __shared__ double red[2 * NW];
   __shared__ double hmax_s;
   __shared__ int done_s;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const bool own = lane < NP;
   for (int q = t; q < (P - 1) * NP; q += NT) {
-    const int round = q / NP, k = q % NP;
     int p, r;
-    if (k == 0) {
-      p = P - 1;
-      r = round;
-    } else {
-      p = (round + k) % (P - 1);
-      r = (round - k + (P - 1)) % (P - 1);
-    }
-    pair_tab[2 * q] = (unsigned char)p;
-    pair_tab[2 * q + 1] = (unsigned char)r;
+    rr_detail::pair_of<P>(q / NP, q % NP, p, r);
+    ptab[q] = (unsigned short)(p | (r << 8));
   }
   // scale by max |H| so that the FP32 working range holds any problem scaling
   double mx = 0.0;
@@ -80,7 +136,7 @@ __global__ void __launch_bounds__(16 * P) k_rr_eig32(const double* H, int m, int
   __syncthreads();
   if (t == 0) {
     double a = 0.0;
-    for (int w = 0; w < NT / 32; ++w) a = fmax(a, red[w]);
+    for (int w = 0; w < NW; ++w) a = fmax(a, red[w]);
     hmax_s = a > 0.0 ? a : 1.0;
   }
   __syncthreads();
@@ -90,35 +146,46 @@ __global__ void __launch_bounds__(16 * P) k_rr_eig32(const double* H, int m, int
     float h = 0.f, v = (i == j) ? 1.f : 0.f;
     if (i < m && j < m) h = inv * (float)(0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]));
     if (i < mprev && j < mprev) v = (float)Xp[(size_t)i * mprev + j];
-    C[i * LD + j] = h;
+    Cc[i * LD + j] = h;
     V[j * LD + i] = v;
   }
   __syncthreads();
-  if (mprev > 0) {  // C <- V^T C V
-    for (int q = t; q < P * P; q += NT) {  // T <- C V
-      const int i = q / P, j = q % P;
-      float a = 0.f;
+  if (mprev > 0) {  // C <- V^T C V in 2 x 2 register tiles (rows 2A, 2A + 1, columns 2B, 2B + 1)
+    const int j0 = 2 * lane;
+    for (int pass = 0; pass < 2; ++pass) {
+      const float* Lm = pass == 0 ? Cc : V;  // left factor rows:  C[i][k]  |  V^T[i][k] = V[i * LD + k]
+      const float* Rm = pass == 0 ? V : Cn;  // right factor:      V[j][k] (= V(k, j))  |  T[k][j]
+      float* Out = pass == 0 ? Cn : Cc;
+      if (own) {
+        for (int half = 0; half < 2; ++half) {
+          const int i0 = 2 * (warp + half * NW);
+          float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
 #pragma unroll 8
-      for (int k = 0; k < P; ++k) a += C[i * LD + k] * V[j * LD + k];
-      T[i * LD + j] = a;
+          for (int k = 0; k < P; ++k) {
+            const float l0 = Lm[i0 * LD + k], l1 = Lm[(i0 + 1) * LD + k];
+            const float r0 = pass == 0 ? Rm[j0 * LD + k] : Rm[k * LD + j0];
+            const float r1 = pass == 0 ? Rm[(j0 + 1) * LD + k] : Rm[k * LD + j0 + 1];
+            a00 += l0 * r0;
+            a01 += l0 * r1;
+            a10 += l1 * r0;
+            a11 += l1 * r1;
+          }
+          Out[i0 * LD + j0] = a00;
+          Out[i0 * LD + j0 + 1] = a01;
+          Out[(i0 + 1) * LD + j0] = a10;
+          Out[(i0 + 1) * LD + j0 + 1] = a11;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int q = t; q < P * P; q += NT) {  // C <- V^T T
-      const int i = q / P, j = q % P;
-      float a = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < P; ++k) a += V[i * LD + k] * T[k * LD + j];
-      C[i * LD + j] = a;
-    }
-    __syncthreads();
   }
   int sweeps = 0;
   for (; sweeps < 30; ++sweeps) {
     // convergence: off-diagonal mass below tol2 of the total
-    double o = 0.0, a = 0.0;
+    float o = 0.f, a = 0.f;
     for (int q = t; q < P * P; q += NT) {
       const int i = q / P, j = q % P;
-      const double v = (double)C[i * LD + j] * (double)C[i * LD + j];
+      const float v = Cc[i * LD + j] * Cc[i * LD + j];
       a += v;
       if (i != j) o += v;
     }
@@ -133,7 +200,7 @@ __global__ void __launch_bounds__(16 * P) k_rr_eig32(const double* H, int m, int
     __syncthreads();
     if (t == 0) {
       double oo = 0.0, aa = 0.0;
-      for (int w = 0; w < NT / 32; ++w) {
+      for (int w = 0; w < NW; ++w) {
         oo += red[2 * w];
         aa += red[2 * w + 1];
       }
@@ -142,52 +209,40 @@ __global__ void __launch_bounds__(16 * P) k_rr_eig32(const double* H, int m, int
     __syncthreads();
     if (done_s) break;
     for (int round = 0; round < P - 1; ++round) {
-      if (t < NP) {  // rotation of slot t
-        const int p = pair_tab[2 * (round * NP + t)], q = pair_tab[2 * (round * NP + t) + 1];
-        float c = 1.f, s = 0.f;
-        const float apq = C[p * LD + q];
-        if (p < m && q < m && apq != 0.f) {
-          const float tau = __fdividef(C[q * LD + q] - C[p * LD + p], 2.f * apq);
-          const float at = fabsf(tau);
-          // tan of the rotation angle, 1 / (|tau| + sqrt(1 + tau^2)), signed like tau
-          float tt = at < 1e18f ? __fdividef(1.f, at + (1.f + at * at) * rsqrtf(1.f + at * at)) : __fdividef(0.5f, at);
-          tt = tau >= 0.f ? tt : -tt;
-          c = rsqrtf(1.f + tt * tt);
-          s = tt * c;
-        }
-        rot[t] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
+      // rotation of column slot `lane` (lanes >= NP hold the identity)
+      int pq = 0;
+      float cB = 1.f, sB = 0.f;
+      if (own) {
+        pq = ptab[round * NP + lane];
+        const int pB = pq & 255, qB = pq >> 8;
+        if (pB < m && qB < m)
+          rr_detail::jacobi_rotation(Cc[pB * LD + pB], Cc[qB * LD + qB], Cc[pB * LD + qB], cB, sB);
+      }
+      // row slots warp and warp + NW: rotations and pairs from those lanes
+      const int A0 = warp, A1 = warp + NW;
+      const float cA0 = __shfl_sync(0xffffffffu, cB, A0), sA0 = __shfl_sync(0xffffffffu, sB, A0);
+      const float cA1 = __shfl_sync(0xffffffffu, cB, A1), sA1 = __shfl_sync(0xffffffffu, sB, A1);
+      const int pqA0 = __shfl_sync(0xffffffffu, pq, A0), pqA1 = __shfl_sync(0xffffffffu, pq, A1);
+      if (own) {
+        const int pB = pq & 255, qB = pq >> 8;
+        const int pA0 = pqA0 & 255, qA0 = pqA0 >> 8, pA1 = pqA1 & 255, qA1 = pqA1 >> 8;
+        rr_detail::rotate_block<LD>(Cc, Cn, pA0, qA0, cA0, sA0, pB, qB, cB, sB);
+        rr_detail::rotate_block<LD>(Cc, Cn, pA1, qA1, cA1, sA1, pB, qB, cB, sB);
+        rr_detail::rotate_vcols<LD>(V, pA0, qA0, cA0, sA0, lane, lane + NP);
+        rr_detail::rotate_vcols<LD>(V, pA1, qA1, cA1, sA1, lane, lane + NP);
       }
       __syncthreads();
-      if (lane < NP) {  // block (A, B): rows (p1, q1) of slot A = warp, columns (p2, q2) of slot B = lane
-        const float4 ra = rot[warp], rb = rot[lane];
-        const int p1 = __float_as_int(ra.z), q1 = __float_as_int(ra.w);
-        const int p2 = __float_as_int(rb.z), q2 = __float_as_int(rb.w);
-        const float b00 = C[p1 * LD + p2], b01 = C[p1 * LD + q2], b10 = C[q1 * LD + p2], b11 = C[q1 * LD + q2];
-        const float l00 = ra.x * b00 - ra.y * b10, l01 = ra.x * b01 - ra.y * b11;
-        const float l10 = ra.y * b00 + ra.x * b10, l11 = ra.y * b01 + ra.x * b11;
-        C[p1 * LD + p2] = rb.x * l00 - rb.y * l01;
-        C[p1 * LD + q2] = rb.y * l00 + rb.x * l01;
-        C[q1 * LD + p2] = rb.x * l10 - rb.y * l11;
-        C[q1 * LD + q2] = rb.y * l10 + rb.x * l11;
-      }
-      // accumulated rotation V <- V J^T: (slot k, row) items
-      for (int it = t; it < NP * P; it += NT) {
-        const int k = it / P, row = it % P;
-        const float4 rk = rot[k];
-        const int pk = __float_as_int(rk.z), qk = __float_as_int(rk.w);
-        const float vp = V[pk * LD + row], vq = V[qk * LD + row];
-        V[pk * LD + row] = rk.x * vp - rk.y * vq;
-        V[qk * LD + row] = rk.y * vp + rk.x * vq;
-      }
-      __syncthreads();
+      float* tmp = Cc;
+      Cc = Cn;
+      Cn = tmp;
     }
   }
   // descending order of the diagonal (ties by index); padding rows excluded
   for (int c = t; c < m; c += NT) {
-    const float tc = C[c * LD + c];
+    const float tc = Cc[c * LD + c];
     int rank = 0;
     for (int o = 0; o < m; ++o) {
-      const float to = C[o * LD + o];
+      const float to = Cc[o * LD + o];
       if (to > tc || (to == tc && o < c)) ++rank;
     }
     for (int i = 0; i < m; ++i) X[(size_t)i * m + rank] = (double)V[c * LD + i];
@@ -209,7 +264,7 @@ inline void rr_eig32_launch(const double* H, int m, int ld, const double* Xp, in
     cudaFuncSetAttribute(k_rr_eig32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_eig32_smem_bytes<P>());
     configured = true;
   }
-  k_rr_eig32<P><<<1, 16 * P, rr_eig32_smem_bytes<P>(), st>>>(H, m, ld, Xp, mprev, X, info, tol2);
+  k_rr_eig32<P><<<1, 8 * P, rr_eig32_smem_bytes<P>(), st>>>(H, m, ld, Xp, mprev, X, info, tol2);
 }
 
 inline void launch_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev, double* X, double* info,

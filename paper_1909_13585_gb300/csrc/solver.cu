@@ -192,7 +192,6 @@ static void layout(tobk_handle* h, Arena& a) {
   h->GV = a.take<double>((size_t)mm * ne);
   h->EW = a.take<double>((size_t)(4 * nb + mm) * ne);   // X, KX, GX, W blocks + restart scratch
   h->EKW = a.take<double>((size_t)2 * nb * ne);
-  h->EGW = a.take<double>((size_t)nb * ne);
   h->Hs = a.take<double>((size_t)mm * mm);
   h->Bs = a.take<double>((size_t)mm * mm);
   h->Ys = a.take<double>((size_t)mm * mm);
@@ -480,6 +479,9 @@ void prof_flush(tobk_handle* h) {
   h->prof_pending.clear();
 }
 
+// Node x RHS count below which a 2D stencil level fuses its residual into the restriction.
+constexpr int64_t kFusedResidualWork = 131072;
+
 // z0_ready: the restriction into this level already took the first smoothing step (z, dA written)
 static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* z, double* t, bool z0_ready = false) {
   cudaStream_t s = h->stream;
@@ -509,22 +511,46 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
     std::swap(z, t);
     std::swap(dA, dB);
   }
-  prof_begin(h, kr, (double)nr * n);
-  launch_apply(op, APPLY_RES, z, b, nullptr, L.r, SmoothArgs<double>{}, nr, n, s);
-  prof_end(h);
   Level& C = h->lv[j + 1];
   const bool fuse = j + 1 < h->L - 1;  // the coarse level smooths (it is not the dense coarsest)
-  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
-  if (fuse)
-    launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s, C.dinv, C.coef, C.z, C.dA);
-  else
-    launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s);
-  prof_end(h);
+  // 2D stencil levels fuse residual + restriction and prolongation + first post-smoothing step.  The
+  // fused residual recomputes the tile halos (about an eighth more FP64 work), which pays only while
+  // the level is latency-bound: large levels with many right-hand sides keep the two launches.
+  const bool fused_transfers = op.S64 != nullptr && op.g.dim == 2;
+  const bool fused_res = fused_transfers && op.g.nnode * nr < kFusedResidualWork;
+  if (fused_res) {
+    prof_begin(h, kr, (double)nr * n);
+    launch_stencil_res_restrict_2d<double>(op.g, C.g, op.S64, op.fixed, z, b, n, C.fixed, C.b, C.g.n,
+                                           fuse ? C.dinv : nullptr, fuse ? C.coef : nullptr, fuse ? C.z : nullptr,
+                                           fuse ? C.dA : nullptr, nr, s);
+    prof_end(h);
+  } else {
+    prof_begin(h, kr, (double)nr * n);
+    launch_apply(op, APPLY_RES, z, b, nullptr, L.r, SmoothArgs<double>{}, nr, n, s);
+    prof_end(h);
+    prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
+    if (fuse)
+      launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s, C.dinv, C.coef, C.z, C.dA);
+    else
+      launch_restrict(L.g, C.g, C.fixed, L.r, C.b, nr, n, C.g.n, s);
+    prof_end(h);
+  }
   double* zc = vcycle64(h, j + 1, nr, C.b, C.z, C.t, fuse);
-  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
-  launch_prolong_add(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
-  prof_end(h);
-  for (int it = 0; it < h->desc.nu_post; ++it) {
+  int it0 = 0;
+  if (fused_transfers && h->desc.nu_post > 0) {
+    prof_begin(h, ks, (double)nr * n);
+    launch_stencil_jac_prolong_2d<double>(op.g, C.g, op.S64, op.fixed, z, zc, b, L.dinv, t,
+                                          SmoothArgs<double>{L.coef, nullptr, dB}, nr, n, C.g.n, s);
+    prof_end(h);
+    std::swap(z, t);
+    std::swap(dA, dB);
+    it0 = 1;
+  } else {
+    prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
+    launch_prolong_add(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
+    prof_end(h);
+  }
+  for (int it = it0; it < h->desc.nu_post; ++it) {
     prof_begin(h, ks, (double)nr * n);
     launch_apply(op, APPLY_JAC, z, b, L.dinv, t, SmoothArgs<double>{L.coef + 2 * it, it == 0 ? nullptr : dA, dB},
                  nr, n, s);
@@ -562,22 +588,43 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
     std::swap(z, t);
     std::swap(dA, dB);
   }
-  prof_begin(h, kr, (double)nr * n);
-  launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, SmoothArgs<float>{}, nr, n, s);
-  prof_end(h);
   Level& C = h->lv[j + 1];
   const bool fuse = j + 1 < h->L - 1;
-  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
-  if (fuse)
-    launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s, C.dinv32, C.coef32, C.z32, C.dA32);
-  else
-    launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s);
-  prof_end(h);
+  const bool fused_transfers = op.S32 != nullptr && op.g.dim == 2;
+  const bool fused_res = fused_transfers && op.g.nnode * nr < kFusedResidualWork;
+  if (fused_res) {
+    prof_begin(h, kr, (double)nr * n);
+    launch_stencil_res_restrict_2d<float>(op.g, C.g, op.S32, op.fixed, z, b, n, C.fixed, C.b32, C.g.n,
+                                          fuse ? C.dinv32 : nullptr, fuse ? C.coef32 : nullptr,
+                                          fuse ? C.z32 : nullptr, fuse ? C.dA32 : nullptr, nr, s);
+    prof_end(h);
+  } else {
+    prof_begin(h, kr, (double)nr * n);
+    launch_apply32(op, APPLY_RES, z, b, nullptr, L.r32, SmoothArgs<float>{}, nr, n, s);
+    prof_end(h);
+    prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
+    if (fuse)
+      launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s, C.dinv32, C.coef32, C.z32, C.dA32);
+    else
+      launch_restrict32(L.g, C.g, C.fixed, L.r32, C.b32, nr, n, C.g.n, s);
+    prof_end(h);
+  }
   float* zc = vcycle32(h, j + 1, nr, C.b32, C.z32, C.t32, fuse);
-  prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
-  launch_prolong_add32(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
-  prof_end(h);
-  for (int it = 0; it < h->desc.nu_post; ++it) {
+  int it0 = 0;
+  if (fused_transfers && h->desc.nu_post > 0) {
+    prof_begin(h, ks, (double)nr * n);
+    launch_stencil_jac_prolong_2d<float>(op.g, C.g, op.S32, op.fixed, z, zc, b, L.dinv32, t,
+                                         SmoothArgs<float>{L.coef32, nullptr, dB}, nr, n, C.g.n, s);
+    prof_end(h);
+    std::swap(z, t);
+    std::swap(dA, dB);
+    it0 = 1;
+  } else {
+    prof_begin(h, TOBK_KC_TRANSFER, (double)nr * n);
+    launch_prolong_add32(L.g, C.g, L.fixed, zc, z, nr, n, C.g.n, s);
+    prof_end(h);
+  }
+  for (int it = it0; it < h->desc.nu_post; ++it) {
     prof_begin(h, ks, (double)nr * n);
     launch_apply32(op, APPLY_JAC, z, b, L.dinv32, t,
                    SmoothArgs<float>{L.coef32 + 2 * it, it == 0 ? nullptr : dA, dB}, nr, n, s);
