@@ -1164,6 +1164,11 @@ static void cg_dir_impl(const Op& op, const double* z, const double* p_old, doub
 
 void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_old, double* p_new, double* q,
                          int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+  if (d.S64) {  // stencil level: 3^d d^2 multiply-adds per row instead of the element matrices
+    launch_stencil_cg_direction(d.g, d.S64, d.fixed, z, p_old, p_new, q, nr, stride, sc, partial,
+                                counters + 2 * kMaxRhs, cg_partial_stride(d.g), s);
+    return;
+  }
   if (d.g.dim == 2 && !d.stored) {
     launch_fine_q4_cg_direction(d.g, d.scale64, d.fixed, d.T0, z, p_old, p_new, q, nr, stride, sc, partial,
                                 counters + 2 * kMaxRhs, cg_partial_stride(d.g), s);

@@ -60,6 +60,11 @@ void launch_apply(const LevelOpDesc& op, int mode, const double* v, const double
 void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float* b, const float* dinv,
                     float* y, SmoothArgs<float> sm, int nr, int64_t stride, cudaStream_t s);
 
+// CG direction p = z + beta p_old, q = K p, p.q and alpha on a stencil level (stencil.cu); the
+// contract of launch_cg_direction.
+void launch_stencil_cg_direction(const Grid& g, const double* S, const uint8_t* fixed, const double* z,
+                                 const double* p_old, double* p_new, double* q, int nr, int64_t stride, double* sc,
+                                 double* partial, unsigned* counters, int64_t pstride, cudaStream_t s);
 // 2D stencil levels, transfers fused into the sweeps (stencil.cu):
 // y = v + d with v = z + P zc (the prolongated coarse correction added on the fly, not at fixed
 // DOFs) and d = coef[0] d_in + coef[1] dinv (b - K v) -- the prolongation and the first

@@ -397,6 +397,85 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32)
   }
 }
 
+// CG direction on a stencil level: p = z + beta p_old (zero at fixed DOFs), q = K p, and the per-RHS
+// reduction p.q -> sc[SC_PQ], alpha = (p.r) / (p.q) (the last block of each right-hand side);
+// the same contract as the element-matrix k_cg_direction.  p at the neighbours is formed on the fly
+// from z and p_old (one FMA each), straight-line as in k_apply_stencil.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_stencil_cg_direction(Grid g, const double* __restrict__ S,
+                                                              const uint8_t* __restrict__ fixed,
+                                                              const double* __restrict__ z,
+                                                              const double* __restrict__ p_old,
+                                                              double* __restrict__ p_new, double* __restrict__ q,
+                                                              int64_t stride, double* sc, double* partial,
+                                                              unsigned* counters, int64_t pstride) {
+  constexpr int NB = StencilDims<DIM>::NB;
+  __shared__ double smem[64];
+  const int rhs = blockIdx.y;
+  double* s = sc + (size_t)rhs * kScStride;
+  if (s[SC_ACTIVE] == 0.0) return;
+  const double beta = s[SC_BETA];
+  const int64_t off = (int64_t)rhs * stride;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  double v[1] = {0.0};
+  if (node_coords(g, node, i, j, k)) {
+    const int64_t nn = g.nnode;
+    double acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = 0.0;
+#pragma unroll
+    for (int nbr = 0; nbr < NB; ++nbr) {
+      const int dx = nbr % 3 - 1, dy = (nbr / 3) % 3 - 1, dz = DIM == 3 ? nbr / 9 - 1 : 0;
+      const bool in = i + dx >= 0 && i + dx < g.nn[0] && j + dy >= 0 && j + dy < g.nn[1] &&
+                      (DIM == 2 || (k + dz >= 0 && k + dz < g.nn[2]));
+      const int64_t nb = in ? node + dx + (int64_t)g.nn[0] * (dy + (int64_t)g.nn[1] * dz) : node;
+#pragma unroll
+      for (int cc = 0; cc < DIM; ++cc) {
+        const int64_t id = off + DIM * nb + cc;
+        const double pv = in ? __ldg(z + id) + beta * __ldg(p_old + id) : 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += __ldg(S + (int64_t)((nbr * DIM + c) * DIM + cc) * nn + node) * pv;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t idx = DIM * node + c;
+      const bool fx = fixed[idx];
+      const double pi = fx ? 0.0 : __ldg(z + off + idx) + beta * __ldg(p_old + off + idx);
+      const double qi = fx ? 0.0 : acc[c];
+      p_new[off + idx] = pi;
+      q[off + idx] = qi;
+      v[0] += pi * qi;
+    }
+  }
+  double tot[1];
+  if (grid_sum_last<1>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    s[SC_PQ] = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      s[SC_STATUS] = 1.0;  // breakdown: K not positive on the search direction
+      s[SC_ACTIVE] = 0.0;
+      s[SC_ALPHA] = 0.0;
+    } else {
+      s[SC_ALPHA] = s[SC_PR] / pq;
+    }
+  }
+}
+
+void launch_stencil_cg_direction(const Grid& g, const double* S, const uint8_t* fixed, const double* z,
+                                 const double* p_old, double* p_new, double* q, int nr, int64_t stride, double* sc,
+                                 double* partial, unsigned* counters, int64_t pstride, cudaStream_t s) {
+  const dim3 grid((unsigned)((g.nnode + 255) / 256), (unsigned)nr);
+  note_launch();
+  if (g.dim == 2)
+    k_stencil_cg_direction<2><<<grid, 256, 0, s>>>(g, S, fixed, z, p_old, p_new, q, stride, sc, partial, counters,
+                                                   pstride);
+  else
+    k_stencil_cg_direction<3><<<grid, 256, 0, s>>>(g, S, fixed, z, p_old, p_new, q, stride, sc, partial, counters,
+                                                   pstride);
+}
+
 static int sm_count_cached() {
   static int c = 0;
   if (c == 0) {
