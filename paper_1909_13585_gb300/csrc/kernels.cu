@@ -905,7 +905,7 @@ template <int DIM, class Op>
 __global__ void __launch_bounds__(kThreads) k_cg_init(const __grid_constant__ Op op, const double* __restrict__ b, double* __restrict__ x,
                                                        double* __restrict__ r, int use_x0, double rtol,
                                                        int64_t stride, double* sc, double* partial,
-                                                       unsigned* counters, int64_t pstride) {
+                                                       unsigned* counters, int64_t pstride, CGZ0 z0) {
   __shared__ double smem[64];
   const int rhs = blockIdx.y;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -923,6 +923,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(const __grid_constant__ Op
       const double bi = op.fixed[idx] ? 0.0 : b[off + idx];
       const double ri = op.fixed[idx] ? 0.0 : bi - acc[c];
       r[off + idx] = ri;
+      if (z0.z) {
+        const double zi = z0.coef[1] * z0.dinv[idx] * ri;
+        z0.z[off + idx] = zi;
+        if (z0.d) z0.d[off + idx] = zi;
+      }
       if (!use_x0) x[off + idx] = 0.0;
       v[0] += bi * bi;
       v[1] += ri * ri;
@@ -1042,7 +1047,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_direction(const __grid_constant
 __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ q,
                                                          int64_t stride, double* sc, double* partial,
-                                                         unsigned* counters, int64_t pstride) {
+                                                         unsigned* counters, int64_t pstride, CGZ0 z0) {
   __shared__ double smem[64];
   const int rhs = blockIdx.y;
   double* s = rhs_sc(sc, rhs);
@@ -1062,12 +1067,26 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* __res
     r[off + i + step] = rb;
     v[0] += ra * ra;
     v[0] += rb * rb;
+    if (z0.z) {
+      const double za = z0.coef[1] * z0.dinv[i] * ra, zb = z0.coef[1] * z0.dinv[i + step] * rb;
+      z0.z[off + i] = za;
+      z0.z[off + i + step] = zb;
+      if (z0.d) {
+        z0.d[off + i] = za;
+        z0.d[off + i + step] = zb;
+      }
+    }
   }
   if (i < n) {
     x[off + i] += alpha * p[off + i];
     const double ri = r[off + i] - alpha * q[off + i];
     r[off + i] = ri;
     v[0] += ri * ri;
+    if (z0.z) {
+      const double zi = z0.coef[1] * z0.dinv[i] * ri;
+      z0.z[off + i] = zi;
+      if (z0.d) z0.d[off + i] = zi;
+    }
   }
   double tot[1];
   if (grid_sum_last<1>(v, partial + rhs * pstride, counters + rhs, tot, smem) && threadIdx.x == 0) {
@@ -1126,24 +1145,28 @@ int64_t cg_partial_stride(const Grid& g) {
 
 template <int DIM, class Op>
 static void cg_init_impl(const Op& op, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
-                         int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+                         int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s, CGZ0 z0) {
   const int64_t ps = cg_partial_stride(op.g);
   ::tobk::note_launch(), k_cg_init<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, use_x0 ? 1 : 0, rtol,
-                                                                            stride, sc, partial, counters, ps);
+                                                                            stride, sc, partial, counters, ps, z0);
 }
 
 void launch_cg_init(const LevelOpDesc& d, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
-                    int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+                    int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s, CGZ0 z0) {
   if (d.g.dim == 2) {
     if (d.stored)
-      cg_init_impl<2>(make_stored<2, double>(d, d.Ke64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+      cg_init_impl<2>(make_stored<2, double>(d, d.Ke64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s,
+                      z0);
     else
-      cg_init_impl<2>(make_fine<2, double>(d, d.scale64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+      cg_init_impl<2>(make_fine<2, double>(d, d.scale64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters,
+                      s, z0);
   } else {
     if (d.stored)
-      cg_init_impl<3>(make_stored<3, double>(d, d.Ke64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+      cg_init_impl<3>(make_stored<3, double>(d, d.Ke64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s,
+                      z0);
     else
-      cg_init_impl<3>(make_fine<3, double>(d, d.scale64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters, s);
+      cg_init_impl<3>(make_fine<3, double>(d, d.scale64), b, x, r, use_x0, rtol, nr, stride, sc, partial, counters,
+                      s, z0);
   }
 }
 
@@ -1193,10 +1216,11 @@ void launch_cg_direction(const LevelOpDesc& d, const double* z, const double* p_
 }
 
 void launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, int nr, int64_t stride,
-                      double* sc, double* partial, unsigned* counters, cudaStream_t s) {
+                      double* sc, double* partial, unsigned* counters, cudaStream_t s, CGZ0 z0) {
   const int64_t ps = 4 * kVecBlocks;
   const unsigned g = vec_blocks(n, nr);
-  ::tobk::note_launch(), k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial, counters + 3 * kMaxRhs, ps);
+  ::tobk::note_launch(), k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial,
+                                                                      counters + 3 * kMaxRhs, ps, z0);
 }
 
 template <int DIM, class Op>

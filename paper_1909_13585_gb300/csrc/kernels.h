@@ -158,14 +158,24 @@ void launch_mask_copy(const double* src, const uint8_t* fixed, double* dst, int6
                       cudaStream_t s);
 
 // ---- multi-RHS PCG kernels (FP64).  sc: [nr][kScStride] scalars; partial/counters: scratch.
+// The first smoothing step of the next V-cycle from a zero guess, z = coef[1] dinv r (also into d),
+// taken by the kernel that writes the residual r (cg_init, cg_update) instead of a launch of its own;
+// z == nullptr: off.
+struct CGZ0 {
+  const double* dinv = nullptr;
+  const double* coef = nullptr;
+  double* z = nullptr;
+  double* d = nullptr;
+};
 void launch_cg_init(const LevelOpDesc& op, const double* b, double* x, double* r, bool use_x0, double rtol,
-                    int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
+                    int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s,
+                    CGZ0 z0 = CGZ0{});
 void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q, const double* p, bool flexible,
                     int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
 void launch_cg_direction(const LevelOpDesc& op, const double* z, const double* p_old, double* p_new, double* q,
                          int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);
 void launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, int nr, int64_t stride,
-                      double* sc, double* partial, unsigned* counters, cudaStream_t s);
+                      double* sc, double* partial, unsigned* counters, cudaStream_t s, CGZ0 z0 = CGZ0{});
 // true residual: r = b - K x; sc[SC_RELRES] = ||r|| / ||b||
 void launch_true_residual(const LevelOpDesc& op, const double* b, const double* x, double* r, int nr,
                           int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s);

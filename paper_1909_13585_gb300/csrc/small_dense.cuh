@@ -2,7 +2,9 @@
 // the coarse eigenproblem (eq. eigenvalueProblemCoarseScale; solved to a residual of 1e-8, Appendix A).
 //
 // The eigensolver keeps its basis K-orthonormal, so the projected problem is the standard
-// symmetric eigenproblem H y = theta y with H = V^T (-G) V (size m <= kRRMax).  A dense eigensolver
+// symmetric eigenproblem H y = theta y with H = V^T (-G) V (size m <= kRRMax; the eigensolver writes
+// every entry pair H[i][j], H[j][i] with one value, so H is exactly symmetric and the kernels below
+// read one triangle's order only).  A dense eigensolver
 // is a long chain of dependent steps confined to one SM, and GB300 executes FP64 at 1/64 of its
 // FP32 rate (2 FP64 FMA per clock per SM), so the O(m^3) work of the decomposition is done in FP32
 // and FP64 accuracy is recovered by a refinement made only of matrix products, spread over one
@@ -31,7 +33,7 @@ constexpr double kRRJacobiTol2 = 1e-9;
 constexpr int kRRRefineSteps = 2;
 static_assert(kRRRefineSteps >= 2, "the eigensolver's warm start reads the first refined X");
 
-// Stage 1.  All m eigenvectors of H [m][ld] (symmetric part) in FP32 by cyclic Jacobi, written in
+// Stage 1.  All m eigenvectors of H [m][ld] (symmetric) in FP32 by cyclic Jacobi, written in
 // FP64 to X [m][m] (column c = eigenvector of the c-th largest eigenvalue).  The matrix is padded
 // to P (a multiple of 8, P >= m; padding rows are never rotated).  One round applies P/2 disjoint
 // rotations J_k (round-robin pairing of the P indices) as C <- J C J^T, as independent 2 x 2
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(8 * P) k_rr_eig32(const double* H, int m, int 
   for (int q = t; q < P * P; q += NT) {
     const int i = q / P, j = q % P;
     float h = 0.f, v = (i == j) ? 1.f : 0.f;
-    if (i < m && j < m) h = inv * (float)(0.5 * (H[(size_t)i * ld + j] + H[(size_t)j * ld + i]));
+    if (i < m && j < m) h = inv * (float)H[(size_t)i * ld + j];
     if (i < mprev && j < mprev) v = (float)Xp[(size_t)i * mprev + j];
     Cc[i * LD + j] = h;
     V[j * LD + i] = v;
@@ -282,7 +284,7 @@ inline void launch_rr_eig32(const double* H, int m, int ld, const double* Xp, in
   }
 }
 
-// Stage 2a.  S = X^T Hs X and R = I - X^T X ([m][m] each), Hs = (H + H^T)/2; block j computes
+// Stage 2a.  S = X^T H X and R = I - X^T X ([m][m] each); block j computes
 // column j.
 __global__ void __launch_bounds__(64) k_rr_oa_products(const double* H, int ld, const double* X, int m, double* S,
                                                        double* R) {
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(64) k_rr_oa_products(const double* H, int ld, 
   __syncthreads();
   for (int i = t; i < m; i += nt) {
     double s = 0.0;
-    for (int k = 0; k < m; ++k) s += 0.5 * (H[(size_t)k * ld + i] + H[(size_t)i * ld + k]) * xj[k];
+    for (int k = 0; k < m; ++k) s += H[(size_t)k * ld + i] * xj[k];
     pj[i] = s;
   }
   __syncthreads();
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(64) k_rr_oa_update(const double* X, const doub
 
 // Stage 3 (one block).  The nvec refined columns Xw [m][ldw] with their lam are sorted by
 // descending lam; each run of neighbours closer than *delta (a cluster the refinement did not
-// split) is diagonalised by FP64 Jacobi rotations of its block B = Z^T Hs Z.  Outputs
+// split) is diagonalised by FP64 Jacobi rotations of its block B = Z^T H Z.  Outputs
 // theta[nvec] (descending) and Y [m][ldy].  Scratch in shared memory (dynamic): Z [nvec][m],
 // HZ [kRRClusterMax][m].
 constexpr int kRRClusterMax = 16;
@@ -397,11 +399,11 @@ __global__ void __launch_bounds__(256) k_rr_finish(const double* H, int ld, int 
     while (c1 < nvec && c1 - c0 < kRRClusterMax && fabs(l[c1 - 1] - l[c1]) <= dl) ++c1;
     const int c = c1 - c0;
     if (c > 1) {
-      // HZ = Hs Z_c, B = Z_c^T HZ
+      // HZ = H Z_c, B = Z_c^T HZ
       for (int q = t; q < c * m; q += nt) {
         const int a = q / m, i = q % m;
         double s = 0.0;
-        for (int k = 0; k < m; ++k) s += 0.5 * (H[(size_t)k * ld + i] + H[(size_t)i * ld + k]) * Z[(size_t)(c0 + a) * m + k];
+        for (int k = 0; k < m; ++k) s += H[(size_t)k * ld + i] * Z[(size_t)(c0 + a) * m + k];
         HZ[(size_t)a * m + i] = s;
       }
       __syncthreads();

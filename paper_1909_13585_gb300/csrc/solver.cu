@@ -636,8 +636,9 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
 }
 
 // z = M r at level s (FP64 result in one of z / zt)
-static double* precondition(tobk_handle* h, int s, int nr, const double* r, double* z, double* zt, int precision) {
-  if (precision == TOBK_FP64) return vcycle64(h, s, nr, r, z, zt);
+static double* precondition(tobk_handle* h, int s, int nr, const double* r, double* z, double* zt, int precision,
+                           bool z0_ready = false) {
+  if (precision == TOBK_FP64) return vcycle64(h, s, nr, r, z, zt, z0_ready);
   Level& L = h->lv[s];
   const int64_t n = L.g.n;
   launch_f64_to_f32(r, L.b32, (int64_t)nr * n, h->stream);
@@ -658,16 +659,31 @@ void apply_vcycle(tobk_handle* h, int j, int nr, const double* r, double* out) {
 // Two CG iterations (the two direction buffers swap roles twice, so the launch sequence and every
 // pointer in it are the same each time): V-cycle, dot products + beta, direction + q = K p + alpha,
 // x/r update + convergence test.  The iterate lives in the handle's buffer w.x.
+// The FP64 V-cycle's first smoothing step at the CG's level (z = coef dinv r into the V-cycle's z and
+// increment buffers), taken by cg_init and cg_update as they write r; none for the FP32 V-cycle or a
+// level solved directly.
+static CGZ0 cg_z0(tobk_handle* h, int s, int precision) {
+  CGZ0 z0;
+  if (precision != TOBK_FP64 || s >= h->L - 1) return z0;
+  Level& L = h->lv[s];
+  z0.dinv = L.dinv;
+  z0.coef = L.coef;
+  z0.z = h->cg.z;
+  z0.d = L.dA;
+  return z0;
+}
+
 static void enqueue_cg_pair(tobk_handle* h, int s, int nr, int precision) {
   cudaStream_t st = h->stream;
   const LevelOpDesc op = level_op(h, s);
   const int64_t n = op.g.n;
   CGWork& w = h->cg;
   const bool flexible = precision != TOBK_FP64;
+  const CGZ0 z0 = cg_z0(h, s, precision);
   for (int k = 0; k < 2; ++k) {
     double* p_old = k == 0 ? w.p0 : w.p1;
     double* p_new = k == 0 ? w.p1 : w.p0;
-    double* z = precondition(h, s, nr, w.r, w.z, w.zt, precision);
+    double* z = precondition(h, s, nr, w.r, w.z, w.zt, precision, z0.z != nullptr);
     prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
     launch_cg_dots(n, z, w.r, w.q, p_old, flexible, nr, n, w.sc, w.partial, w.counters, st);
     prof_end(h);
@@ -675,7 +691,7 @@ static void enqueue_cg_pair(tobk_handle* h, int s, int nr, int precision) {
     launch_cg_direction(op, z, p_old, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
     prof_end(h);
     prof_begin(h, TOBK_KC_VECTOR, (double)nr * n);
-    launch_cg_update(n, w.x, w.r, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st);
+    launch_cg_update(n, w.x, w.r, p_new, w.q, nr, n, w.sc, w.partial, w.counters, st, z0);
     prof_end(h);
   }
 }
@@ -736,7 +752,7 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
   if (fixed_iters) {
     // a fixed number of iterations as an approximate inverse (a preconditioner): no host
     // synchronisation, no exit check; breakdown shows in the caller's own residuals
-    launch_cg_init(op, B, w.x, w.r, use_x0, rtol, nr, n, w.sc, w.partial, w.counters, st);
+    launch_cg_init(op, B, w.x, w.r, use_x0, rtol, nr, n, w.sc, w.partial, w.counters, st, cg_z0(h, s, precision));
     cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
     cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
     while (2 * pairs < max_iter) {
@@ -756,7 +772,8 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
     return rc ? rc : check_cuda(h, "pcg_solve");
   }
   for (int attempt = 0; attempt < 4; ++attempt) {
-    launch_cg_init(op, B, w.x, w.r, use_x0 || attempt > 0, rtol, nr, n, w.sc, w.partial, w.counters, st);
+    launch_cg_init(op, B, w.x, w.r, use_x0 || attempt > 0, rtol, nr, n, w.sc, w.partial, w.counters, st,
+                   cg_z0(h, s, precision));
     cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
     cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
     while (2 * pairs < max_iter) {
