@@ -47,6 +47,7 @@ __global__ void k_random_block(double* X, int64_t n, int64_t stride, const uint8
 // i >= col0 both C[i][j] and C[col0 + j][i - col0] name the same pair; the one with i <= col0 + j is
 // used, so that H is exactly symmetric and every entry has a single writer.
 __global__ void k_scatter_sym(const double* C, int rows, int cols, int col0, double sign, double* H, int ld) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * cols) return;
   const int i = t / cols, j = t % cols;
@@ -59,6 +60,7 @@ __global__ void k_scatter_sym(const double* C, int rows, int cols, int col0, dou
 // Cholesky M = R^T R of a small SPD matrix (k <= 32) and Rinv = R^{-1} (upper triangular).
 // info[0] is set to 1 when a pivot is not positive (and left unchanged otherwise).
 __global__ void k_small_cholinv(const double* M, int k, double* Rinv, double* info) {
+  pdl_wait();
   __shared__ double L[32 * 32];
   __shared__ double Li[32 * 32];
   __shared__ int bad;
@@ -108,6 +110,7 @@ __global__ void k_small_cholinv(const double* M, int k, double* Rinv, double* in
 // Column-wise dot products out[i] = sum_k A_i[k] B_i[k] (two stage, deterministic).
 constexpr int kColChunk = 2048;
 __global__ void k_coldots_partial(const double* A, const double* B, int64_t n, int64_t stride, double* partial) {
+  pdl_wait();
   __shared__ double red[32];
   const int col = blockIdx.y;
   const int64_t k0 = (int64_t)blockIdx.x * kColChunk;
@@ -124,6 +127,7 @@ __global__ void k_coldots_partial(const double* A, const double* B, int64_t n, i
   }
 }
 __global__ void k_coldots_final(const double* partial, int chunks, int ncols, double* out) {
+  pdl_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   double s = 0.0;
@@ -134,14 +138,15 @@ __global__ void k_coldots_final(const double* partial, int chunks, int ncols, do
 void launch_coldots(const double* A, const double* B, int ncols, int64_t n, int64_t stride, double* out,
                     double* partial, cudaStream_t s) {
   const int chunks = (int)((n + kColChunk - 1) / kColChunk);
-  ::tobk::note_launch(), k_coldots_partial<<<dim3(chunks, ncols), 256, 0, s>>>(A, B, n, stride, partial);
-  ::tobk::note_launch(), k_coldots_final<<<(ncols + 63) / 64, 64, 0, s>>>(partial, chunks, ncols, out);
+  launch_pdl(k_coldots_partial, dim3(dim3(chunks, ncols)), dim3(256), 0, s, A, B, n, stride, partial);
+  launch_pdl(k_coldots_final, dim3((ncols + 63) / 64), dim3(64), 0, s, partial, chunks, ncols, out);
 }
 
 // Squared norms of the pencil residuals and of K x for the Ritz pairs i < ncols (two stages,
 // deterministic): resn[i] = ||KX_i + (1/theta_i) GX_i||^2, kxn[i] = ||KX_i||^2.
 __global__ void k_resnorm_partial(const double* KX, const double* GX, const double* theta, int64_t n, int64_t stride,
                                   double* partial) {
+  pdl_wait();
   __shared__ double red[2][32];
   const int col = blockIdx.y;
   const double th = theta[col];
@@ -174,6 +179,7 @@ __global__ void k_resnorm_partial(const double* KX, const double* GX, const doub
   }
 }
 __global__ void k_resnorm_final(const double* partial, int chunks, int ncols, double* resn, double* kxn) {
+  pdl_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   double a = 0.0, b = 0.0;
@@ -188,14 +194,15 @@ __global__ void k_resnorm_final(const double* partial, int chunks, int ncols, do
 static void launch_resnorms(const double* KX, const double* GX, const double* theta, int ncols, int64_t n,
                             int64_t stride, double* resn, double* kxn, double* partial, cudaStream_t s) {
   const int chunks = (int)((n + kColChunk - 1) / kColChunk);
-  ::tobk::note_launch(), k_resnorm_partial<<<dim3(chunks, ncols), 256, 0, s>>>(KX, GX, theta, n, stride, partial);
-  ::tobk::note_launch(), k_resnorm_final<<<(ncols + 63) / 64, 64, 0, s>>>(partial, chunks, ncols, resn, kxn);
+  launch_pdl(k_resnorm_partial, dim3(dim3(chunks, ncols)), dim3(256), 0, s, KX, GX, theta, n, stride, partial);
+  launch_pdl(k_resnorm_final, dim3((ncols + 63) / 64), dim3(64), 0, s, partial, chunks, ncols, resn, kxn);
 }
 
 // W_c = -GX_{s} - theta_s KX_{s}, s = sel[c]: the residual of the pencil -G x = mu K x at the Ritz
 // pair (theta_s, x_s)
 __global__ void k_gather_residual(const double* GX, const double* KX, const double* theta, const int* sel,
                                   double* W, int64_t n, int64_t stride) {
+  pdl_wait();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int c = blockIdx.y;
@@ -302,7 +309,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       eig_gram(h, src, nadd, KW, nadd, n, sd, M);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)nadd);
-      ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, nadd, Rinv, sinfo);
+      launch_pdl(k_small_cholinv, dim3(1), dim3(256), 0, st, M, nadd, Rinv, sinfo);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
       launch_combine(src, nadd, Rinv, nadd, nadd, 1.0, 0.0, dst, n, sd, st);
@@ -313,7 +320,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     const int mn = m + nadd;
     prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)mn * n);
     eig_gram(h, h->V, mn, GVn, nadd, n, sd, Cs);
-    ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)mn * nadd), 256, 0, st>>>(Cs, mn, nadd, m, -1.0, h->Hs, mmax);
+    launch_pdl(k_scatter_sym, dim3(nblk((int64_t)mn * nadd)), dim3(256), 0, st, Cs, mn, nadd, m, -1.0, h->Hs, mmax);
     prof_end(h);
     m = mn;
     // ---- Rayleigh-Ritz (the basis is K-orthonormal, so V^T K V = I): the leading eigenpairs of
@@ -322,18 +329,18 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     const int rr0 = pm.mark();
     prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)m);
     // warm start from the previous refined eigenvectors while the basis only grew since then
-    ::tobk::note_launch(), launch_rr_eig32(h->Hs, m, mmax, rrX1, rr_prev, rrX0, sinfo + 2, st);
+    launch_rr_eig32(h->Hs, m, mmax, rrX1, rr_prev, rrX0, sinfo + 2, st);
     // refinement: X0 -> X1 -> X0 ... (the last step writes the nvec wanted columns to Xw); the error
     // bound of the FP32 result decides the clusters of every step and of the finish
     for (int step = 0; step < kRRRefineSteps; ++step) {
       const bool last = step == kRRRefineSteps - 1;
       double* xin = (step & 1) ? rrX1 : rrX0;
       double* xout = last ? rrXw : ((step & 1) ? rrX0 : rrX1);
-      ::tobk::note_launch(), k_rr_oa_products<<<m, 64, 0, st>>>(h->Hs, mmax, xin, m, rrS, rrR);
-      ::tobk::note_launch(), k_rr_oa_update<<<last ? nvec : m, 64, 0, st>>>(xin, rrS, rrR, m, xout, last ? mmax : m,
+      launch_pdl(k_rr_oa_products, dim3(m), dim3(64), 0, st, h->Hs, mmax, xin, m, rrS, rrR);
+      launch_pdl(k_rr_oa_update, dim3(last ? nvec : m), dim3(64), 0, st, xin, rrS, rrR, m, xout, last ? mmax : m,
                                                                            last ? rrLam : nullptr, rrDelta, step == 0);
     }
-    ::tobk::note_launch(), k_rr_finish<<<1, 256, rr_finish_smem_bytes(m, nvec), st>>>(
+    launch_pdl(k_rr_finish, dim3(1), dim3(256), rr_finish_smem_bytes(m, nvec), st, 
         h->Hs, mmax, m, nvec, rrXw, mmax, rrLam, rrDelta, theta, h->Ys, mmax);
     prof_end(h);
     rr_marks.emplace_back(rr0, pm.mark());
@@ -383,7 +390,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     // selected Ritz pairs, M = one multigrid V-cycle for K on this level and below
     nadd = (int)sel.size();
     cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice, st);
-    ::tobk::note_launch(), k_gather_residual<<<dim3(nblk(n), nadd), 256, 0, st>>>(GX, KX, theta, dsel, Tb, n, sd);
+    launch_pdl(k_gather_residual, dim3(dim3(nblk(n), nadd)), dim3(256), 0, st, GX, KX, theta, dsel, Tb, n, sd);
     const int pre0 = pm.mark();
     if (h->desc.eig_inner_iters <= 0) {
       apply_vcycle(h, j, nadd, Tb, W);
@@ -412,7 +419,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
         cudaMemcpyAsync(bsp, tmp, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st);
       }
       eig_gram(h, h->V, keep, h->GV, keep, n, sd, Cs);
-      ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)keep * keep), 256, 0, st>>>(Cs, keep, keep, 0, -1.0, h->Hs,
+      launch_pdl(k_scatter_sym, dim3(nblk((int64_t)keep * keep)), dim3(256), 0, st, Cs, keep, keep, 0, -1.0, h->Hs,
                                                                                        mmax);
       m = keep;
       rr_prev = 0;  // the basis was replaced by Ritz vectors: its projected matrix is diagonal
@@ -484,23 +491,23 @@ int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host) {
   for (int pass = 0; pass < 2; ++pass) {
     apply_K_level(h, j, Psi, KW, q, n);
     eig_gram(h, Psi, q, KW, q, n, n, M);
-    ::tobk::note_launch(), k_small_cholinv<<<1, 256, 0, st>>>(M, q, Rinv, sinfo);
+    launch_pdl(k_small_cholinv, dim3(1), dim3(256), 0, st, M, q, Rinv, sinfo);
     launch_combine(Psi, q, Rinv, q, q, 1.0, 0.0, Tb, n, n, st);
     cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);
   }
   apply_G_level(h, j, Psi, GW, q, n);
   eig_gram(h, Psi, q, GW, q, n, n, Cs);
-  ::tobk::note_launch(), k_scatter_sym<<<nblk((int64_t)q * q), 256, 0, st>>>(Cs, q, q, 0, -1.0, h->Hs, mmax);
-  ::tobk::note_launch(), launch_rr_eig32(h->Hs, q, mmax, nullptr, 0, rrX0, sinfo + 2, st);
+  launch_pdl(k_scatter_sym, dim3(nblk((int64_t)q * q)), dim3(256), 0, st, Cs, q, q, 0, -1.0, h->Hs, mmax);
+  launch_rr_eig32(h->Hs, q, mmax, nullptr, 0, rrX0, sinfo + 2, st);
   for (int step = 0; step < kRRRefineSteps; ++step) {
     const bool last = step == kRRRefineSteps - 1;
     double* xin = (step & 1) ? rrX1 : rrX0;
     double* xout = last ? rrXw : ((step & 1) ? rrX0 : rrX1);
-    ::tobk::note_launch(), k_rr_oa_products<<<q, 64, 0, st>>>(h->Hs, mmax, xin, q, rrS, rrR);
-    ::tobk::note_launch(), k_rr_oa_update<<<q, 64, 0, st>>>(xin, rrS, rrR, q, xout, last ? mmax : q,
+    launch_pdl(k_rr_oa_products, dim3(q), dim3(64), 0, st, h->Hs, mmax, xin, q, rrS, rrR);
+    launch_pdl(k_rr_oa_update, dim3(q), dim3(64), 0, st, xin, rrS, rrR, q, xout, last ? mmax : q,
                                                             last ? rrLam : nullptr, rrDelta, step == 0);
   }
-  ::tobk::note_launch(), k_rr_finish<<<1, 256, rr_finish_smem_bytes(q, q), st>>>(h->Hs, mmax, q, q, rrXw, mmax, rrLam,
+  launch_pdl(k_rr_finish, dim3(1), dim3(256), rr_finish_smem_bytes(q, q), st, h->Hs, mmax, q, q, rrXw, mmax, rrLam,
                                                                                  rrDelta, theta, h->Ys, mmax);
   launch_combine(Psi, q, h->Ys, mmax, q, 1.0, 0.0, Tb, n, n, st);
   cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);

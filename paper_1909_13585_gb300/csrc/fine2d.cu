@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4(Grid g, const T* __restr
                                                     Q4Consts<T> cst, const T* __restrict__ v, const T* __restrict__ b,
                                                     const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
                                                     int64_t stride, const double* __restrict__ act) {
+  pdl_wait();
   __shared__ T su[NY][NX], sv[NY][NX];
   __shared__ T fe[EY][EX][8];
   const int rhs = blockIdx.z;
@@ -109,13 +110,12 @@ void launch_fine_q4(const Grid& g, const T* Ek, const uint8_t* fixed, const doub
   const Q4Consts<T> cst = q4_consts<T>(Ke0);
   dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)nr);
   const double* act = active_rhs();
-  note_launch();
   if (mode == APPLY_KV)
-    k_fine_q4<T, APPLY_KV><<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+    launch_pdl(k_fine_q4<T, APPLY_KV>, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
   else if (mode == APPLY_RES)
-    k_fine_q4<T, APPLY_RES><<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+    launch_pdl(k_fine_q4<T, APPLY_RES>, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
   else
-    k_fine_q4<T, APPLY_JAC><<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+    launch_pdl(k_fine_q4<T, APPLY_JAC>, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
 }
 
 template void launch_fine_q4<double>(const Grid&, const double*, const uint8_t*, const double*, int, const double*,
@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, con
                                                                  double* __restrict__ p_new, double* __restrict__ q,
                                                                  int64_t stride, double* sc, double* partial,
                                                                  unsigned* counters, int64_t pstride) {
+  pdl_wait();
   __shared__ double su[NY][NX], sv[NY][NX];
   __shared__ double fe[EY][EX][8];
   __shared__ double red[64];
@@ -198,8 +199,7 @@ void launch_fine_q4_cg_direction(const Grid& g, const double* Ek, const uint8_t*
                                  cudaStream_t s) {
   const Q4Consts<double> cst = q4_consts<double>(Ke0);
   dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)nr);
-  note_launch();
-  k_fine_q4_cg_direction<<<grid, kThreadsQ4, 0, s>>>(g, Ek, fixed, cst, z, p_old, p_new, q, stride, sc, partial, counters,
+  launch_pdl(k_fine_q4_cg_direction, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, z, p_old, p_new, q, stride, sc, partial, counters,
                                                       pstride);
 }
 

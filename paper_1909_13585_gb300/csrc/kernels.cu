@@ -55,6 +55,7 @@ template <int DIM, class Op, typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_apply(const __grid_constant__ Op op, const T* __restrict__ v, const T* __restrict__ b,
                                                      const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
                                                      int64_t stride, const double* __restrict__ act) {
+  pdl_wait();
   if (rhs_done(act)) return;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
@@ -92,11 +93,11 @@ void apply_dispatch(const Op& op, int mode, const T* v, const T* b, const T* din
                     int64_t stride, cudaStream_t s) {
   dim3 grid(blocks_for(op.g.nnode), nr);
   if (mode == APPLY_KV)
-    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_KV><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, sm, stride, active_rhs());
+    launch_pdl(k_apply<DIM, Op, T, APPLY_KV>, dim3(grid), dim3(kThreads), 0, s, op, v, b, dinv, y, sm, stride, active_rhs());
   else if (mode == APPLY_RES)
-    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_RES><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, sm, stride, active_rhs());
+    launch_pdl(k_apply<DIM, Op, T, APPLY_RES>, dim3(grid), dim3(kThreads), 0, s, op, v, b, dinv, y, sm, stride, active_rhs());
   else
-    ::tobk::note_launch(), k_apply<DIM, Op, T, APPLY_JAC><<<grid, kThreads, 0, s>>>(op, v, b, dinv, y, sm, stride, active_rhs());
+    launch_pdl(k_apply<DIM, Op, T, APPLY_JAC>, dim3(grid), dim3(kThreads), 0, s, op, v, b, dinv, y, sm, stride, active_rhs());
 }
 
 template <int DIM>
@@ -169,6 +170,7 @@ void launch_apply32(const LevelOpDesc& op, int mode, const float* v, const float
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_apply_kron(ScalarKronOp<DIM, double> op, const double* __restrict__ v,
                                                          double* __restrict__ y, int64_t stride) {
+  pdl_wait();
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
   if (!node_coords(op.g, node, i, j, k)) return;
@@ -189,10 +191,10 @@ void launch_apply_kron(const Grid& g, const uint8_t* fixed, const double* Gs, co
   dim3 grid(blocks_for(g.nnode), nr);
   if (g.dim == 2) {
     ScalarKronOp<2, double> op{g, Gs, fixed};
-    ::tobk::note_launch(), k_apply_kron<2><<<grid, kThreads, 0, s>>>(op, v, y, stride);
+    launch_pdl(k_apply_kron<2>, dim3(grid), dim3(kThreads), 0, s, op, v, y, stride);
   } else {
     ScalarKronOp<3, double> op{g, Gs, fixed};
-    ::tobk::note_launch(), k_apply_kron<3><<<grid, kThreads, 0, s>>>(op, v, y, stride);
+    launch_pdl(k_apply_kron<3>, dim3(grid), dim3(kThreads), 0, s, op, v, y, stride);
   }
 }
 
@@ -249,6 +251,7 @@ void launch_diag(const LevelOpDesc& d, double* dinv, float* dinv32, cudaStream_t
 template <typename T>
 __global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ z, SmoothArgs<T> sm,
                           int64_t n, int64_t stride, const double* __restrict__ act) {
+  pdl_wait();
   if (rhs_done(act)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -260,11 +263,11 @@ __global__ void k_jacobi0(const T* __restrict__ b, const T* __restrict__ dinv, T
 
 void launch_jacobi0(const double* b, const double* dinv, double* z, SmoothArgs<double> sm, int64_t n, int nr,
                     int64_t stride, cudaStream_t s) {
-  ::tobk::note_launch(), k_jacobi0<double><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, sm, n, stride, active_rhs());
+  launch_pdl(k_jacobi0<double>, dim3(dim3(blocks_for(n), nr)), dim3(kThreads), 0, s, b, dinv, z, sm, n, stride, active_rhs());
 }
 void launch_jacobi0_32(const float* b, const float* dinv, float* z, SmoothArgs<float> sm, int64_t n, int nr, int64_t stride,
                        cudaStream_t s) {
-  ::tobk::note_launch(), k_jacobi0<float><<<dim3(blocks_for(n), nr), kThreads, 0, s>>>(b, dinv, z, sm, n, stride, active_rhs());
+  launch_pdl(k_jacobi0<float>, dim3(dim3(blocks_for(n), nr)), dim3(kThreads), 0, s, b, dinv, z, sm, n, stride, active_rhs());
 }
 
 // ---- transfers ----------------------------------------------------------------------------------
@@ -275,6 +278,7 @@ __global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c
                            T* __restrict__ bc, int64_t sf, int64_t sc, const double* __restrict__ act,
                            const T* __restrict__ dinv_c, const T* __restrict__ coef_c, T* __restrict__ zc,
                            T* __restrict__ dc) {
+  pdl_wait();
   if (rhs_done(act)) return;
   const int64_t cn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int I, J, K;
@@ -321,6 +325,7 @@ __global__ void k_restrict(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_c
 template <int DIM, typename T>
 __global__ void k_prolong_add(Grid gf, Grid gc, const uint8_t* __restrict__ fixed_f, const T* __restrict__ zc,
                               T* __restrict__ zf, int64_t sf, int64_t sc, const double* __restrict__ act) {
+  pdl_wait();
   if (rhs_done(act)) return;
   const int64_t fn = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
@@ -365,10 +370,10 @@ static void restrict_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_c
                           int64_t sf, int64_t sc, cudaStream_t s, const T* dinv_c, const T* coef_c, T* zc, T* dc) {
   dim3 grid(blocks_for(gc.nnode), nr);
   if (gf.dim == 2)
-    ::tobk::note_launch(), k_restrict<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs(),
+    launch_pdl(k_restrict<2, T>, dim3(grid), dim3(kThreads), 0, s, gf, gc, fixed_c, rf, bc, sf, sc, active_rhs(),
                                                                       dinv_c, coef_c, zc, dc);
   else
-    ::tobk::note_launch(), k_restrict<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_c, rf, bc, sf, sc, active_rhs(),
+    launch_pdl(k_restrict<3, T>, dim3(grid), dim3(kThreads), 0, s, gf, gc, fixed_c, rf, bc, sf, sc, active_rhs(),
                                                                       dinv_c, coef_c, zc, dc);
 }
 template <typename T>
@@ -376,9 +381,9 @@ static void prolong_impl(const Grid& gf, const Grid& gc, const uint8_t* fixed_f,
                          int64_t sf, int64_t sc, cudaStream_t s) {
   dim3 grid(blocks_for(gf.nnode), nr);
   if (gf.dim == 2)
-    ::tobk::note_launch(), k_prolong_add<2, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc, active_rhs());
+    launch_pdl(k_prolong_add<2, T>, dim3(grid), dim3(kThreads), 0, s, gf, gc, fixed_f, zc, zf, sf, sc, active_rhs());
   else
-    ::tobk::note_launch(), k_prolong_add<3, T><<<grid, kThreads, 0, s>>>(gf, gc, fixed_f, zc, zf, sf, sc, active_rhs());
+    launch_pdl(k_prolong_add<3, T>, dim3(grid), dim3(kThreads), 0, s, gf, gc, fixed_f, zc, zf, sf, sc, active_rhs());
 }
 
 void launch_restrict(const Grid& gf, const Grid& gc, const uint8_t* fixed_c, const double* rf, double* bc, int nr,
@@ -404,6 +409,7 @@ void launch_prolong_add32(const Grid& gf, const Grid& gc, const uint8_t* fixed_f
 template <typename T>
 __global__ void k_dense_gemv(const double* __restrict__ A, const T* __restrict__ b, T* __restrict__ z, int64_t n,
                              int64_t stride, const double* __restrict__ act) {
+  pdl_wait();
   if (rhs_done(act)) return;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -420,11 +426,11 @@ __global__ void k_dense_gemv(const double* __restrict__ A, const T* __restrict__
 
 void launch_dense_gemv(const double* Ainv, const double* b, double* z, int64_t n, int nr, int64_t stride,
                        cudaStream_t s) {
-  ::tobk::note_launch(), k_dense_gemv<double><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride, active_rhs());
+  launch_pdl(k_dense_gemv<double>, dim3(dim3(blocks_for(n * 32), nr)), dim3(kThreads), 0, s, Ainv, b, z, n, stride, active_rhs());
 }
 void launch_dense_gemv32(const double* Ainv, const float* b, float* z, int64_t n, int nr, int64_t stride,
                          cudaStream_t s) {
-  ::tobk::note_launch(), k_dense_gemv<float><<<dim3(blocks_for(n * 32), nr), kThreads, 0, s>>>(Ainv, b, z, n, stride, active_rhs());
+  launch_pdl(k_dense_gemv<float>, dim3(dim3(blocks_for(n * 32), nr)), dim3(kThreads), 0, s, Ainv, b, z, n, stride, active_rhs());
 }
 
 template <int DIM, class Op>
@@ -860,18 +866,20 @@ void launch_simp(const double* x, int64_t m, double penal, double E0, double Emi
 }
 
 __global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
 __global__ void k_f32_to_f64(const float* a, double* b, int64_t n) {
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
 }
 void launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
-  ::tobk::note_launch(), k_f64_to_f32<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
+  launch_pdl(k_f64_to_f32, dim3(blocks_for(n)), dim3(kThreads), 0, s, a, b, n);
 }
 void launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
-  ::tobk::note_launch(), k_f32_to_f64<<<blocks_for(n), kThreads, 0, s>>>(a, b, n);
+  launch_pdl(k_f32_to_f64, dim3(blocks_for(n)), dim3(kThreads), 0, s, a, b, n);
 }
 
 __global__ void k_mask_copy(const double* __restrict__ src, const uint8_t* __restrict__ fixed, double* __restrict__ dst,
@@ -906,6 +914,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(const __grid_constant__ Op
                                                        double* __restrict__ r, int use_x0, double rtol,
                                                        int64_t stride, double* sc, double* partial,
                                                        unsigned* counters, int64_t pstride, CGZ0 z0) {
+  pdl_wait();
   __shared__ double smem[64];
   const int rhs = blockIdx.y;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -957,6 +966,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_dots(int64_t n, const double* _
                                                        const double* __restrict__ p, int flexible, int64_t stride,
                                                        double* sc, double* partial, unsigned* counters,
                                                        int64_t pstride) {
+  pdl_wait();
   __shared__ double smem[96];
   const int rhs = blockIdx.y;
   double* s = rhs_sc(sc, rhs);
@@ -1005,6 +1015,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_direction(const __grid_constant
                                                             double* __restrict__ p_new, double* __restrict__ q,
                                                             int64_t stride, double* sc, double* partial,
                                                             unsigned* counters, int64_t pstride) {
+  pdl_wait();
   __shared__ double smem[64];
   const int rhs = blockIdx.y;
   double* s = rhs_sc(sc, rhs);
@@ -1048,6 +1059,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(int64_t n, double* __res
                                                          const double* __restrict__ p, const double* __restrict__ q,
                                                          int64_t stride, double* sc, double* partial,
                                                          unsigned* counters, int64_t pstride, CGZ0 z0) {
+  pdl_wait();
   __shared__ double smem[64];
   const int rhs = blockIdx.y;
   double* s = rhs_sc(sc, rhs);
@@ -1147,7 +1159,7 @@ template <int DIM, class Op>
 static void cg_init_impl(const Op& op, const double* b, double* x, double* r, bool use_x0, double rtol, int nr,
                          int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s, CGZ0 z0) {
   const int64_t ps = cg_partial_stride(op.g);
-  ::tobk::note_launch(), k_cg_init<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, b, x, r, use_x0 ? 1 : 0, rtol,
+  launch_pdl(k_cg_init<DIM, Op>, dim3(dim3(blocks_for(op.g.nnode), nr)), dim3(kThreads), 0, s, op, b, x, r, use_x0 ? 1 : 0, rtol,
                                                                             stride, sc, partial, counters, ps, z0);
 }
 
@@ -1174,14 +1186,14 @@ void launch_cg_dots(int64_t n, const double* z, const double* r, const double* q
                     int nr, int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = 4 * kVecBlocks;
   const unsigned g = vec_blocks(n, nr);
-  ::tobk::note_launch(), k_cg_dots<<<dim3(g, nr), kThreads, 0, s>>>(n, z, r, q, p, flexible ? 1 : 0, stride, sc, partial, counters + kMaxRhs, ps);
+  launch_pdl(k_cg_dots, dim3(dim3(g, nr)), dim3(kThreads), 0, s, n, z, r, q, p, flexible ? 1 : 0, stride, sc, partial, counters + kMaxRhs, ps);
 }
 
 template <int DIM, class Op>
 static void cg_dir_impl(const Op& op, const double* z, const double* p_old, double* p_new, double* q, int nr,
                         int64_t stride, double* sc, double* partial, unsigned* counters, cudaStream_t s) {
   const int64_t ps = cg_partial_stride(op.g);
-  ::tobk::note_launch(), k_cg_direction<DIM, Op><<<dim3(blocks_for(op.g.nnode), nr), kThreads, 0, s>>>(op, z, p_old, p_new, q, stride, sc,
+  launch_pdl(k_cg_direction<DIM, Op>, dim3(dim3(blocks_for(op.g.nnode), nr)), dim3(kThreads), 0, s, op, z, p_old, p_new, q, stride, sc,
                                                                                  partial, counters + 2 * kMaxRhs, ps);
 }
 
@@ -1219,7 +1231,7 @@ void launch_cg_update(int64_t n, double* x, double* r, const double* p, const do
                       double* sc, double* partial, unsigned* counters, cudaStream_t s, CGZ0 z0) {
   const int64_t ps = 4 * kVecBlocks;
   const unsigned g = vec_blocks(n, nr);
-  ::tobk::note_launch(), k_cg_update<<<dim3(g, nr), kThreads, 0, s>>>(n, x, r, p, q, stride, sc, partial,
+  launch_pdl(k_cg_update, dim3(dim3(g, nr)), dim3(kThreads), 0, s, n, x, r, p, q, stride, sc, partial,
                                                                       counters + 3 * kMaxRhs, ps, z0);
 }
 
@@ -1279,6 +1291,7 @@ static int gram_chunk_rows(int na, int nb, int64_t n) {
 // partial[chunk][i][j] = sum_{k in chunk} A[i][k] B[j][k]; shared rows of odd stride len + 1.
 __global__ void k_gram_partial(const double* __restrict__ A, int na, const double* __restrict__ B, int nb, int64_t n,
                                int64_t stride, int chunk, double* __restrict__ partial) {
+  pdl_wait();
   extern __shared__ double sm[];
   const int ldc = chunk + 1;
   double* sA = sm;              // [na][ldc]
@@ -1309,6 +1322,7 @@ __global__ void k_gram_partial(const double* __restrict__ A, int na, const doubl
 // 8th chunk (coalesced over the outputs) and the 8 partial sums are added in a fixed order.
 __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ partial, int nchunks, int nout,
                                                     double* __restrict__ C) {
+  pdl_wait();
   __shared__ double red[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int o = blockIdx.x * 32 + lane;
@@ -1335,7 +1349,7 @@ int gram_partial_blocks(int64_t n) {
 }
 
 void launch_gram_final(const double* partial, int nchunks, int nout, double* C, cudaStream_t s) {
-  ::tobk::note_launch(), k_gram_final<<<(nout + 31) / 32, 256, 0, s>>>(partial, nchunks, nout, C);
+  launch_pdl(k_gram_final, dim3((nout + 31) / 32), dim3(256), 0, s, partial, nchunks, nout, C);
 }
 
 void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, int64_t stride, double* C,
@@ -1348,8 +1362,8 @@ void launch_gram(const double* A, int na, const double* B, int nb, int64_t n, in
     cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
     configured = true;
   }
-  ::tobk::note_launch(), k_gram_partial<<<chunks, kThreads, smem, s>>>(A, na, B, nb, n, stride, chunk, partial);
-  ::tobk::note_launch(), k_gram_final<<<(na * nb + 31) / 32, 256, 0, s>>>(partial, chunks, na * nb, C);
+  launch_pdl(k_gram_partial, dim3(chunks), dim3(kThreads), smem, s, A, na, B, nb, n, stride, chunk, partial);
+  launch_pdl(k_gram_final, dim3((na * nb + 31) / 32), dim3(256), 0, s, partial, chunks, na * nb, C);
 }
 
 // Y[j] = beta * Y[j] + alpha * sum_i X[i] C[i][j].  A work item is one row index k and kCombineJ
@@ -1364,6 +1378,7 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(const double* __res
                                                              const double* __restrict__ C, int ldc, int ny,
                                                              double alpha, double beta, double* __restrict__ Y,
                                                              int64_t n, int64_t stride, int64_t per_block) {
+  pdl_wait();
   const int groups = (ny + kCombineJ - 1) / kCombineJ;
   const int64_t items = n * groups;
   const int64_t end = min(items, ((int64_t)blockIdx.x + 1) * per_block);
@@ -1400,6 +1415,7 @@ struct CombineSet {
 __global__ void __launch_bounds__(kCombineThreads) k_combine_set(CombineSet cs, int nsrc, int nx,
                                                                  const double* __restrict__ C, int ldc, int ny,
                                                                  int64_t n, int64_t stride, int64_t per_block) {
+  pdl_wait();
   const int groups = (ny + kCombineJ - 1) / kCombineJ;
   const int64_t per_src = n * groups;
   const int64_t items = per_src * nsrc;
@@ -1434,7 +1450,7 @@ void launch_combine3(const double* X0, const double* X1, const double* X2, int n
   const int64_t items = 3 * n * ((ny + kCombineJ - 1) / kCombineJ);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 31) / 32, 4 * (int64_t)device_sm_count()));
   const int64_t per_block = (items + grid - 1) / grid;
-  ::tobk::note_launch(), k_combine_set<<<(unsigned)grid, kCombineThreads, 0, s>>>(cs, 3, nx, C, ldc, ny, n, stride,
+  launch_pdl(k_combine_set, dim3((unsigned)grid), dim3(kCombineThreads), 0, s, cs, 3, nx, C, ldc, ny, n, stride,
                                                                                  per_block);
 }
 
@@ -1443,7 +1459,7 @@ void launch_combine(const double* X, int nx, const double* C, int ldc, int ny, d
   const int64_t items = n * ((ny + kCombineJ - 1) / kCombineJ);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((items + 31) / 32, 4 * (int64_t)device_sm_count()));
   const int64_t per_block = (items + grid - 1) / grid;
-  ::tobk::note_launch(), k_combine<<<(unsigned)grid, kCombineThreads, 0, s>>>(X, nx, C, ldc, ny, alpha, beta, Y, n,
+  launch_pdl(k_combine, dim3((unsigned)grid), dim3(kCombineThreads), 0, s, X, nx, C, ldc, ny, alpha, beta, Y, n,
                                                                              stride, per_block);
 }
 

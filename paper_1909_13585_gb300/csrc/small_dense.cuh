@@ -109,6 +109,7 @@ __device__ __forceinline__ void rotate_vcols(float* V, int pa, int qa, float ca,
 template <int P>
 __global__ void __launch_bounds__(8 * P) k_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev,
                                                     double* X, double* info, double tol2) {
+  pdl_wait();
   static_assert(P % 8 == 0 && P <= kRRMax, "padded size");
   constexpr int NP = P / 2;    // rotations per round (column slots, one per lane)
   constexpr int NW = NP / 2;   // warps; warp w owns row slots w and w + NW
@@ -266,7 +267,7 @@ inline void rr_eig32_launch(const double* H, int m, int ld, const double* Xp, in
     cudaFuncSetAttribute(k_rr_eig32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_eig32_smem_bytes<P>());
     configured = true;
   }
-  k_rr_eig32<P><<<1, 8 * P, rr_eig32_smem_bytes<P>(), st>>>(H, m, ld, Xp, mprev, X, info, tol2);
+  launch_pdl(k_rr_eig32<P>, dim3(1), dim3(8 * P), rr_eig32_smem_bytes<P>(), st, H, m, ld, Xp, mprev, X, info, tol2);
 }
 
 inline void launch_rr_eig32(const double* H, int m, int ld, const double* Xp, int mprev, double* X, double* info,
@@ -288,6 +289,7 @@ inline void launch_rr_eig32(const double* H, int m, int ld, const double* Xp, in
 // column j.
 __global__ void __launch_bounds__(64) k_rr_oa_products(const double* H, int ld, const double* X, int m, double* S,
                                                        double* R) {
+  pdl_wait();
   __shared__ double xj[kRRMax], pj[kRRMax];
   const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   for (int i = t; i < m; i += nt) xj[i] = X[(size_t)i * m + j];
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(64) k_rr_oa_products(const double* H, int ld, 
 __global__ void __launch_bounds__(64) k_rr_oa_update(const double* X, const double* S, const double* R, int m,
                                                      double* Xout, int ldo, double* lam_out, double* delta,
                                                      int set_delta) {
+  pdl_wait();
   __shared__ double lam[kRRMax], e[kRRMax], red[6];
   const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   for (int i = t; i < m; i += nt) lam[i] = S[(size_t)i * m + i] / (1.0 - R[(size_t)i * m + i]);
@@ -375,6 +378,7 @@ constexpr int kRRClusterMax = 16;
 __global__ void __launch_bounds__(256) k_rr_finish(const double* H, int ld, int m, int nvec, const double* Xw, int ldw,
                                                    const double* lam_in, const double* delta, double* theta, double* Y,
                                                    int ldy) {
+  pdl_wait();
   extern __shared__ double smd[];
   double* Z = smd;                                   // [nvec][m]
   double* HZ = Z + (size_t)nvec * m;                 // [kRRClusterMax][m]

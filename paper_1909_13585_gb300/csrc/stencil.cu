@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_apply_stencil(Grid g, const T* __restri
                                                        const T* __restrict__ v, const T* __restrict__ b,
                                                        const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
                                                        int nr, int64_t stride, const double* __restrict__ act) {
+  pdl_wait();
   constexpr int NB = StencilDims<DIM>::NB;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int i, j, k;
@@ -140,13 +141,12 @@ static void stencil_dispatch(const Grid& g, const T* S, const uint8_t* fixed, in
                              const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
   dim3 grid((unsigned)((g.nnode + 255) / 256), (unsigned)((nr + R - 1) / R));
   const double* act = active_rhs();
-  note_launch();
   if (mode == APPLY_KV)
-    k_apply_stencil<DIM, T, APPLY_KV, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
+    launch_pdl(k_apply_stencil<DIM, T, APPLY_KV, R>, dim3(grid), dim3(256), 0, s, g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
   else if (mode == APPLY_RES)
-    k_apply_stencil<DIM, T, APPLY_RES, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
+    launch_pdl(k_apply_stencil<DIM, T, APPLY_RES, R>, dim3(grid), dim3(256), 0, s, g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
   else
-    k_apply_stencil<DIM, T, APPLY_JAC, R><<<grid, 256, 0, s>>>(g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
+    launch_pdl(k_apply_stencil<DIM, T, APPLY_JAC, R>, dim3(grid), dim3(256), 0, s, g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
 }
 
 // Right-hand sides per thread: reusing a stencil row across several RHS saves loads on large levels,
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(TX * TY) k_stencil_jac_prolong(Grid g, Grid gc
                                                                  T* __restrict__ y, SmoothArgs<T> sm, int nr,
                                                                  int64_t stride, int64_t cstride,
                                                                  const double* __restrict__ act) {
+  pdl_wait();
   constexpr int NX = TX + 2, NY = TY + 2;
   __shared__ T vs[R][NY][NX][2];
   const int r0 = blockIdx.z * R;
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(((2 * CX + 1) * (2 * CY + 1) + 31) / 32 * 32)
                            const uint8_t* __restrict__ fixed_c, T* __restrict__ bc, int64_t cstride,
                            const T* __restrict__ dinv_c, const T* __restrict__ coef_c, T* __restrict__ zc,
                            T* __restrict__ dc, const double* __restrict__ act) {
+  pdl_wait();
   constexpr int RX = 2 * CX + 1, RY = 2 * CY + 1;  // fine nodes whose residual the tile restricts
   constexpr int ZX = RX + 2, ZY = RY + 2;          // ... and the iterate around them
   constexpr int NTH = (RX * RY + 31) / 32 * 32;
@@ -409,6 +411,7 @@ __global__ void __launch_bounds__(256) k_stencil_cg_direction(Grid g, const doub
                                                               double* __restrict__ p_new, double* __restrict__ q,
                                                               int64_t stride, double* sc, double* partial,
                                                               unsigned* counters, int64_t pstride) {
+  pdl_wait();
   constexpr int NB = StencilDims<DIM>::NB;
   __shared__ double smem[64];
   const int rhs = blockIdx.y;
@@ -467,12 +470,11 @@ void launch_stencil_cg_direction(const Grid& g, const double* S, const uint8_t* 
                                  const double* p_old, double* p_new, double* q, int nr, int64_t stride, double* sc,
                                  double* partial, unsigned* counters, int64_t pstride, cudaStream_t s) {
   const dim3 grid((unsigned)((g.nnode + 255) / 256), (unsigned)nr);
-  note_launch();
   if (g.dim == 2)
-    k_stencil_cg_direction<2><<<grid, 256, 0, s>>>(g, S, fixed, z, p_old, p_new, q, stride, sc, partial, counters,
+    launch_pdl(k_stencil_cg_direction<2>, dim3(grid), dim3(256), 0, s, g, S, fixed, z, p_old, p_new, q, stride, sc, partial, counters,
                                                    pstride);
   else
-    k_stencil_cg_direction<3><<<grid, 256, 0, s>>>(g, S, fixed, z, p_old, p_new, q, stride, sc, partial, counters,
+    launch_pdl(k_stencil_cg_direction<3>, dim3(grid), dim3(256), 0, s, g, S, fixed, z, p_old, p_new, q, stride, sc, partial, counters,
                                                    pstride);
 }
 
@@ -494,18 +496,17 @@ void launch_stencil_jac_prolong_2d(const Grid& g, const Grid& gc, const T* S, co
   const double* act = active_rhs();
   const int nsm = sm_count_cached();
   const int64_t tiles32 = (int64_t)((g.nn[0] + 31) / 32) * ((g.nn[1] + 7) / 8);
-  note_launch();
   if (tiles32 * ((nr + 1) / 2) >= 2 * nsm) {
     const dim3 grid((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, (nr + 1) / 2);
-    k_stencil_jac_prolong<T, 32, 8, 2><<<grid, 256, 0, s>>>(g, gc, S, fixed, z, zc, b, dinv, y, sm, nr, stride,
+    launch_pdl(k_stencil_jac_prolong<T, 32, 8, 2>, dim3(grid), dim3(256), 0, s, g, gc, S, fixed, z, zc, b, dinv, y, sm, nr, stride,
                                                             cstride, act);
   } else if (tiles32 * nr >= nsm) {
     const dim3 grid((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, nr);
-    k_stencil_jac_prolong<T, 32, 8, 1><<<grid, 256, 0, s>>>(g, gc, S, fixed, z, zc, b, dinv, y, sm, nr, stride,
+    launch_pdl(k_stencil_jac_prolong<T, 32, 8, 1>, dim3(grid), dim3(256), 0, s, g, gc, S, fixed, z, zc, b, dinv, y, sm, nr, stride,
                                                             cstride, act);
   } else {
     const dim3 grid((g.nn[0] + 15) / 16, (g.nn[1] + 7) / 8, nr);
-    k_stencil_jac_prolong<T, 16, 8, 1><<<grid, 128, 0, s>>>(g, gc, S, fixed, z, zc, b, dinv, y, sm, nr, stride,
+    launch_pdl(k_stencil_jac_prolong<T, 16, 8, 1>, dim3(grid), dim3(128), 0, s, g, gc, S, fixed, z, zc, b, dinv, y, sm, nr, stride,
                                                             cstride, act);
   }
 }
@@ -517,14 +518,13 @@ void launch_stencil_res_restrict_2d(const Grid& g, const Grid& gc, const T* S, c
   const double* act = active_rhs();
   const int nsm = sm_count_cached();
   const int64_t big = (int64_t)((gc.nn[0] + 7) / 8) * ((gc.nn[1] + 7) / 8);
-  note_launch();
   if (big * nr >= 2 * nsm) {  // 17 x 17 fine nodes per tile, two or more blocks resident per SM
     const dim3 grid((gc.nn[0] + 7) / 8, (gc.nn[1] + 7) / 8, nr);
-    k_stencil_res_restrict<T, 8, 8><<<grid, 320, 0, s>>>(g, gc, S, fixed, z, b, stride, fixed_c, bc, cstride,
+    launch_pdl(k_stencil_res_restrict<T, 8, 8>, dim3(grid), dim3(320), 0, s, g, gc, S, fixed, z, b, stride, fixed_c, bc, cstride,
                                                          dinv_c, coef_c, zc, dc, act);
   } else {
     const dim3 grid((gc.nn[0] + 7) / 8, (gc.nn[1] + 3) / 4, nr);
-    k_stencil_res_restrict<T, 8, 4><<<grid, 160, 0, s>>>(g, gc, S, fixed, z, b, stride, fixed_c, bc, cstride,
+    launch_pdl(k_stencil_res_restrict<T, 8, 4>, dim3(grid), dim3(160), 0, s, g, gc, S, fixed, z, b, stride, fixed_c, bc, cstride,
                                                          dinv_c, coef_c, zc, dc, act);
   }
 }

@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace tobk {
@@ -134,6 +135,31 @@ namespace tobk {
 // Number of kernels this library has launched (all handles); read through tobk_launch_count().
 extern std::atomic<long long> g_launch_count;
 inline void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
+
+// Programmatic dependent launch.  The solver's inner loops are long chains of short, dependent
+// kernels; a kernel launched with launch_pdl may be scheduled while the previous kernel of the
+// stream is still finishing, so that its launch and block scheduling overlap that kernel's tail.
+// Every kernel launched this way calls pdl_wait() before its first global-memory access: the wait
+// returns once the previous kernel has completed and its writes are visible (and at once when the
+// kernel was launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 }  // namespace tobk
 
 // The opaque handle of the C-ABI.
