@@ -139,14 +139,20 @@ __global__ void __launch_bounds__(256) k_apply_stencil(Grid g, const T* __restri
 template <int DIM, typename T, int R>
 static void stencil_dispatch(const Grid& g, const T* S, const uint8_t* fixed, int mode, const T* v, const T* b,
                              const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
-  dim3 grid((unsigned)((g.nnode + 255) / 256), (unsigned)((nr + R - 1) / R));
+  // 128-thread blocks: the FP64-bound sweeps of a level with many right-hand sides run at the pace of
+  // the SM with the most blocks, and smaller blocks even out the count per SM
+  constexpr int kTh = 128;
+  dim3 grid((unsigned)((g.nnode + kTh - 1) / kTh), (unsigned)((nr + R - 1) / R));
   const double* act = active_rhs();
   if (mode == APPLY_KV)
-    launch_pdl(k_apply_stencil<DIM, T, APPLY_KV, R>, dim3(grid), dim3(256), 0, s, g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
+    launch_pdl(k_apply_stencil<DIM, T, APPLY_KV, R>, grid, dim3(kTh), 0, s, g, S, fixed, v, b, dinv, y, sm, nr,
+               stride, act);
   else if (mode == APPLY_RES)
-    launch_pdl(k_apply_stencil<DIM, T, APPLY_RES, R>, dim3(grid), dim3(256), 0, s, g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
+    launch_pdl(k_apply_stencil<DIM, T, APPLY_RES, R>, grid, dim3(kTh), 0, s, g, S, fixed, v, b, dinv, y, sm, nr,
+               stride, act);
   else
-    launch_pdl(k_apply_stencil<DIM, T, APPLY_JAC, R>, dim3(grid), dim3(256), 0, s, g, S, fixed, v, b, dinv, y, sm, nr, stride, act);
+    launch_pdl(k_apply_stencil<DIM, T, APPLY_JAC, R>, grid, dim3(kTh), 0, s, g, S, fixed, v, b, dinv, y, sm, nr,
+               stride, act);
 }
 
 // Right-hand sides per thread: reusing a stencil row across several RHS saves loads on large levels,
