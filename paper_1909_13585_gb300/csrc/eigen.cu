@@ -336,8 +336,8 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       const bool last = step == kRRRefineSteps - 1;
       double* xin = (step & 1) ? rrX1 : rrX0;
       double* xout = last ? rrXw : ((step & 1) ? rrX0 : rrX1);
-      launch_pdl(k_rr_oa_products, dim3(m), dim3(64), 0, st, h->Hs, mmax, xin, m, rrS, rrR);
-      launch_pdl(k_rr_oa_update, dim3(last ? nvec : m), dim3(64), 0, st, xin, rrS, rrR, m, xout, last ? mmax : m,
+      launch_pdl(k_rr_oa_products, dim3(m), dim3(kOAThreads), 0, st, h->Hs, mmax, xin, m, rrS, rrR);
+      launch_pdl(k_rr_oa_update, dim3(last ? nvec : m), dim3(kOAThreads), 0, st, xin, rrS, rrR, m, xout, last ? mmax : m,
                                                                            last ? rrLam : nullptr, rrDelta, step == 0);
     }
     launch_pdl(k_rr_finish, dim3(1), dim3(256), rr_finish_smem_bytes(m, nvec), st, 
@@ -503,8 +503,8 @@ int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host) {
     const bool last = step == kRRRefineSteps - 1;
     double* xin = (step & 1) ? rrX1 : rrX0;
     double* xout = last ? rrXw : ((step & 1) ? rrX0 : rrX1);
-    launch_pdl(k_rr_oa_products, dim3(q), dim3(64), 0, st, h->Hs, mmax, xin, q, rrS, rrR);
-    launch_pdl(k_rr_oa_update, dim3(q), dim3(64), 0, st, xin, rrS, rrR, q, xout, last ? mmax : q,
+    launch_pdl(k_rr_oa_products, dim3(q), dim3(kOAThreads), 0, st, h->Hs, mmax, xin, q, rrS, rrR);
+    launch_pdl(k_rr_oa_update, dim3(q), dim3(kOAThreads), 0, st, xin, rrS, rrR, q, xout, last ? mmax : q,
                                                             last ? rrLam : nullptr, rrDelta, step == 0);
   }
   launch_pdl(k_rr_finish, dim3(1), dim3(256), rr_finish_smem_bytes(q, q), st, h->Hs, mmax, q, q, rrXw, mmax, rrLam,

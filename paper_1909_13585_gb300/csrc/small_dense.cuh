@@ -285,45 +285,60 @@ inline void launch_rr_eig32(const double* H, int m, int ld, const double* Xp, in
   }
 }
 
-// Stage 2a.  S = X^T H X and R = I - X^T X ([m][m] each); block j computes
-// column j.
-__global__ void __launch_bounds__(64) k_rr_oa_products(const double* H, int ld, const double* X, int m, double* S,
-                                                       double* R) {
+// Stage 2a.  S = X^T H X and R = I - X^T X ([m][m] each); block j computes column j.  256 threads:
+// four groups of 64 take every fourth term of each dot product (four times the loads in flight of
+// one thread per row) and the four partial sums are added in a fixed order.
+constexpr int kOAThreads = 256;
+__global__ void __launch_bounds__(kOAThreads) k_rr_oa_products(const double* H, int ld, const double* X, int m,
+                                                               double* S, double* R) {
   pdl_wait();
   __shared__ double xj[kRRMax], pj[kRRMax];
-  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
-  for (int i = t; i < m; i += nt) xj[i] = X[(size_t)i * m + j];
+  __shared__ double part[3][4][kRRMax];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const int g = t >> 6, i = t & 63;
+  if (t < m) xj[t] = X[(size_t)t * m + j];
   __syncthreads();
-  for (int i = t; i < m; i += nt) {
+  if (i < m) {
     double s = 0.0;
-    for (int k = 0; k < m; ++k) s += H[(size_t)k * ld + i] * xj[k];
-    pj[i] = s;
+    for (int k = g; k < m; k += 4) s += H[(size_t)k * ld + i] * xj[k];
+    part[0][g][i] = s;
   }
   __syncthreads();
-  for (int i = t; i < m; i += nt) {
+  if (t < m) pj[t] = ((part[0][0][t] + part[0][1][t]) + part[0][2][t]) + part[0][3][t];
+  __syncthreads();
+  if (i < m) {
     double s = 0.0, r = 0.0;
-    for (int k = 0; k < m; ++k) {
+    for (int k = g; k < m; k += 4) {
       const double xki = X[(size_t)k * m + i];
       s += xki * pj[k];
       r += xki * xj[k];
     }
-    S[(size_t)i * m + j] = s;
-    R[(size_t)i * m + j] = (i == j ? 1.0 : 0.0) - r;
+    part[1][g][i] = s;
+    part[2][g][i] = r;
+  }
+  __syncthreads();
+  if (t < m) {
+    const double sv = ((part[1][0][t] + part[1][1][t]) + part[1][2][t]) + part[1][3][t];
+    const double rv = ((part[2][0][t] + part[2][1][t]) + part[2][2][t]) + part[2][3][t];
+    S[(size_t)t * m + j] = sv;
+    R[(size_t)t * m + j] = (t == j ? 1.0 : 0.0) - rv;
   }
 }
 
-// Stage 2b.  One refinement step for columns j < gridDim.x (block j, 64 threads):
+// Stage 2b.  One refinement step for columns j < gridDim.x (block j, 256 threads):
 // Xout[:, j] = X[:, j] + X E[:, j] (ldo = leading dimension of Xout) and lam_out[j].
 // set_delta != 0: the step's error bound delta = 2 (||S - diag(lambda)||_F + max|lambda| ||R||_F)
 // is computed (by every block, identically) and block 0 stores it in *delta; otherwise *delta is
 // read.
-__global__ void __launch_bounds__(64) k_rr_oa_update(const double* X, const double* S, const double* R, int m,
-                                                     double* Xout, int ldo, double* lam_out, double* delta,
-                                                     int set_delta) {
+__global__ void __launch_bounds__(kOAThreads) k_rr_oa_update(const double* X, const double* S, const double* R, int m,
+                                                             double* Xout, int ldo, double* lam_out, double* delta,
+                                                             int set_delta) {
   pdl_wait();
-  __shared__ double lam[kRRMax], e[kRRMax], red[6];
+  constexpr int NW = kOAThreads / 32;
+  __shared__ double lam[kRRMax], e[kRRMax], red[3 * NW];
+  __shared__ double part[4][kRRMax];
   const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
-  for (int i = t; i < m; i += nt) lam[i] = S[(size_t)i * m + i] / (1.0 - R[(size_t)i * m + i]);
+  if (t < m) lam[t] = S[(size_t)t * m + t] / (1.0 - R[(size_t)t * m + t]);
   __syncthreads();
   double dl;
   if (set_delta) {
@@ -334,7 +349,7 @@ __global__ void __launch_bounds__(64) k_rr_oa_update(const double* X, const doub
       so += sv * sv;
       ro += R[q] * R[q];
     }
-    for (int i = t; i < m; i += nt) lm = fmax(lm, fabs(lam[i]));
+    if (t < m) lm = fabs(lam[t]);
     for (int o = 16; o > 0; o >>= 1) {
       so += __shfl_xor_sync(0xffffffffu, so, o);
       ro += __shfl_xor_sync(0xffffffffu, ro, o);
@@ -346,26 +361,34 @@ __global__ void __launch_bounds__(64) k_rr_oa_update(const double* X, const doub
       red[3 * (t >> 5) + 2] = lm;
     }
     __syncthreads();
-    so = red[0] + red[3];
-    ro = red[1] + red[4];
-    lm = fmax(red[2], red[5]);
+    so = 0.0;
+    ro = 0.0;
+    lm = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      so += red[3 * w];
+      ro += red[3 * w + 1];
+      lm = fmax(lm, red[3 * w + 2]);
+    }
     dl = 2.0 * (sqrt(so) + lm * sqrt(ro));
     if (j == 0 && t == 0) *delta = dl;
   } else {
     dl = *delta;
   }
-  for (int i = t; i < m; i += nt) {
-    const double rij = R[(size_t)i * m + j];
+  if (t < m) {
+    const double rij = R[(size_t)t * m + j];
     double eij = 0.5 * rij;
-    if (i != j && fabs(lam[j] - lam[i]) > dl) eij = (S[(size_t)i * m + j] + lam[j] * rij) / (lam[j] - lam[i]);
-    e[i] = eij;
+    if (t != j && fabs(lam[j] - lam[t]) > dl) eij = (S[(size_t)t * m + j] + lam[j] * rij) / (lam[j] - lam[t]);
+    e[t] = eij;
   }
   __syncthreads();
-  for (int r = t; r < m; r += nt) {
-    double s = X[(size_t)r * m + j];
-    for (int i = 0; i < m; ++i) s += X[(size_t)r * m + i] * e[i];
-    Xout[(size_t)r * ldo + j] = s;
+  const int g = t >> 6, r = t & 63;
+  if (r < m) {
+    double s = 0.0;
+    for (int i = g; i < m; i += 4) s += X[(size_t)r * m + i] * e[i];
+    part[g][r] = s;
   }
+  __syncthreads();
+  if (t < m) Xout[(size_t)t * ldo + j] = X[(size_t)t * m + j] + (((part[0][t] + part[1][t]) + part[2][t]) + part[3][t]);
   if (t == 0 && lam_out) lam_out[j] = lam[j];
 }
 
