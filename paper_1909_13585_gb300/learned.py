@@ -10,6 +10,7 @@ step of the solver and of the network runs in libtobk.so.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import multiprocessing as mp
 import os
@@ -168,15 +169,17 @@ def load_weights(pkg, torch, path, stream=None):
     return net
 
 
-def evaluate(pkg, torch, net, X, nel=NEL, rtol=1e-8, flush=None):
+def evaluate(pkg, torch, net, X, nel=NEL, rtol=1e-8, flush=None, precision=None):
     """Per held-out design: mgPCG iterations and device time from zero and from the network's guess
-    (network inference included) and the true relative residual of both.  Both arms go through
-    tobk_solve_equilibrium; the plain arm is the fallback.  `flush`: a device tensor larger than L2,
-    zeroed before each timed arm."""
+    (network inference included), the true relative residual of both and the relative energy-norm
+    error of the guess.  Both arms go through tobk_solve_equilibrium; the plain arm is the fallback.
+    `flush`: a device tensor larger than L2, zeroed before each timed arm; `precision`: the solver's
+    V-cycle precision (default: the FP32 V-cycle)."""
     dev = torch.device("cuda")
     p0 = problem(X[0], nel)
     stream = net.stream  # the solver shares the network's stream, so that the guess is ordered before the solve
-    s = pkg.Solver(p0, stream=stream, precision=pkg.TOBK_FP32_VCYCLE, rtol=rtol, max_rhs=1)
+    prec = pkg.TOBK_FP32_VCYCLE if precision is None else precision
+    s = pkg.Solver(p0, stream=stream, precision=prec, rtol=rtol, max_rhs=1)
     f = torch.from_numpy(p0.f).to(dev)
     fixed = torch.from_numpy(p0.fixed.astype(np.uint8)).to(dev)
     u0 = torch.zeros(p0.num_dofs, dtype=torch.float64, device=dev)
@@ -201,6 +204,22 @@ def evaluate(pkg, torch, net, X, nel=NEL, rtol=1e-8, flush=None):
             torch.cuda.synchronize()
             row[arm] = {"iterations": info["iterations"], "ms": e0.elapsed_time(e1),
                         "rel_residual": info["rel_residual"], "converged": info["converged"]}
+        # relative energy-norm error of the guess the solve started from (the network's output scaled
+        # by alpha = u0^T f / u0^T K u0, as tobk_set_initial_guess does), against the converged solution
+        u = torch.zeros(p0.num_dofs, dtype=torch.float64, device=dev)
+        s.get_field(pkg.TOBK_FIELD_U, u)
+        Ku = torch.zeros_like(u)
+        Ku0 = torch.zeros_like(u)
+        s.apply_K(1, u, Ku)
+        s.apply_K(1, u0, Ku0)
+        torch.cuda.synchronize()
+        u0m = torch.where(fixed.bool(), torch.zeros_like(u0), u0)
+        Ku0 = torch.where(fixed.bool(), torch.zeros_like(Ku0), Ku0)
+        den = float(u0m @ Ku0)
+        alpha = float(u0m @ f) / den if den > 0.0 else 0.0
+        e_energy = float(u @ Ku) - 2.0 * alpha * float(u0m @ Ku) + alpha * alpha * den
+        row["guess_energy_error"] = math.sqrt(max(e_energy, 0.0) / float(u @ Ku))
+        row["rtol"] = rtol
         out.append(row)
     s.set_initial_guess(None)
     s.close()
@@ -216,7 +235,14 @@ def summary(rows):
             "iterations_learned_mean": float(it_l.mean()), "ms_plain_mean": float(ms_p.mean()),
             "ms_learned_mean": float(ms_l.mean()),
             "fallback_rate": float(np.mean([r["learned"]["iterations"] >= r["plain"]["iterations"] for r in rows])),
-            "rel_residual_max": float(max(max(r["plain"]["rel_residual"], r["learned"]["rel_residual"]) for r in rows))}
+            "rel_residual_max": float(max(max(r["plain"]["rel_residual"], r["learned"]["rel_residual"]) for r in rows)),
+            # what the guess can buy: mgPCG reduces the error by the same factor per iteration from any
+            # start, rho = rtol^(1 / plain iterations), so a start with relative energy error e saves
+            # about log(e) / log(rho) iterations
+            "guess_energy_error_mean": float(np.mean([r["guess_energy_error"] for r in rows])),
+            "iterations_saved_expected": float(np.mean([
+                math.log(max(r["guess_energy_error"], 1e-300)) / math.log(r["rtol"] ** (1.0 / r["plain"]["iterations"]))
+                for r in rows]))}
 
 
 def main():
