@@ -78,6 +78,13 @@ struct tobk_handle {
   };
   std::map<uint64_t, CGGraph> cg_graphs;
   bool use_graphs = true;
+  // Split multi-RHS solves: the second half of the right-hand sides runs on stream2 (forked from
+  // and joined to the handle's stream by events), so that one half's latency-bound coarse levels
+  // overlap the other half's FP64-bound fine level.  rhs_off = first RHS column of the half being
+  // enqueued (0 otherwise); every RHS-sized work buffer is used from that column on.
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int rhs_off = 0;
   bool solve_only = false;
 
   // kernel-class timing

@@ -284,6 +284,14 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
     destroy_handle(h);
     return TOBK_E_NOMEM;
   }
+  if (h->stream != nullptr &&
+      (cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    destroy_handle(h);
+    return TOBK_E_CUDA;
+  }
   cudaStream_t s = h->stream;
   cudaMemsetAsync(h->arena.base, 0, bytes, s);
   cudaMemcpyAsync(h->d_Ke0, h->tab.Ke0.data(), sizeof(double) * h->tab.Ke0.size(), cudaMemcpyHostToDevice, s);
@@ -304,6 +312,12 @@ void destroy_handle(tobk_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->stream2) {
+    cudaStreamSynchronize(h->stream2);
+    cudaStreamDestroy(h->stream2);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto& p : h->prof_pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -479,13 +493,44 @@ void prof_flush(tobk_handle* h) {
   h->prof_pending.clear();
 }
 
+// The level's work buffers from RHS column h->rhs_off on (vectors are [rhs][n] blocks); per-DOF data
+// (mask, operator, diagonal, smoother coefficients) is shared by all right-hand sides.
+static Level lvl(tobk_handle* h, int j) {
+  Level L = h->lv[j];
+  const int64_t o = (int64_t)h->rhs_off * L.g.n;
+  if (o) {
+    for (double** p : {&L.dA, &L.dB, &L.b, &L.z, &L.t, &L.r})
+      if (*p) *p += o;
+    for (float** p : {&L.dA32, &L.dB32, &L.b32, &L.z32, &L.t32, &L.r32})
+      if (*p) *p += o;
+  }
+  return L;
+}
+
+// The CG work space from RHS column h->rhs_off on: vectors of length n, per-RHS scalars and
+// counters, and reduction partials (each kernel writes partial + rhs * its stride, every stride at
+// most the fine level's cg_partial_stride, which the buffer is sized for per RHS).
+static CGWork cgw(tobk_handle* h, int64_t n) {
+  CGWork w = h->cg;
+  const int r = h->rhs_off;
+  if (r) {
+    const int64_t o = (int64_t)r * n;
+    for (double** p : {&w.x, &w.r, &w.z, &w.zt, &w.p0, &w.p1, &w.q}) *p += o;
+    w.sc += (size_t)r * kScStride;
+    w.host_sc += (size_t)r * kScStride;
+    w.partial += (size_t)r * cg_partial_stride(h->lv[0].g);
+    w.counters += r;
+  }
+  return w;
+}
+
 // Node x RHS count below which a 2D stencil level fuses its residual into the restriction.
 constexpr int64_t kFusedResidualWork = 131072;
 
 // z0_ready: the restriction into this level already took the first smoothing step (z, dA written)
 static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* z, double* t, bool z0_ready = false) {
   cudaStream_t s = h->stream;
-  Level& L = h->lv[j];
+  const Level L = lvl(h, j);
   const int64_t n = L.g.n;
   const int ks = j == 0 ? TOBK_KC_FINE_SMOOTH : TOBK_KC_COARSE;
   const int kr = j == 0 ? TOBK_KC_FINE_RESIDUAL : TOBK_KC_COARSE;
@@ -511,7 +556,7 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
     std::swap(z, t);
     std::swap(dA, dB);
   }
-  Level& C = h->lv[j + 1];
+  const Level C = lvl(h, j + 1);
   const bool fuse = j + 1 < h->L - 1;  // the coarse level smooths (it is not the dense coarsest)
   // 2D stencil levels fuse residual + restriction and prolongation + first post-smoothing step.  The
   // fused residual recomputes the tile halos (about an eighth more FP64 work), which pays only while
@@ -563,7 +608,7 @@ static double* vcycle64(tobk_handle* h, int j, int nr, const double* b, double* 
 
 static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, float* t, bool z0_ready = false) {
   cudaStream_t s = h->stream;
-  Level& L = h->lv[j];
+  const Level L = lvl(h, j);
   const int64_t n = L.g.n;
   const int ks = j == 0 ? TOBK_KC_FINE_SMOOTH : TOBK_KC_COARSE;
   const int kr = j == 0 ? TOBK_KC_FINE_RESIDUAL : TOBK_KC_COARSE;
@@ -588,7 +633,7 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
     std::swap(z, t);
     std::swap(dA, dB);
   }
-  Level& C = h->lv[j + 1];
+  const Level C = lvl(h, j + 1);
   const bool fuse = j + 1 < h->L - 1;
   const bool fused_transfers = op.S32 != nullptr && op.g.dim == 2;
   const bool fused_res = fused_transfers && op.g.nnode * nr < kFusedResidualWork;
@@ -639,7 +684,7 @@ static float* vcycle32(tobk_handle* h, int j, int nr, const float* b, float* z, 
 static double* precondition(tobk_handle* h, int s, int nr, const double* r, double* z, double* zt, int precision,
                            bool z0_ready = false) {
   if (precision == TOBK_FP64) return vcycle64(h, s, nr, r, z, zt, z0_ready);
-  Level& L = h->lv[s];
+  const Level L = lvl(h, s);
   const int64_t n = L.g.n;
   launch_f64_to_f32(r, L.b32, (int64_t)nr * n, h->stream);
   float* z32 = vcycle32(h, s, nr, L.b32, L.z32, L.t32);
@@ -665,10 +710,10 @@ void apply_vcycle(tobk_handle* h, int j, int nr, const double* r, double* out) {
 static CGZ0 cg_z0(tobk_handle* h, int s, int precision) {
   CGZ0 z0;
   if (precision != TOBK_FP64 || s >= h->L - 1) return z0;
-  Level& L = h->lv[s];
+  const Level L = lvl(h, s);
   z0.dinv = L.dinv;
   z0.coef = L.coef;
-  z0.z = h->cg.z;
+  z0.z = cgw(h, L.g.n).z;
   z0.d = L.dA;
   return z0;
 }
@@ -677,7 +722,7 @@ static void enqueue_cg_pair(tobk_handle* h, int s, int nr, int precision) {
   cudaStream_t st = h->stream;
   const LevelOpDesc op = level_op(h, s);
   const int64_t n = op.g.n;
-  CGWork& w = h->cg;
+  const CGWork w = cgw(h, n);
   const bool flexible = precision != TOBK_FP64;
   const CGZ0 z0 = cg_z0(h, s, precision);
   for (int k = 0; k < 2; ++k) {
@@ -703,7 +748,7 @@ static int run_cg_pair(tobk_handle* h, int s, int nr, int precision) {
     enqueue_cg_pair(h, s, nr, precision);
     return TOBK_OK;
   }
-  const uint64_t key = (uint64_t)s | ((uint64_t)nr << 8) | ((uint64_t)precision << 16);
+  const uint64_t key = (uint64_t)s | ((uint64_t)nr << 8) | ((uint64_t)precision << 16) | ((uint64_t)h->rhs_off << 24);
   auto it = h->cg_graphs.find(key);
   if (it == h->cg_graphs.end()) {
     cudaGraph_t g = nullptr;
@@ -725,6 +770,42 @@ static int run_cg_pair(tobk_handle* h, int s, int nr, int precision) {
   cudaGraphLaunch(it->second.exec, h->stream);
   g_launch_count.fetch_add(it->second.kernels);
   return TOBK_OK;
+}
+
+// Enqueues the work of one half of a split solve: the handle's stream, RHS offset and active-RHS
+// pointer are switched to the half's for the lifetime of the scope.
+struct HalfScope {
+  tobk_handle* h;
+  cudaStream_t s0;
+  int off0;
+  const double* act0;
+  HalfScope(tobk_handle* hh, cudaStream_t s, int off) : h(hh), s0(hh->stream), off0(hh->rhs_off), act0(active_rhs()) {
+    h->stream = s;
+    h->rhs_off = off;
+    set_active_rhs(h->cg.sc + (size_t)off * kScStride);
+  }
+  ~HalfScope() {
+    h->stream = s0;
+    h->rhs_off = off0;
+    set_active_rhs(act0);
+  }
+};
+
+// One CG iteration pair for every still-active half of the solve: the first n0 right-hand sides on
+// the handle's stream, the rest (when split) on stream2, forked after the work already enqueued.
+static int run_cg_pair_halves(tobk_handle* h, int s, int nr, int n0, int precision, const bool (&active)[2]) {
+  if (n0 >= nr) return run_cg_pair(h, s, nr, precision);
+  cudaEventRecord(h->ev_fork, h->stream);
+  cudaStreamWaitEvent(h->stream2, h->ev_fork, 0);
+  int rc = TOBK_OK;
+  if (active[0]) rc = run_cg_pair(h, s, n0, precision);
+  if (rc == TOBK_OK && active[1]) {
+    HalfScope hs(h, h->stream2, n0);
+    rc = run_cg_pair(h, s, nr - n0, precision);
+  }
+  cudaEventRecord(h->ev_join, h->stream2);
+  cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+  return rc;
 }
 
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
@@ -749,6 +830,11 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
   double worst = 0.0;
   int iters = 0;
   bool all_conv = true;
+  // independent CG recurrences: with two or more right-hand sides on a stream of the caller's, the
+  // second half of them runs concurrently on stream2 (graph-replayed pairs only)
+  const bool split = nr >= 2 && h->stream != nullptr && h->stream2 != nullptr && h->use_graphs && !h->prof_on;
+  const int n0 = split ? (nr + 1) / 2 : nr;
+  bool half_active[2] = {true, true};
   if (fixed_iters) {
     // a fixed number of iterations as an approximate inverse (a preconditioner): no host
     // synchronisation, no exit check; breakdown shows in the caller's own residuals
@@ -756,7 +842,7 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
     cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
     cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
     while (2 * pairs < max_iter) {
-      rc = run_cg_pair(h, s, nr, precision);
+      rc = run_cg_pair_halves(h, s, nr, n0, precision, half_active);
       if (rc) break;
       ++pairs;
     }
@@ -776,15 +862,16 @@ int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double 
                    cg_z0(h, s, precision));
     cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
     cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+    half_active[0] = half_active[1] = true;
     while (2 * pairs < max_iter) {
-      rc = run_cg_pair(h, s, nr, precision);
+      rc = run_cg_pair_halves(h, s, nr, n0, precision, half_active);
       if (rc) break;
       ++pairs;
       cudaMemcpyAsync(w.host_sc, w.sc, sizeof(double) * nr * kScStride, cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
-      bool any = false;
-      for (int r = 0; r < nr; ++r) any |= w.host_sc[r * kScStride + SC_ACTIVE] != 0.0;
-      if (!any) break;
+      half_active[0] = half_active[1] = false;
+      for (int r = 0; r < nr; ++r) half_active[r < n0 ? 0 : 1] |= w.host_sc[r * kScStride + SC_ACTIVE] != 0.0;
+      if (!half_active[0] && !half_active[1]) break;
     }
     if (rc) break;
     int status = 0;
