@@ -440,10 +440,23 @@ int setup_hierarchy(tobk_handle* h) {
     launch_diag(level_op(h, j), Lc.dinv, mixed ? Lc.dinv32 : nullptr, s);
     launch_stencil_assemble(Lc.g, Lc.Ke, Lc.fixed, Lc.S, mixed ? Lc.S32 : nullptr, s);
   }
+  // The coarsest inverse (a chain of pivot blocks, each on one SM) and the smoothers' eigenvalue
+  // bounds (power iterations on every smoothing level) depend on the Galerkin operators only and not
+  // on each other: with a second stream they run concurrently.
   const int jc = h->L - 1;
-  launch_dense_assemble(level_op(h, jc), h->Adense, s);
-  h->Ainv = launch_dense_invert(h->Adense, h->Awork, h->lv[jc].g.n, h->dscal + 1000, s);
+  cudaStream_t sc = s;
+  if (h->stream2 != nullptr) {
+    cudaEventRecord(h->ev_fork, s);
+    cudaStreamWaitEvent(h->stream2, h->ev_fork, 0);
+    sc = h->stream2;
+  }
+  launch_dense_assemble(level_op(h, jc), h->Adense, sc);
+  h->Ainv = launch_dense_invert(h->Adense, h->Awork, h->lv[jc].g.n, h->dscal + 1000, sc);
   setup_smoothers(h);
+  if (sc != s) {
+    cudaEventRecord(h->ev_join, sc);
+    cudaStreamWaitEvent(s, h->ev_join, 0);
+  }
   int rc = check_cuda(h, "setup_hierarchy");
   if (rc) return rc;
   h->setup_done = true;
