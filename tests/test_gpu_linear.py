@@ -163,3 +163,30 @@ def test_graph_replayed_solves_match_direct_launches():
     assert i1["iterations"] == i2["iterations"] == i3["iterations"]
     assert np.array_equal(u1, u2)
     assert J1 == J2 == J3
+
+
+@pytest.mark.parametrize("case", [CASES_2D[2], CASES_3D[1]])
+def test_two_stream_split_solve_is_bit_identical(case):
+    """A multi-RHS solve on a caller's stream runs its right-hand sides as two halves on two streams;
+    every RHS is an independent CG recurrence with the same kernels, so the solutions and iteration
+    counts must equal those of the single-stream launch sequence (the legacy stream, which never
+    splits) bit for bit, for an odd RHS count too."""
+    torch, pkg = require_gpu()
+    p = _problem(case)
+    rng = np.random.default_rng(7)
+    for nr in (2, 5):
+        B = rng.standard_normal((nr, p.num_dofs))
+        B[:, p.fixed == 1] = 0.0
+        out = []
+        for stream in (None, torch.cuda.Stream()):
+            s = pkg.Solver(p, stream=stream, max_rhs=nr)
+            s.solve_equilibrium()
+            X = torch.zeros((nr, p.num_dofs), dtype=torch.float64, device="cuda")
+            info = s.solve(1, to_dev(torch, B), X, nr)
+            info2 = s.solve(1, to_dev(torch, B), X, nr)        # replays the halves' cached graphs
+            torch.cuda.synchronize()
+            out.append((X.cpu().numpy(), info["iterations"], info2["iterations"]))
+            s.close()
+        assert out[0][1] == out[1][1] == out[1][2]
+        assert np.array_equal(out[0][0], out[1][0])
+
