@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision / 3D form measurements")
     ap.add_argument("--profile-run", action="store_true",
                     help="one untimed step only (for an external profiler's launch list)")
+    ap.add_argument("--profile-classes", action="store_true",
+                    help="with --profile-run: the library's kernel-class profiler on during the step, i.e. every "
+                         "kernel launched directly on the solver's stream, as in the class timing of the bench line")
     ap.add_argument("--eig-gram-tc", type=int, default=0, choices=[0, 1],
                     help="eigensolver Gram products on the tensor cores (FP64-accurate splitting)")
     return ap.parse_args()
@@ -498,6 +501,8 @@ def ours(args):
         step()
     torch.cuda.synchronize()
     if args.profile_run:
+        if args.profile_classes:
+            s.profile(True)
         step()
         torch.cuda.synchronize()
         if rank == 0:

@@ -2,13 +2,20 @@
 // Algorithm 1 step 3 and Appendix A) for Q4 elements.
 //
 // Q4 operator in factored form (q4_element.cuh), element by element on
-// shared-memory tiles: a block computes the 32 x 8 elements around a 31 x 7 tile of nodes once (one
-// element per thread, so the FP64-bound force phase is a single full round), stores their nodal
-// forces in shared memory and gathers the four contributions of each node.  On GB300,
+// shared-memory tiles: a block computes the (TX + 1) x (TY + 1) elements around a TX x TY tile of
+// nodes once (one element per thread, so the FP64-bound force phase is a single full round), stores
+// their nodal forces in shared memory and gathers the four contributions of each node.  On GB300,
 // where FP64 runs at 2 FMA/clk/SM, the FP64 fine-level smoother is bound by the element's
 // arithmetic, so the ~41 operations of the factored form (against 64 multiply-adds for the dense
-// 8 x 8 product) set its speed.
+// 8 x 8 product) set its speed -- and so does every element a tile computes beyond the grid's own:
+// the ring of elements around a tile is computed by each of its neighbours too, and a last tile row
+// or column that the grid only partly covers computes its whole element tile.  The tile shape is
+// therefore chosen per grid (q4_tile_choice) among a few with a multiple of 32 threads, to minimise
+// the elements computed: on the 161 x 481-node column, 24 x 12 elements over 23 x 11 nodes compute
+// 88,704 element forces per RHS against 105,984 for 32 x 8 over 31 x 7.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "device_common.cuh"
 #include "kernels.h"
@@ -16,20 +23,23 @@
 
 namespace tobk {
 
-namespace {
-constexpr int TX = 31, TY = 7;  // node tile; (TX + 1) (TY + 1) = 256 elements = one per thread
-constexpr int kThreadsQ4 = 256;
-static_assert((TX + 1) * (TY + 1) == kThreadsQ4, "one element per thread");
-constexpr int EX = TX + 1, EY = TY + 1;  // element tile
-constexpr int NX = TX + 2, NY = TY + 2;  // node tile
-}  // namespace
+// Node tile TX x TY, element tile (TX + 1) x (TY + 1) = one element per thread.
+template <int TX_, int TY_>
+struct Q4Tile {
+  static constexpr int TX = TX_, TY = TY_;
+  static constexpr int EX = TX + 1, EY = TY + 1;  // element tile
+  static constexpr int NX = TX + 2, NY = TY + 2;  // node tile with its halo
+  static constexpr int kThreads = EX * EY;
+  static_assert(kThreads % 32 == 0 && kThreads <= 512, "whole warps, one element per thread");
+};
 
 // Element forces of the (EX x EY) element tile into fe, zero outside the grid.
-template <typename T>
+template <typename T, class Tl>
 __device__ __forceinline__ void q4_tile_forces(const Grid& g, const T* __restrict__ Ek, const Q4Consts<T>& cst, int x0,
-                                               int y0, const T (&su)[NY][NX], const T (&sv)[NY][NX],
-                                               T (&fe)[EY][EX][8]) {
-  for (int q = threadIdx.x; q < EX * EY; q += kThreadsQ4) {
+                                               int y0, const T (&su)[Tl::NY][Tl::NX], const T (&sv)[Tl::NY][Tl::NX],
+                                               T (&fe)[Tl::EY][Tl::EX][8]) {
+  constexpr int EX = Tl::EX, EY = Tl::EY;
+  for (int q = threadIdx.x; q < EX * EY; q += Tl::kThreads) {
     const int lx = q % EX, ly = q / EX;
     const int ex = x0 - 1 + lx, ey = y0 - 1 + ly;
     T f[8];
@@ -45,12 +55,13 @@ __device__ __forceinline__ void q4_tile_forces(const Grid& g, const T* __restric
   }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreadsQ4) k_fine_q4(Grid g, const T* __restrict__ Ek, const uint8_t* __restrict__ fixed,
-                                                    Q4Consts<T> cst, const T* __restrict__ v, const T* __restrict__ b,
-                                                    const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
-                                                    int64_t stride, const double* __restrict__ act) {
+template <typename T, int MODE, class Tl>
+__global__ void __launch_bounds__(Tl::kThreads) k_fine_q4(Grid g, const T* __restrict__ Ek, const uint8_t* __restrict__ fixed,
+                                                      Q4Consts<T> cst, const T* __restrict__ v, const T* __restrict__ b,
+                                                      const T* __restrict__ dinv, T* __restrict__ y, SmoothArgs<T> sm,
+                                                      int64_t stride, const double* __restrict__ act) {
   pdl_wait();
+  constexpr int TX = Tl::TX, TY = Tl::TY, NX = Tl::NX, NY = Tl::NY, EX = Tl::EX, EY = Tl::EY;
   __shared__ T su[NY][NX], sv[NY][NX];
   __shared__ T fe[EY][EX][8];
   const int rhs = blockIdx.z;
@@ -59,7 +70,7 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4(Grid g, const T* __restr
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nnx = g.nn[0], nny = g.nn[1];
   const int64_t off = (int64_t)rhs * stride;
-  for (int q = tid; q < NX * NY; q += kThreadsQ4) {
+  for (int q = tid; q < NX * NY; q += Tl::kThreads) {
     const int lx = q % NX, ly = q / NX;
     const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
     T a = T(0), c = T(0);
@@ -72,9 +83,9 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4(Grid g, const T* __restr
     sv[ly][lx] = c;
   }
   __syncthreads();
-  q4_tile_forces<T>(g, Ek, cst, x0, y0, su, sv, fe);
+  q4_tile_forces<T, Tl>(g, Ek, cst, x0, y0, su, sv, fe);
   __syncthreads();
-  const int tx = tid % TX, ty = tid / TX;  // threads TX * TY .. 255 only computed elements
+  const int tx = tid % TX, ty = tid / TX;  // threads TX * TY .. only computed elements
   const int X = x0 + tx, Y = y0 + ty;
   if (tid >= TX * TY || X >= nnx || Y >= nny) return;
   // elements around node (X, Y): (X-1,Y-1) local node 2, (X,Y-1) node 3, (X-1,Y) node 1, (X,Y) node 0
@@ -104,18 +115,52 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4(Grid g, const T* __restr
   }
 }
 
+// The candidate tile shapes (node tiles; element tiles of 256, 288 and 224 threads) and the one used
+// on grid g: the shape that computes the fewest elements (ties: the earlier one).  The choice depends
+// on the grid only, not on the number of right-hand sides, so that the block partition of the CG
+// reductions -- and with it every right-hand side's result, bit for bit -- is the same however a
+// solve is batched or split.
+using Q4TileA = Q4Tile<31, 7>;
+using Q4TileB = Q4Tile<23, 11>;
+using Q4TileC = Q4Tile<15, 13>;
+static int64_t q4_tiles_of(const Grid& g, int tx, int ty) {
+  return (int64_t)((g.nn[0] + tx - 1) / tx) * ((g.nn[1] + ty - 1) / ty);
+}
+static int q4_tile_choice(const Grid& g) {
+  const int64_t w[3] = {q4_tiles_of(g, Q4TileA::TX, Q4TileA::TY) * Q4TileA::kThreads,
+                        q4_tiles_of(g, Q4TileB::TX, Q4TileB::TY) * Q4TileB::kThreads,
+                        q4_tiles_of(g, Q4TileC::TX, Q4TileC::TY) * Q4TileC::kThreads};
+  int best = 0;
+  for (int c = 1; c < 3; ++c)
+    if (w[c] < w[best]) best = c;
+  return best;
+}
+
+template <typename T, class Tl>
+static void fine_q4_launch(const Grid& g, const T* Ek, const uint8_t* fixed, const Q4Consts<T>& cst, int mode,
+                           const T* v, const T* b, const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride,
+                           const double* act, cudaStream_t s) {
+  const dim3 grid((unsigned)((g.nn[0] + Tl::TX - 1) / Tl::TX), (unsigned)((g.nn[1] + Tl::TY - 1) / Tl::TY),
+                  (unsigned)nr);
+  const dim3 block(Tl::kThreads);
+  if (mode == APPLY_KV)
+    launch_pdl(k_fine_q4<T, APPLY_KV, Tl>, grid, block, 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+  else if (mode == APPLY_RES)
+    launch_pdl(k_fine_q4<T, APPLY_RES, Tl>, grid, block, 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+  else
+    launch_pdl(k_fine_q4<T, APPLY_JAC, Tl>, grid, block, 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+}
+
 template <typename T>
 void launch_fine_q4(const Grid& g, const T* Ek, const uint8_t* fixed, const double* Ke0, int mode, const T* v,
                     const T* b, const T* dinv, T* y, SmoothArgs<T> sm, int nr, int64_t stride, cudaStream_t s) {
   const Q4Consts<T> cst = q4_consts<T>(Ke0);
-  dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)nr);
   const double* act = active_rhs();
-  if (mode == APPLY_KV)
-    launch_pdl(k_fine_q4<T, APPLY_KV>, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
-  else if (mode == APPLY_RES)
-    launch_pdl(k_fine_q4<T, APPLY_RES>, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
-  else
-    launch_pdl(k_fine_q4<T, APPLY_JAC>, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, v, b, dinv, y, sm, stride, act);
+  switch (q4_tile_choice(g)) {
+    case 0: fine_q4_launch<T, Q4TileA>(g, Ek, fixed, cst, mode, v, b, dinv, y, sm, nr, stride, act, s); break;
+    case 1: fine_q4_launch<T, Q4TileB>(g, Ek, fixed, cst, mode, v, b, dinv, y, sm, nr, stride, act, s); break;
+    default: fine_q4_launch<T, Q4TileC>(g, Ek, fixed, cst, mode, v, b, dinv, y, sm, nr, stride, act, s); break;
+  }
 }
 
 template void launch_fine_q4<double>(const Grid&, const double*, const uint8_t*, const double*, int, const double*,
@@ -124,11 +169,17 @@ template void launch_fine_q4<double>(const Grid&, const double*, const uint8_t*,
 template void launch_fine_q4<float>(const Grid&, const float*, const uint8_t*, const double*, int, const float*,
                                     const float*, const float*, float*, SmoothArgs<float>, int, int64_t, cudaStream_t);
 
-int64_t fine_q4_tiles(const Grid& g) { return (int64_t)((g.nn[0] + TX - 1) / TX) * ((g.nn[1] + TY - 1) / TY); }
+// Blocks per RHS of the fine Q4 kernels on grid g (the most any candidate tile shape uses, so that
+// reduction buffers sized with it hold every choice).
+int64_t fine_q4_tiles(const Grid& g) {
+  return std::max({q4_tiles_of(g, Q4TileA::TX, Q4TileA::TY), q4_tiles_of(g, Q4TileB::TX, Q4TileB::TY),
+                   q4_tiles_of(g, Q4TileC::TX, Q4TileC::TY)});
+}
 
 // CG direction on the fine level (FP64): p = z + beta p_old (zero at fixed DOFs), q = K p, and the
 // per-RHS reduction p.q -> sc[SC_PQ], alpha = (p.r) / (p.q) (last block of the RHS).
-__global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, const double* __restrict__ Ek,
+template <class Tl>
+__global__ void __launch_bounds__(Tl::kThreads) k_fine_q4_cg_direction(Grid g, const double* __restrict__ Ek,
                                                                  const uint8_t* __restrict__ fixed, Q4Consts<double> cst,
                                                                  const double* __restrict__ z,
                                                                  const double* __restrict__ p_old,
@@ -136,6 +187,7 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, con
                                                                  int64_t stride, double* sc, double* partial,
                                                                  unsigned* counters, int64_t pstride) {
   pdl_wait();
+  constexpr int TX = Tl::TX, TY = Tl::TY, NX = Tl::NX, NY = Tl::NY, EX = Tl::EX, EY = Tl::EY;
   __shared__ double su[NY][NX], sv[NY][NX];
   __shared__ double fe[EY][EX][8];
   __shared__ double red[64];
@@ -147,7 +199,7 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, con
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nnx = g.nn[0], nny = g.nn[1];
   const int64_t off = (int64_t)rhs * stride;
-  for (int t = tid; t < NX * NY; t += kThreadsQ4) {
+  for (int t = tid; t < NX * NY; t += Tl::kThreads) {
     const int lx = t % NX, ly = t / NX;
     const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
     double a = 0.0, c = 0.0;
@@ -161,7 +213,7 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, con
     sv[ly][lx] = c;
   }
   __syncthreads();
-  q4_tile_forces<double>(g, Ek, cst, x0, y0, su, sv, fe);
+  q4_tile_forces<double, Tl>(g, Ek, cst, x0, y0, su, sv, fe);
   __syncthreads();
   const int tx = tid % TX, ty = tid / TX;
   const int X = x0 + tx, Y = y0 + ty;
@@ -193,14 +245,36 @@ __global__ void __launch_bounds__(kThreadsQ4) k_fine_q4_cg_direction(Grid g, con
   }
 }
 
+template <class Tl>
+static void fine_q4_cg_direction_launch(const Grid& g, const double* Ek, const uint8_t* fixed,
+                                        const Q4Consts<double>& cst, const double* z, const double* p_old,
+                                        double* p_new, double* q, int nr, int64_t stride, double* sc, double* partial,
+                                        unsigned* counters, int64_t pstride, cudaStream_t s) {
+  const dim3 grid((unsigned)((g.nn[0] + Tl::TX - 1) / Tl::TX), (unsigned)((g.nn[1] + Tl::TY - 1) / Tl::TY),
+                  (unsigned)nr);
+  launch_pdl(k_fine_q4_cg_direction<Tl>, grid, dim3(Tl::kThreads), 0, s, g, Ek, fixed, cst, z, p_old, p_new, q,
+             stride, sc, partial, counters, pstride);
+}
+
 void launch_fine_q4_cg_direction(const Grid& g, const double* Ek, const uint8_t* fixed, const double* Ke0,
                                  const double* z, const double* p_old, double* p_new, double* q, int nr,
                                  int64_t stride, double* sc, double* partial, unsigned* counters, int64_t pstride,
                                  cudaStream_t s) {
   const Q4Consts<double> cst = q4_consts<double>(Ke0);
-  dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)nr);
-  launch_pdl(k_fine_q4_cg_direction, dim3(grid), dim3(kThreadsQ4), 0, s, g, Ek, fixed, cst, z, p_old, p_new, q, stride, sc, partial, counters,
-                                                      pstride);
+  switch (q4_tile_choice(g)) {
+    case 0:
+      fine_q4_cg_direction_launch<Q4TileA>(g, Ek, fixed, cst, z, p_old, p_new, q, nr, stride, sc, partial, counters,
+                                           pstride, s);
+      break;
+    case 1:
+      fine_q4_cg_direction_launch<Q4TileB>(g, Ek, fixed, cst, z, p_old, p_new, q, nr, stride, sc, partial, counters,
+                                           pstride, s);
+      break;
+    default:
+      fine_q4_cg_direction_launch<Q4TileC>(g, Ek, fixed, cst, z, p_old, p_new, q, nr, stride, sc, partial, counters,
+                                           pstride, s);
+      break;
+  }
 }
 
 }  // namespace tobk
