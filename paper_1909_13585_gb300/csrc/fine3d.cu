@@ -2,15 +2,21 @@
 // Algorithm 1 step 3 and Appendix A) for H8 elements: the operator in factored form
 // (h8_element.cuh), element by element.
 //
-// A block owns a 31 x 7 column of nodes in the (x, y) plane and a range of zc node planes, and
+// A block owns a (EX - 1) x 7 column of nodes in the (x, y) plane and a range of zc node planes, and
 // marches up in z one element layer at a time: it keeps two node planes of the input (with a
-// one-node halo) in shared memory, computes the forces of the 32 x 8 elements of the layer (one
+// one-node halo) in shared memory, computes the forces of the EX x 8 elements of the layer (one
 // element per thread), stores them structure-of-arrays in shared memory, and each node thread adds
 // the four contributions from below (finishing its node plane, which is then written out with the
 // smoother / residual / CG update) and keeps the four from above for the next plane.  The factored
 // element needs about 200 FP64 operations instead of the 576 multiply-adds of the dense 24 x 24
 // product, which on GB300 (2 FP64 instructions per clock per SM) sets the speed of the FP64 path.
+// The tile width EX (32, 36 or 44) is chosen per grid to minimise the element slots of the launch:
+// a tile column the grid only partly covers holds its SM slot for the whole march with most of its
+// threads idle (97 nodes across: 31-node tiles leave 4 of the last tile's 31 columns in use, 35-node
+// tiles cover them with 3 tiles; 129 nodes: 43-node tiles exactly).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "device_common.cuh"
 #include "h8_element.cuh"
@@ -19,14 +25,14 @@
 namespace tobk {
 
 namespace {
-constexpr int EX = 32, EY = 8;            // element tile per layer (one element per thread)
-constexpr int TX = EX - 1, TY = EY - 1;   // node tile
-constexpr int PX = EX + 1, PY = EY + 1;   // node-plane tile with halo
-constexpr int kThreads3 = EX * EY;        // 256
+constexpr int EY = 8;                     // element tile rows per layer (one element per thread)
+constexpr int TY = EY - 1;                // node tile rows
+constexpr int PY = EY + 1;                // node-plane tile rows with halo
 constexpr int APPLY_CGDIR = 3;
 
-template <typename T>
+template <typename T, int EX>
 struct H8Smem {
+  static constexpr int PX = EX + 1;  // node-plane tile columns with halo
   T pv[2][3][PY][PX];     // ring of two node planes (components separate)
   T fe[24][EY][EX];       // element forces of the current layer, [c*8 + cz*4 + cy*2 + cx]
   double red[64];
@@ -48,12 +54,13 @@ struct H8Args {
 };
 }  // namespace
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads3) k_fine_h8(Grid g, const T* __restrict__ Ek,
-                                                       const uint8_t* __restrict__ fixed, H8Consts<T> cst, H8Args<T> a,
-                                                       int zc, int nzc, int64_t stride) {
+template <typename T, int MODE, int EX>
+__global__ void __launch_bounds__(EX * EY) k_fine_h8(Grid g, const T* __restrict__ Ek,
+                                                     const uint8_t* __restrict__ fixed, H8Consts<T> cst, H8Args<T> a,
+                                                     int zc, int nzc, int64_t stride) {
+  constexpr int TX = EX - 1, PX = EX + 1, kThreads3 = EX * EY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  H8Smem<T>& S = *reinterpret_cast<H8Smem<T>*>(smem_raw);
+  H8Smem<T, EX>& S = *reinterpret_cast<H8Smem<T, EX>*>(smem_raw);
   const int rhs = blockIdx.z / nzc, chunk = blockIdx.z % nzc;
   double beta = 0.0;
   if (MODE == APPLY_CGDIR) {
@@ -192,35 +199,60 @@ __global__ void __launch_bounds__(kThreads3) k_fine_h8(Grid g, const T* __restri
 
 namespace {
 
+// tile width of the grid: the fewest element slots (tiles x EX x EY per layer; ties: the earlier)
+constexpr int kH8Widths[3] = {32, 36, 44};
+int64_t h8_cols(const Grid& g, int ex) {
+  return (int64_t)((g.nn[0] + ex - 2) / (ex - 1)) * ((g.nn[1] + TY - 1) / TY);
+}
+int h8_width(const Grid& g) {
+  int best = kH8Widths[0];
+  for (int w : kH8Widths)
+    if (h8_cols(g, w) * w < h8_cols(g, best) * best) best = w;
+  return best;
+}
+
 // node planes per block: as many as keep at least two blocks per SM busy for one RHS
-int h8_zc(const Grid& g, int nr) {
-  const int64_t cols = (int64_t)((g.nn[0] + TX - 1) / TX) * ((g.nn[1] + TY - 1) / TY);
+int h8_zc(const Grid& g, int nr, int ex) {
+  const int64_t cols = h8_cols(g, ex);
   int zc = 16;
   while (zc > 4 && cols * ((g.nn[2] + zc - 1) / zc) * nr < 2 * 152) zc /= 2;
   return zc;
 }
 
-template <typename T, int MODE>
-void h8_launch(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int element, const H8Args<T>& a, int nr, int64_t stride,
-               cudaStream_t s) {
+template <typename T, int MODE, int EX>
+void h8_launch_w(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int element, const H8Args<T>& a, int nr,
+                 int64_t stride, cudaStream_t s) {
   static bool configured = false;
-  const size_t smem = sizeof(H8Smem<T>);
+  const size_t smem = sizeof(H8Smem<T, EX>);
   if (!configured) {
-    cudaFuncSetAttribute(k_fine_h8<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fine_h8<T, MODE, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  const int zc = h8_zc(g, nr), nzc = (g.nn[2] + zc - 1) / zc;
-  dim3 grid((unsigned)((g.nn[0] + TX - 1) / TX), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)(nzc * nr));
+  const int zc = h8_zc(g, nr, EX), nzc = (g.nn[2] + zc - 1) / zc;
+  dim3 grid((unsigned)((g.nn[0] + EX - 2) / (EX - 1)), (unsigned)((g.nn[1] + TY - 1) / TY), (unsigned)(nzc * nr));
   note_launch();
-  k_fine_h8<T, MODE><<<grid, kThreads3, smem, s>>>(g, Ek, fixed, h8_consts<T>(nu, element), a, zc, nzc, stride);
+  k_fine_h8<T, MODE, EX><<<grid, EX * EY, smem, s>>>(g, Ek, fixed, h8_consts<T>(nu, element), a, zc, nzc, stride);
+}
+
+template <typename T, int MODE>
+void h8_launch(const Grid& g, const T* Ek, const uint8_t* fixed, double nu, int element, const H8Args<T>& a, int nr,
+               int64_t stride, cudaStream_t s) {
+  switch (h8_width(g)) {
+    case 32: h8_launch_w<T, MODE, 32>(g, Ek, fixed, nu, element, a, nr, stride, s); break;
+    case 36: h8_launch_w<T, MODE, 36>(g, Ek, fixed, nu, element, a, nr, stride, s); break;
+    default: h8_launch_w<T, MODE, 44>(g, Ek, fixed, nu, element, a, nr, stride, s); break;
+  }
 }
 
 }  // namespace
 
 int64_t fine_h8_blocks(const Grid& g) {
-  // the CG-direction launch reduces over this many blocks per RHS (at most, for one RHS)
+  // the CG-direction launch reduces over this many blocks per RHS (at most: one RHS, the smallest
+  // z range, the widest column count of the candidate tiles)
   const int zc = 4;
-  return (int64_t)((g.nn[0] + TX - 1) / TX) * ((g.nn[1] + TY - 1) / TY) * ((g.nn[2] + zc - 1) / zc);
+  int64_t cols = 0;
+  for (int w : kH8Widths) cols = std::max(cols, h8_cols(g, w));
+  return cols * ((g.nn[2] + zc - 1) / zc);
 }
 
 template <typename T>
