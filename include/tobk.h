@@ -70,7 +70,14 @@ typedef enum {
   TOBK_FIELD_U = 0,          /* displacement u [n] */
   TOBK_FIELD_MODES = 1,      /* buckling modes [q][n], phi_i^T K phi_j = delta_ij */
   TOBK_FIELD_ADJOINT = 2,    /* adjoint solutions z_i [q][n] */
-  TOBK_FIELD_ADJOINT_RHS = 3 /* adjoint right-hand sides phi_i^T (grad_u G) phi_i [q][n] */
+  TOBK_FIELD_ADJOINT_RHS = 3, /* adjoint right-hand sides phi_i^T (grad_u G) phi_i [q][n] (with
+                                 consistent_sens: the combined right-hand sides g_i, see
+                                 tobk_compute_sensitivities) */
+  /* consistent sensitivities only (desc.consistent_sens = 1, multilevel path), each [q][n] in the order
+   * and on the scale of the modes: */
+  TOBK_FIELD_FINE_ADJOINT = 4,   /* w_i, K w_i = (K + lambda_i G) phi_i */
+  TOBK_FIELD_COARSE_ADJOINT = 5, /* P c_i, the coarse adjoint prolongated to Omega_1 */
+  TOBK_FIELD_PROLONGATED = 6     /* Psi_i = P psi_i with K phi_i = G Psi_i */
 } tobk_field;
 
 typedef struct {
@@ -117,6 +124,12 @@ typedef struct {
   int eig_gram_tc;   /* 1: the eigensolver's Gram products V^T W run on the tensor cores with FP64
                         accuracy (error-free splitting, see tobk_gram_tc); 0 (default): FP64 CUDA-core
                         products, faster for the eigen levels of the configured workloads */
+  int consistent_sens; /* 1: on the multilevel path, tobk_compute_sensitivities returns the exact
+                          derivative of the multilevel load factors (eq. consistentSensitivity, with the
+                          fine and coarse adjoints; see there); 0 (default): eq. SensitivityLambda applied
+                          to the multilevel pairs, as the paper does.  Requires Sec. 2.1 steps 1-4 as they
+                          stand (no Kaczmarz sweeps, Ritz projections or extra fine steps) and plain
+                          elements; ignored for eig_level = 1, whose pairs are exact */
 } tobk_desc;
 
 /* Elements (Sec. 2).  TOBK_ELEMENT_INCOMPATIBLE: Wilson's quadrilateral (2D) and the hexahedron with
@@ -143,7 +156,7 @@ typedef struct tobk_handle tobk_handle;
 /* Fills *desc with defaults: nu 0.3, E0 1, Emin 1e-6, p 3, 3 levels, eig_level 1, 6 modes, FP64,
  * rtol 1e-8, max_iter 500, omega 0.6, nu_pre = nu_post = 2, eig_tol 1e-8, eig_max_iter 200,
  * max_rhs = num_modes + 4, no Kaczmarz sweeps, no per-level Ritz projection, one fine solve, plain
- * Q4 / H8 elements, FP64 CUDA-core Gram products in the eigensolver.
+ * Q4 / H8 elements, FP64 CUDA-core Gram products in the eigensolver, no consistent sensitivities.
  * Returns TOBK_OK. */
 int tobk_default_desc(tobk_desc* desc);
 
@@ -186,7 +199,19 @@ int tobk_compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info)
  *   K z_i = phi_i^T (grad_u G) phi_i   (eq. AdjointSystem; all q systems in one multi-RHS solve),
  *   dJ/dx_e = -dE_kappa/dx_e u_e^T K_e0 u_e.
  * (eq. SensitivityLambda is the bracket; the factor -1/(phi^T G phi) equals lambda under the K
- * normalisation.)  out_on_device selects device or host output pointers. */
+ * normalisation.)  out_on_device selects device or host output pointers.
+ *
+ * With desc.consistent_sens on the multilevel path, dlambda_dx is instead the exact derivative of the
+ * multilevel load factors lambda_i = R(phi_i), phi_i = K^{-1} G P psi_i (Sec. 2.1; eq. eigResidual and
+ * eq. consistentSensitivity): with y_i = (K + lambda_i G) phi_i, mu_i the coarse load factor of psi_i and
+ * Psi_i = P psi_i,
+ *   K w_i = y_i                                        (fine adjoint, mgPCG)
+ *   (K^l + mu_i G^l) c_i = P^T G w_i, psi_i^T G^l c_i = 0   (coarse adjoint, deflated PCG on Omega_l)
+ *   K z_i = g_i = grad_u [lambda_i phi_i^T G phi_i + (2 w_i - 2 mu_i P c_i)^T G Psi_i]
+ *   d lambda_i / d x_e = -{ dE_kappa [(phi - 2w)^T K_e0 phi - 2 (Pc)^T K_e0 Psi - z^T K_e0 u]
+ *                          + dE_sigma [lambda phi^T G_e0 phi + (2w - 2 mu Pc)^T G_e0 Psi] } / (phi^T G phi).
+ * info reports the largest iteration count of the three solves; TOBK_E_NOT_CONVERGED if one of them
+ * stopped at max_iter. */
 int tobk_compute_sensitivities(tobk_handle* h, double* dlambda_dx, double* dJ_dx, int out_on_device,
                                tobk_solve_info* info);
 

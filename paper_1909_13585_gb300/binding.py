@@ -16,7 +16,8 @@ TOBK_OK, TOBK_E_ARG, TOBK_E_STATE, TOBK_E_NOMEM, TOBK_E_CUDA, TOBK_E_NOT_CONVERG
     TOBK_E_BREAKDOWN, TOBK_E_TIMEOUT, TOBK_E_NONFINITE = range(9)
 TOBK_FP64, TOBK_FP32_VCYCLE = 0, 1
 TOBK_ELEMENT_PLAIN, TOBK_ELEMENT_INCOMPATIBLE = 0, 1
-TOBK_FIELD_U, TOBK_FIELD_MODES, TOBK_FIELD_ADJOINT, TOBK_FIELD_ADJOINT_RHS = range(4)
+TOBK_FIELD_U, TOBK_FIELD_MODES, TOBK_FIELD_ADJOINT, TOBK_FIELD_ADJOINT_RHS, TOBK_FIELD_FINE_ADJOINT, \
+    TOBK_FIELD_COARSE_ADJOINT, TOBK_FIELD_PROLONGATED = range(7)
 
 
 class tobk_desc(C.Structure):
@@ -28,7 +29,7 @@ class tobk_desc(C.Structure):
                 ("eig_max_iter", C.c_int), ("max_rhs", C.c_int), ("eig_inner_iters", C.c_int),
                 ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double),
                 ("kaczmarz_sweeps", C.c_int), ("ritz_levels", C.c_int), ("fine_steps", C.c_int),
-                ("element", C.c_int), ("eig_gram_tc", C.c_int)]
+                ("element", C.c_int), ("eig_gram_tc", C.c_int), ("consistent_sens", C.c_int)]
 
 
 class tobk_solve_info(C.Structure):

@@ -51,6 +51,7 @@ int tobk_default_desc(tobk_desc* d) {
   d->fine_steps = 1;
   d->element = TOBK_ELEMENT_PLAIN;
   d->eig_gram_tc = 0;
+  d->consistent_sens = 0;
   return TOBK_OK;
 }
 
@@ -143,6 +144,13 @@ int tobk_get_field(tobk_handle* h, int which, double* out, int64_t len, int out_
     case TOBK_FIELD_ADJOINT_RHS:
       if (!h->have_sens) return fail(h, TOBK_E_STATE, "no adjoints yet");
       src = h->adj_rhs;
+      need = (int64_t)h->q * n;
+      break;
+    case TOBK_FIELD_FINE_ADJOINT:
+    case TOBK_FIELD_COARSE_ADJOINT:
+    case TOBK_FIELD_PROLONGATED:
+      if (!h->have_sens || !h->have_cs) return fail(h, TOBK_E_STATE, "no consistent sensitivities yet");
+      src = which == TOBK_FIELD_FINE_ADJOINT ? h->cs_W : which == TOBK_FIELD_COARSE_ADJOINT ? h->cs_C : h->cs_Psi;
       need = (int64_t)h->q * n;
       break;
     default:

@@ -67,6 +67,19 @@ struct tobk_handle {
   // (timed-out wait, non-finite input); used for vectors up to gtc_nmax long
   unsigned* gtc_err = nullptr;
   int64_t gtc_nmax = 0;
+  // consistent sensitivities of the multilevel load factors (allocated when desc.consistent_sens is set on
+  // the multilevel path): the coarse modes as the eigensolver returned them (K^l-orthonormal) and their
+  // load factors, the pairing of the normalised fine modes with them (fine mode r = cs_scale[r] times the
+  // solution from coarse mode cs_perm[r]), fine [q][n] fields Psi, w, P c, coarse [q][n_l] CG vectors
+  double *cs_psi = nullptr, *cs_Kpsi = nullptr, *cs_b = nullptr, *cs_c = nullptr, *cs_r = nullptr, *cs_r0 = nullptr,
+         *cs_z = nullptr, *cs_p = nullptr, *cs_ap = nullptr, *cs_t = nullptr;
+  double *cs_Psi = nullptr, *cs_W = nullptr, *cs_C = nullptr;
+  double* cs_scal = nullptr;     // device scalars [tobk::kCsSize]
+  double cs_mu[64] = {0};
+  double cs_scale[64] = {0};
+  int cs_perm[64] = {0};
+  bool cs_ready = false;  // the pairing of the last compute_buckling is recorded
+  bool have_cs = false;   // the last compute_sensitivities took the consistent path
   // small scalars
   double* dscal = nullptr;       // device scratch scalars [256]
   double* hscal = nullptr;       // pinned host scratch [256]
@@ -131,6 +144,11 @@ int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info)
 int setup_stress(tobk_handle* h);  // Gs from u, Galerkin G down to the eigen level
 int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info);
 int compute_sensitivities(tobk_handle* h, double* dlam, double* dJ, bool out_on_device, tobk_solve_info* info);
+// consistent sensitivities (consistent.cu): the fine and coarse adjoints and the u-adjoint right-hand
+// side g [q][n]; then, after K z = g, the derivative of the multilevel load factors into h->dlam
+constexpr int kCsSize = 2240;
+int consistent_adjoint_rhs(tobk_handle* h, double* g_out, tobk_solve_info* info);
+void launch_sens_consistent(tobk_handle* h, const double* pGp);
 // eigensolver at level j: q lowest positive load factors, modes K_j-normalised -> out [q][n_j]
 int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info);
 // Rayleigh-Ritz projection of (K^j, G^j) on span Psi (q columns, stride n_j; Algorithm 2 'R[Psi]'):

@@ -171,6 +171,10 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     rc = eigen_solve(h, l, q, Psi, lam_h, &ei);
     if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
     m_eig = pm.mark();
+    if (h->cs_psi) {  // the coarse pairs, for the consistent sensitivities
+      cudaMemcpyAsync(h->cs_psi, Psi, sizeof(double) * q * h->lv[l].g.n, cudaMemcpyDeviceToDevice, st);
+      for (int i = 0; i < q; ++i) h->cs_mu[i] = lam_h[i];
+    }
     // step 2: Psi^j = I^j_{j+1} Psi^{j+1}, and on each finer level the optional steps of
     // Algorithm 2: Kaczmarz smoothing on K^j + sigma G^j (sigma the smallest load factor known from
     // the level above) and the Rayleigh-Ritz projection of (K^j, G^j) on span Psi^j
@@ -240,6 +244,11 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     }
   }
   cudaMemcpyAsync(h->hscal, h->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
+  const bool record_cs = h->cs_psi && h->eig > 0;
+  if (record_cs) {  // fine mode r = scale[r] x the solution from coarse mode perm[r] (finalize_modes)
+    cudaMemcpyAsync(h->hscal + 64, h->dscal + 640, sizeof(int) * q, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h->hscal + 128, h->dscal + 704, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
+  }
   const int m_end = pm.mark();
   cudaEventRecord(e1, st);
   cudaEventSynchronize(e1);
@@ -252,6 +261,14 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     h->phase_ms[TOBK_PHASE_RQ] = pm.ms(m_solve, m_end);
   }
   for (int i = 0; i < q; ++i) h->lam_host[i] = h->hscal[i];
+  h->cs_ready = record_cs;
+  if (record_cs) {
+    const int* perm = (const int*)(h->hscal + 64);
+    for (int i = 0; i < q; ++i) {
+      h->cs_perm[i] = perm[i];
+      h->cs_scale[i] = h->hscal[128 + i];
+    }
+  }
   if (lambda)
     for (int i = 0; i < q; ++i) lambda[i] = h->lam_host[i];
   float ms = 0.f;
@@ -264,6 +281,7 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
   }
   h->have_modes = true;
   h->have_sens = false;
+  h->have_cs = false;
   return rc;
 }
 
@@ -380,6 +398,14 @@ __global__ void k_adjoint_gather(Grid g, const uint8_t* __restrict__ fixed, cons
   }
 }
 
+void launch_adjoint_gather(const Grid& g, const uint8_t* fixed, const double* sgp, const double* dN, double* b,
+                           cudaStream_t st) {
+  if (g.dim == 2)
+    ::tobk::note_launch(), k_adjoint_gather<2><<<nblk(g.nnode), 256, 0, st>>>(g, fixed, sgp, dN, b);
+  else
+    ::tobk::note_launch(), k_adjoint_gather<3><<<nblk(g.nnode), 256, 0, st>>>(g, fixed, sgp, dN, b);
+}
+
 // per element: dJ and, for every mode, dlambda (eq. SensitivityLambda with -1/(phi^T G phi))
 template <int DIM>
 __global__ void k_sensitivities(Grid g, int q, const double* __restrict__ u, const double* __restrict__ modes,
@@ -469,8 +495,16 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
+  // consistent sensitivities of the multilevel pairs: fine and coarse adjoints, combined right-hand sides
+  const bool cons = h->cs_ready && h->cs_psi;
+  tobk_solve_info ci{};
+  int rc_c = TOBK_OK;
+  if (cons) {
+    rc_c = consistent_adjoint_rhs(h, h->adj_rhs, &ci);
+    if (rc_c && rc_c != TOBK_E_NOT_CONVERGED) return rc_c;
+  }
   // adjoint right-hand sides, one mode at a time through the element Gauss-point scratch
-  for (int i = 0; i < q; ++i) {
+  for (int i = 0; i < (cons ? 0 : q); ++i) {
     const double* phi = h->modes + (size_t)i * n;
     double* b = h->adj_rhs + (size_t)i * n;
     if (h->Gc0) {
@@ -502,12 +536,14 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
   apply_G_level(h, 0, h->modes, GP, q, n);
   double* pGp = h->dscal + 960;
   launch_coldots(h->modes, GP, q, n, n, pGp, h->gram_partial, st);
+  const int qs = cons ? 0 : q;  // the consistent path leaves dJ alone to this kernel
   if (g.dim == 2)
-    ::tobk::note_launch(), k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->Gc0, h->d_Ke0, h->dEk,
+    ::tobk::note_launch(), k_sensitivities<2><<<nblk(g.m, 128), 128, 0, st>>>(g, qs, h->u, h->modes, h->adj, h->Gs0, h->Gc0, h->d_Ke0, h->dEk,
                                                        h->dEs, h->lam, pGp, h->dlam, h->dJ);
   else
-    ::tobk::note_launch(), k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, q, h->u, h->modes, h->adj, h->Gs0, h->Gc0, h->d_Ke0, h->dEk, h->dEs,
+    ::tobk::note_launch(), k_sensitivities<3><<<nblk(g.m, 64), 64, 0, st>>>(g, qs, h->u, h->modes, h->adj, h->Gs0, h->Gc0, h->d_Ke0, h->dEk, h->dEs,
                                                      h->lam, pGp, h->dlam, h->dJ);
+  if (cons) launch_sens_consistent(h, pGp);
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (dlam_out) cudaMemcpyAsync(dlam_out, h->dlam, sizeof(double) * q * g.m, kind, st);
   if (dJ_out) cudaMemcpyAsync(dJ_out, h->dJ, sizeof(double) * g.m, kind, st);
@@ -522,9 +558,14 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
   if (info) {
     *info = si;
     info->time_ms = ms;
+    if (cons) {
+      info->iterations = std::max(si.iterations, ci.iterations);
+      info->converged = si.converged && ci.converged;
+    }
   }
   h->have_sens = true;
-  return rc;
+  h->have_cs = cons;
+  return rc ? rc : rc_c;
 }
 
 }  // namespace tobk

@@ -206,6 +206,16 @@ static void layout(tobk_handle* h, Arena& a) {
     h->gtc_nmax = std::max(ne, nf);
     h->gtc_err = a.take<unsigned>(2);
   }
+  if (h->desc.consistent_sens && h->eig > 0) {
+    const int64_t nl = h->lv[h->eig].g.n;
+    for (double** v : {&h->cs_psi, &h->cs_Kpsi, &h->cs_b, &h->cs_c, &h->cs_r, &h->cs_r0, &h->cs_z, &h->cs_p,
+                       &h->cs_ap, &h->cs_t})
+      *v = a.take<double>((size_t)q * nl);
+    h->cs_Psi = a.take<double>((size_t)q * nf);
+    h->cs_W = a.take<double>((size_t)q * nf);
+    h->cs_C = a.take<double>((size_t)q * nf);
+    h->cs_scal = a.take<double>(kCsSize);
+  }
   if (h->desc.kaczmarz_sweeps > 0 && h->eig > 0) {
     const int d = h->dim;
     h->kz_S = a.take<double>((size_t)(d == 2 ? 9 : 27) * d * d * g.nnode);
@@ -232,6 +242,10 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   if (d->element != TOBK_ELEMENT_PLAIN && d->element != TOBK_ELEMENT_INCOMPATIBLE) return TOBK_E_ARG;
   if (d->element != TOBK_ELEMENT_PLAIN && solve_only) return TOBK_E_ARG;  // batches: plain elements only
   if (d->eig_gram_tc != 0 && d->eig_gram_tc != 1) return TOBK_E_ARG;
+  if (d->consistent_sens != 0 && d->consistent_sens != 1) return TOBK_E_ARG;
+  if (d->consistent_sens && d->eig_level > 1 &&
+      (d->kaczmarz_sweeps > 0 || d->ritz_levels || d->fine_steps > 1 || d->element != TOBK_ELEMENT_PLAIN))
+    return TOBK_E_ARG;  // the derivative follows Sec. 2.1 steps 1-4 with plain elements only
   for (int a = 0; a < d->dim; ++a) {
     if (d->nel[a] < 1) return TOBK_E_ARG;
     if (d->nel[a] % (1 << (d->mg_levels - 1)) != 0) return TOBK_E_ARG;
