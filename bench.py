@@ -87,7 +87,8 @@ def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush, 
         lam, i2 = s.compute_buckling()
         info["eigen_ms"] = s.phase_read()["eigen"]
         _, _, i3 = s.compute_sensitivities(dlam_d, dJ_d)
-        info.update(la_iters=i1["iterations"], buckling_iters=i2["iterations"], adjoint_iters=i3["iterations"])
+        info.update(la_iters=i1["iterations"], buckling_iters=i2["iterations"], adjoint_iters=i3["iterations"],
+                    sensitivities_ms=i3["time_ms"])
         info["_lam"] = lam
 
     for _ in range(warmup):
@@ -101,15 +102,19 @@ def measure_form(pkg, torch, name, precision, fused, steps, warmup, dev, flush, 
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-    units = p.num_dofs * rhs_per_step(p, fused)
+    # the consistent sensitivities solve the q fine adjoints K w = y besides (their coarse adjoints are
+    # on the eigen level and not counted)
+    extra = p.num_modes if overrides.get("consistent_sens") else 0
+    units = p.num_dofs * (rhs_per_step(p, fused) + extra)
     lam = info.pop("_lam")
     if outputs is not None:
         outputs.update(u=s.get_field(pkg.TOBK_FIELD_U), lam=np.array(lam), dlam=dlam_d.cpu().numpy(),
                        dJ=dJ_d.cpu().numpy())
     s.close()
     return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "dofs": p.num_dofs,
-            "rhs_per_step": rhs_per_step(p, fused), "precision": "fp64" if precision == 0 else "fp32_vcycle",
+            "rhs_per_step": rhs_per_step(p, fused) + extra, "precision": "fp64" if precision == 0 else "fp32_vcycle",
             "fused_load_adjoint": bool(fused), "steps": steps, "warmup": warmup,
+            **({"consistent_sensitivities": True} if extra else {}),
             **({"smoother": "damped_jacobi", "omega": overrides.get("omega", 0.6)} if overrides.get("smoother") == 0
                else {}), **info}
 
@@ -596,6 +601,13 @@ def ours(args):
                                                                  fs, fw, dev, flush, smoother=0, omega=0.6)
         forms["column480x160_fp64_tensor_core_gram"] = measure_form(pkg, torch, "column480x160", pkg.TOBK_FP64, False,
                                                                     fs, fw, dev, flush, eig_gram_tc=1)
+        ocons, oplain = {}, {}
+        forms["column480x160_fp64_consistent_sensitivities"] = measure_form(
+            pkg, torch, "column480x160", pkg.TOBK_FP64, False, fs, fw, dev, flush, outputs=ocons, consistent_sens=1)
+        measure_form(pkg, torch, "column480x160", pkg.TOBK_FP64, False, 1, 1, dev, flush, outputs=oplain)
+        forms["column480x160_fp64_consistent_sensitivities"]["difference_from_eq_SensitivityLambda"] = \
+            output_errors(ocons, oplain)
+        del ocons, oplain
         forms["column60x20_fp64_exact_lba"] = measure_form(pkg, torch, "column60x20", pkg.TOBK_FP64, False,
                                                            fs, fw, dev, flush)
         o64, o32 = {}, {}

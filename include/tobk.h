@@ -210,8 +210,8 @@ int tobk_compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info)
  *   K z_i = g_i = grad_u [lambda_i phi_i^T G phi_i + (2 w_i - 2 mu_i P c_i)^T G Psi_i]
  *   d lambda_i / d x_e = -{ dE_kappa [(phi - 2w)^T K_e0 phi - 2 (Pc)^T K_e0 Psi - z^T K_e0 u]
  *                          + dE_sigma [lambda phi^T G_e0 phi + (2w - 2 mu Pc)^T G_e0 Psi] } / (phi^T G phi).
- * info reports the largest iteration count of the three solves; TOBK_E_NOT_CONVERGED if one of them
- * stopped at max_iter. */
+ * info reports the largest iteration count of the three solves and, in status_detail, the coarse
+ * adjoint's CG iterations; TOBK_E_NOT_CONVERGED if one of them stopped at max_iter. */
 int tobk_compute_sensitivities(tobk_handle* h, double* dlambda_dx, double* dJ_dx, int out_on_device,
                                tobk_solve_info* info);
 

@@ -561,6 +561,7 @@ int compute_sensitivities(tobk_handle* h, double* dlam_out, double* dJ_out, bool
     if (cons) {
       info->iterations = std::max(si.iterations, ci.iterations);
       info->converged = si.converged && ci.converged;
+      info->status_detail = ci.status_detail;
     }
   }
   h->have_sens = true;
