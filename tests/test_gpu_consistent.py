@@ -107,3 +107,46 @@ def test_consistent_on_exact_path_is_sensitivity_lambda_and_invalid_combinations
         with pytest.raises(pkg.TobkError) as ei:
             pkg.Solver(q, consistent_sens=1, **bad)
         assert ei.value.code == pkg.TOBK_E_ARG
+
+
+def _ml_lambda(pkg, p, x):
+    s = pkg.Solver(p)
+    s.set_densities(x)
+    s.solve_equilibrium()
+    lam, _ = s.compute_buckling()
+    s.close()
+    return lam
+
+
+@pytest.mark.parametrize("name", ["column480x160", "cantilever48x24x24"])
+def test_consistent_sensitivities_are_the_derivative_of_the_gpu_load_factors_full_size(name):
+    """At the benchmark's size, along a random direction d (relative to x, all elements), the
+    consistent derivative equals the central difference of the GPU's own multilevel load factors
+    (step h = 1e-4: rounding and solver tolerance give ~1e-6 of the difference), and eq.
+    SensitivityLambda of the same pairs does not."""
+    torch, pkg = require_gpu()
+    if name == "column480x160":
+        p = synthetic.config(name)
+    else:
+        p = synthetic.cantilever_3d(48, 24, 24, seed=34, radius=2, volfrac=0.4, mg_levels=4, eig_level=2, num_modes=6)
+    lam, dlam, _, info, _ = _gpu(p)
+    assert info["converged"] == 1
+    s = pkg.Solver(p)
+    s.solve_equilibrium()
+    s.compute_buckling()
+    plain, _, _ = s.compute_sensitivities()
+    s.close()
+    rng = np.random.default_rng(35)
+    d = rng.standard_normal(p.x.size) * np.minimum(p.x, 1.0 - p.x)  # x +- h d stays inside (0, 1)
+    h = 1e-4
+    lp = _ml_lambda(pkg, p, p.x + h * d)
+    lm = _ml_lambda(pkg, p, p.x - h * d)
+    fd = (lp - lm) / (2 * h)
+    ok = _gaps(lam) > 1e-3  # modes that cannot swap order under the perturbation
+    assert ok.sum() >= p.num_modes // 2, lam
+    worst_plain = 0.0
+    for i in np.flatnonzero(ok):
+        scale = np.abs(dlam[i]) @ np.abs(d)
+        assert abs(fd[i] - dlam[i] @ d) <= 1e-5 * scale, (i, fd[i], dlam[i] @ d, plain[i] @ d)
+        worst_plain = max(worst_plain, abs(fd[i] - plain[i] @ d) / scale)
+    assert worst_plain > 1e-3
