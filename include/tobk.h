@@ -421,8 +421,8 @@ int tobk_unet_train_step(tobk_unet* net, const float* x, const double* f, const 
  * exits.  Every call on a device shares that array: calls whose kernels may overlap on the GPU
  * (different streams without ordering) race and must not be issued.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture begins.  Later calls whose stream is not being
- * captured look the address up again, so that it stays valid after a device reset.
+ * later calls look it up again unless their stream is in capture mode, so that the address stays
+ * valid after a device reset.
  * Errors: TOBK_E_ARG (null pointer, bad dim or sizes, nrhs out of range, the material checks of
  * tobk_create: -1 < nu < 0.5, E0 > 0, Emin > 0, penal >= 1), TOBK_E_CUDA. */
 int tobk_residual_noalloc(const tobk_desc* desc, const double* x, const uint8_t* fixed, const double* B,
