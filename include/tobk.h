@@ -420,11 +420,13 @@ int tobk_unet_train_step(tobk_unet* net, const float* x, const double* f, const 
  * the library's own device memory, which every GPU that loads the library keeps until the process
  * exits.  Every call on a device shares that array: calls whose kernels may overlap on the GPU
  * (different streams without ordering) race and must not be issued.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress, with that device current);
- * later calls look it up again unless their stream is in capture mode, so that the address stays
- * valid after a device reset.
+ * device does the set-up: it looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current), so that first call should come before any stream capture begins.  Later calls
+ * look the address up again unless their stream is in capture mode, so that it stays valid after a
+ * device reset.
  * Errors: TOBK_E_ARG (null pointer, bad dim or sizes, nrhs out of range, the material checks of
- * tobk_create: -1 < nu < 0.5, E0 > 0, Emin > 0, penal >= 1), TOBK_E_CUDA. */
+ * tobk_create: -1 < nu < 0.5, E0 > 0, Emin > 0, penal >= 1), TOBK_E_CUDA; tobk_last_error(NULL), on the
+ * calling thread, then names the check that failed. */
 int tobk_residual_noalloc(const tobk_desc* desc, const double* x, const uint8_t* fixed, const double* B,
                           const double* X, int nrhs, double* relres, void* cuda_stream);
 

@@ -13,6 +13,12 @@ using namespace tobk;
 
 static thread_local std::string g_create_error;
 
+namespace tobk {
+// message of a failed call that has no handle (tobk_create, tobk_residual_noalloc), read through
+// tobk_last_error(NULL) on the same thread
+void set_handleless_error(const char* msg) { g_create_error = msg; }
+}  // namespace tobk
+
 #define TOBK_GUARD(h)                                  \
   do {                                                 \
     if (!(h)) return TOBK_E_ARG;                       \

@@ -20,6 +20,8 @@
 
 namespace tobk {
 
+void set_handleless_error(const char* msg);
+
 constexpr int kNoAllocMaxRhs = 16;    // largest nrhs accepted
 constexpr int kNoAllocBlocks = 1024;  // fixed grid width (grid-stride loop over nodes)
 
@@ -138,21 +140,28 @@ void launch_noalloc(const tobk_desc& d, const double* x, const uint8_t* fixed, c
 extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, const uint8_t* fixed, const double* B,
                                      const double* X, int nrhs, double* relres, void* cuda_stream) {
   using namespace tobk;
-  if (!desc || !x || !fixed || !B || !X || !relres) return TOBK_E_ARG;
-  if (desc->dim != 2 && desc->dim != 3) return TOBK_E_ARG;
+  auto reject = [](int code, const char* msg) {
+    set_handleless_error(msg);
+    return code;
+  };
+  if (!desc || !x || !fixed || !B || !X || !relres) return reject(TOBK_E_ARG, "tobk_residual_noalloc: null pointer");
+  if (desc->dim != 2 && desc->dim != 3) return reject(TOBK_E_ARG, "tobk_residual_noalloc: dim must be 2 or 3");
   for (int a = 0; a < desc->dim; ++a)
-    if (desc->nel[a] < 1) return TOBK_E_ARG;
+    if (desc->nel[a] < 1) return reject(TOBK_E_ARG, "tobk_residual_noalloc: nel must be >= 1 on every axis");
   // the material checks of tobk_create: a Poisson ratio of 1/2 or more makes the 3D Lame constant
   // infinite, a non-positive modulus or p < 1 leaves K(x) without meaning
   if (!(desc->nu > -1.0 && desc->nu < 0.5) || !(desc->E0 > 0.0) || !(desc->Emin > 0.0) || !(desc->penal >= 1.0))
-    return TOBK_E_ARG;
-  if (desc->element != TOBK_ELEMENT_PLAIN && desc->element != TOBK_ELEMENT_INCOMPATIBLE) return TOBK_E_ARG;
+    return reject(TOBK_E_ARG, "tobk_residual_noalloc: material parameters out of range");
+  if (desc->element != TOBK_ELEMENT_PLAIN && desc->element != TOBK_ELEMENT_INCOMPATIBLE)
+    return reject(TOBK_E_ARG, "tobk_residual_noalloc: unknown element");
   // the built-in scratch holds kNoAllocMaxRhs right-hand sides; larger blocks are rejected
-  if (nrhs < 1 || nrhs > kNoAllocMaxRhs) return TOBK_E_ARG;
+  if (nrhs < 1 || nrhs > kNoAllocMaxRhs)
+    return reject(TOBK_E_ARG, "tobk_residual_noalloc: nrhs must be between 1 and 16 (the size of its built-in "
+                              "scratch)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
-    return TOBK_E_CUDA;
+    return reject(TOBK_E_CUDA, "tobk_residual_noalloc: cudaGetDevice failed");
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
@@ -160,7 +169,7 @@ extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, con
   double* partial = nullptr;
   unsigned* counters = nullptr;
   if (scratch_for_device(dev, cs == cudaStreamCaptureStatusNone, &partial, &counters) != TOBK_OK) {
-    return TOBK_E_CUDA;
+    return reject(TOBK_E_CUDA, "tobk_residual_noalloc: cudaGetSymbolAddress of the scratch failed");
   }
   // the arrival counters must start at zero (an interrupted earlier call could have left them set)
   cudaMemsetAsync(counters, 0, sizeof(unsigned) * kNoAllocMaxRhs, s);
@@ -170,7 +179,7 @@ extern "C" int tobk_residual_noalloc(const tobk_desc* desc, const double* x, con
     launch_noalloc<3>(*desc, x, fixed, B, X, nrhs, relres, partial, counters, s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    return TOBK_E_CUDA;
+    return reject(TOBK_E_CUDA, "tobk_residual_noalloc: kernel launch failed");
   }
   return TOBK_OK;
 }

@@ -144,3 +144,4 @@ def test_noalloc_rejects_too_many_rhs():
     rc = lib.tobk_residual_noalloc(C.byref(d), x.data_ptr(), fixed.data_ptr(), buf.data_ptr(), buf.data_ptr(),
                                    17, out.data_ptr(), None)
     assert rc == binding.TOBK_E_ARG
+    assert b"between 1 and 16" in lib.tobk_last_error(None)
