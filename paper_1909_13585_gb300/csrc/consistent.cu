@@ -340,37 +340,67 @@ static int coarse_adjoint(tobk_handle* h, const double* b, double* c, int* iters
   cudaStreamSynchronize(st);
   double tol2[64];
   for (int r = 0; r < q; ++r) tol2[r] = h->desc.rtol * h->desc.rtol * hs[r];
-  const int maxit = h->desc.max_iter;
-  int it = 0;
   bool done = true;  // nothing to do when every projected right-hand side is 0
   for (int r = 0; r < q; ++r)
     if (hs[r] > 0.0) done = false;
-  while (!done && it < maxit) {
-    ++it;
-    apply_K_level(h, l, P, AP, q, nl);
-    apply_G_level(h, l, P, GP, q, nl);
-    ::tobk::note_launch(), k_cols_axpy<<<grid, 256, 0, st>>>(AP, GP, mu_dev, AP, nl);
-    project_r(AP);
-    launch_coldots(P, AP, q, nl, nl, pq, h->gram_partial, st);
-    cudaMemcpyAsync(R0, R, sizeof(double) * q * nl, cudaMemcpyDeviceToDevice, st);
-    ::tobk::note_launch(), k_pcg_step<<<grid, 256, 0, st>>>(c, R, P, AP, rz_a, pq, nl);
-    if (it % 2 == 0 || it == maxit) {  // the exit test (a host synchronisation) every second iteration
-      launch_coldots(R, R, q, nl, nl, rr, h->gram_partial, st);
-      cudaMemcpyAsync(hs, rr, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
-      done = true;
-      for (int r = 0; r < q; ++r) {
-        if (!std::isfinite(hs[r])) return fail(h, TOBK_E_NONFINITE, "coarse adjoint: non-finite residual");
-        if (hs[r] > tol2[r]) done = false;
-      }
-      if (done) break;
+  // Two iterations and the exit test (||r_r||^2 into the pinned host scalars) per replay of a CUDA graph
+  // captured on first use; launched directly while profiling or on the legacy default stream.
+  auto enqueue_pair = [&]() {
+    for (int k = 0; k < 2; ++k) {
+      double* rz_old = k == 0 ? rz_a : rz_b;
+      double* rz_new = k == 0 ? rz_b : rz_a;
+      apply_K_level(h, l, P, AP, q, nl);
+      apply_G_level(h, l, P, GP, q, nl);
+      ::tobk::note_launch(), k_cols_axpy<<<grid, 256, 0, st>>>(AP, GP, mu_dev, AP, nl);
+      project_r(AP);
+      launch_coldots(P, AP, q, nl, nl, pq, h->gram_partial, st);
+      cudaMemcpyAsync(R0, R, sizeof(double) * q * nl, cudaMemcpyDeviceToDevice, st);
+      ::tobk::note_launch(), k_pcg_step<<<grid, 256, 0, st>>>(c, R, P, AP, rz_old, pq, nl);
+      apply_vcycle(h, l, q, R, Z);
+      project_s(Z);
+      launch_coldots(R, Z, q, nl, nl, rz_new, h->gram_partial, st);
+      launch_coldots(R0, Z, q, nl, nl, rz_m, h->gram_partial, st);
+      ::tobk::note_launch(), k_pcg_dir<<<grid, 256, 0, st>>>(P, Z, rz_new, rz_m, rz_old, nl);
     }
-    apply_vcycle(h, l, q, R, Z);
-    project_s(Z);
-    launch_coldots(R, Z, q, nl, nl, rz_b, h->gram_partial, st);
-    launch_coldots(R0, Z, q, nl, nl, rz_m, h->gram_partial, st);
-    ::tobk::note_launch(), k_pcg_dir<<<grid, 256, 0, st>>>(P, Z, rz_b, rz_m, rz_a, nl);
-    std::swap(rz_a, rz_b);
+    launch_coldots(R, R, q, nl, nl, rr, h->gram_partial, st);
+    cudaMemcpyAsync(hs, rr, sizeof(double) * q, cudaMemcpyDeviceToHost, st);
+  };
+  const bool graphs = !h->prof_on && st != nullptr && h->use_graphs;
+  const uint64_t key = (1ull << 40) | (uint64_t)l;  // beside the CG pairs' (level, RHS, precision) keys
+  const int maxit = h->desc.max_iter;
+  int it = 0;
+  while (!done && it < maxit) {
+    if (graphs) {
+      auto g = h->cg_graphs.find(key);
+      if (g == h->cg_graphs.end()) {
+        cudaGraph_t gr = nullptr;
+        const long long c0 = g_launch_count.load();
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+          return check_cuda(h, "coarse adjoint capture");
+        enqueue_pair();
+        if (cudaStreamEndCapture(st, &gr) != cudaSuccess) return check_cuda(h, "coarse adjoint capture");
+        const long long kernels = g_launch_count.load() - c0;
+        g_launch_count.fetch_sub(kernels);
+        cudaGraphExec_t ex = nullptr;
+        if (cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) {
+          cudaGraphDestroy(gr);
+          return check_cuda(h, "coarse adjoint instantiate");
+        }
+        cudaGraphDestroy(gr);
+        g = h->cg_graphs.emplace(key, tobk_handle::CGGraph{ex, kernels}).first;
+      }
+      cudaGraphLaunch(g->second.exec, st);
+      g_launch_count.fetch_add(g->second.kernels);
+    } else {
+      enqueue_pair();
+    }
+    it += 2;
+    cudaStreamSynchronize(st);
+    done = true;
+    for (int r = 0; r < q; ++r) {
+      if (!std::isfinite(hs[r])) return fail(h, TOBK_E_NONFINITE, "coarse adjoint: non-finite residual");
+      if (hs[r] > tol2[r]) done = false;
+    }
   }
   // c += sum_{j != perm r} psi_j (psi_j^T b_r) / (1 - mu_r / mu_j)
   std::vector<double> c0((size_t)q * q), cf((size_t)q * q, 0.0);

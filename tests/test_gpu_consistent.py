@@ -150,3 +150,22 @@ def test_consistent_sensitivities_are_the_derivative_of_the_gpu_load_factors_ful
         assert abs(fd[i] - dlam[i] @ d) <= 1e-5 * scale, (i, fd[i], dlam[i] @ d, plain[i] @ d)
         worst_plain = max(worst_plain, abs(fd[i] - plain[i] @ d) / scale)
     assert worst_plain > 1e-3
+
+
+def test_consistent_sensitivities_graph_replay_is_bit_identical():
+    """On a caller's stream the coarse adjoint's iteration pairs replay a captured CUDA graph; on the
+    legacy stream they are launched directly.  Same kernels in the same order: the same bits."""
+    torch, pkg = require_gpu()
+    p = CASES[0][1]()
+    out = []
+    for stream in (None, torch.cuda.Stream()):
+        s = pkg.Solver(p, stream=stream, consistent_sens=1)
+        s.solve_equilibrium()
+        s.compute_buckling()
+        for _ in range(2):  # the second call replays the graph captured by the first
+            dlam, _, info = s.compute_sensitivities()
+        torch.cuda.synchronize()
+        out.append((dlam.copy(), info["status_detail"]))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] > 0
