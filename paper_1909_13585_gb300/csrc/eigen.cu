@@ -57,52 +57,57 @@ __global__ void k_scatter_sym(const double* C, int rows, int cols, int col0, dou
   H[(size_t)(col0 + j) * ld + i] = v;
 }
 
-// Cholesky M = R^T R of a small SPD matrix (k <= 32) and Rinv = R^{-1} (upper triangular).
-// info[0] is set to 1 when a pivot is not positive (and left unchanged otherwise).
-__global__ void k_small_cholinv(const double* M, int k, double* Rinv, double* info) {
+// Cholesky M = R^T R of a small SPD matrix (k <= 32) and Rinv = R^{-1} (upper triangular), by one
+// warp.  Lower factor L = R^T, right-looking: at pivot j one rsqrt of the updated diagonal gives both
+// L_jj = d rsqrt(d) and 1 / L_jj, lane i > j scales its entry of column j and updates its row of the
+// trailing block (independent multiply-adds, no dependent dot-product chain).  The inverse Linv is
+// formed by forward substitution with lane c owning column c (rows updated right-looking, so a lane
+// never waits for another).  A chain of FP64 operations on one SM is latency-bound; this keeps it at
+// about 2k dependent steps.  info[0] is set to 1 when a pivot is not positive (left unchanged
+// otherwise).
+__global__ void __launch_bounds__(32) k_small_cholinv(const double* M, int k, double* Rinv, double* info) {
   pdl_wait();
-  __shared__ double L[32 * 32];
-  __shared__ double Li[32 * 32];
-  __shared__ int bad;
+  __shared__ double A[32][33];   // lower triangle of M, overwritten by L
+  __shared__ double B[32][33];   // B[r][c]: Linv, column c in lane c
+  __shared__ double dinv[32];
   const int t = threadIdx.x;
-  if (t == 0) bad = 0;
-  for (int q = t; q < k * k; q += blockDim.x) {
-    L[q] = M[q];
-    Li[q] = 0.0;
-  }
-  __syncthreads();
-  // lower Cholesky L L^T = M (so R = L^T)
+  if (t < k)
+    for (int l = 0; l <= t; ++l) A[t][l] = M[t * k + l];
+  __syncwarp();
+  bool bad = false;
   for (int j = 0; j < k; ++j) {
-    if (t == 0) {
-      double d = L[j * k + j];
-      for (int p = 0; p < j; ++p) d -= L[j * k + p] * L[j * k + p];
-      if (!(d > 0.0)) {
-        bad = 1;
-        d = 1e-300;
-      }
-      L[j * k + j] = sqrt(d);
+    double d = A[j][j];
+    if (!(d > 0.0)) {
+      bad = true;
+      d = 1e-300;
     }
-    __syncthreads();
-    for (int i = j + 1 + t; i < k; i += blockDim.x) {
-      double s = L[i * k + j];
-      for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
-      L[i * k + j] = s / L[j * k + j];
+    const double r = rsqrt(d);
+    double lij = 0.0;
+    if (t > j && t < k) lij = A[t][j] * r;
+    __syncwarp();
+    if (t > j && t < k) A[t][j] = lij;
+    if (t == j) {
+      A[j][j] = d * r;
+      dinv[j] = r;
     }
-    __syncthreads();
+    __syncwarp();
+    if (t > j && t < k)
+      for (int l = j + 1; l <= t; ++l) A[t][l] -= lij * A[l][j];
+    __syncwarp();
   }
-  // Linv (lower) by forward substitution, one column per thread
-  for (int c = t; c < k; c += blockDim.x) {
-    for (int i = 0; i < k; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int p = c; p < i; ++p) s -= L[i * k + p] * Li[p * k + c];
-      Li[i * k + c] = (i < c) ? 0.0 : s / L[i * k + i];
+  if (t < k) {
+    for (int r = 0; r < k; ++r) B[r][t] = r == t ? 1.0 : 0.0;
+    for (int i = t; i < k; ++i) {  // rows above t stay 0
+      const double li = B[i][t] * dinv[i];
+      B[i][t] = li;
+      for (int r = i + 1; r < k; ++r) B[r][t] -= A[r][i] * li;
     }
   }
-  __syncthreads();
+  __syncwarp();
   // Rinv = (L^T)^{-1} = (Linv)^T
-  for (int q = t; q < k * k; q += blockDim.x) {
+  for (int q = t; q < k * k; q += 32) {
     const int i = q / k, j = q % k;
-    Rinv[q] = Li[j * k + i];
+    Rinv[q] = B[j][i];
   }
   if (t == 0 && bad) info[0] = 1.0;
 }
@@ -309,7 +314,7 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
       eig_gram(h, src, nadd, KW, nadd, n, sd, M);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_DENSE, (double)nadd);
-      launch_pdl(k_small_cholinv, dim3(1), dim3(256), 0, st, M, nadd, Rinv, sinfo);
+      launch_pdl(k_small_cholinv, dim3(1), dim3(32), 0, st, M, nadd, Rinv, sinfo);
       prof_end(h);
       prof_begin(h, TOBK_KC_EIGEN_BLOCK, (double)nadd * n);
       launch_combine(src, nadd, Rinv, nadd, nadd, 1.0, 0.0, dst, n, sd, st);
@@ -491,7 +496,7 @@ int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host) {
   for (int pass = 0; pass < 2; ++pass) {
     apply_K_level(h, j, Psi, KW, q, n);
     eig_gram(h, Psi, q, KW, q, n, n, M);
-    launch_pdl(k_small_cholinv, dim3(1), dim3(256), 0, st, M, q, Rinv, sinfo);
+    launch_pdl(k_small_cholinv, dim3(1), dim3(32), 0, st, M, q, Rinv, sinfo);
     launch_combine(Psi, q, Rinv, q, q, 1.0, 0.0, Tb, n, n, st);
     cudaMemcpyAsync(Psi, Tb, sizeof(double) * q * n, cudaMemcpyDeviceToDevice, st);
   }
