@@ -130,6 +130,11 @@ typedef struct {
                           to the multilevel pairs, as the paper does.  Requires Sec. 2.1 steps 1-4 as they
                           stand (no Kaczmarz sweeps, Ritz projections or extra fine steps) and plain
                           elements; ignored for eig_level = 1, whose pairs are exact */
+  int early_fine;    /* 1 (default): on the multilevel path of Sec. 2.1 (no Kaczmarz sweeps, Ritz projections
+                        or extra fine steps) and on a stream of the caller's, the fine systems K phi =
+                        G P psi of the coarse pairs that meet eig_tol while the eigensolver still iterates
+                        on others are solved beside it (a second stream, the same rtol); 0: all q after
+                        the eigensolve.  The load factors agree to the solver tolerances, not bit for bit */
 } tobk_desc;
 
 /* Elements (Sec. 2).  TOBK_ELEMENT_INCOMPATIBLE: Wilson's quadrilateral (2D) and the hexahedron with
@@ -156,7 +161,8 @@ typedef struct tobk_handle tobk_handle;
 /* Fills *desc with defaults: nu 0.3, E0 1, Emin 1e-6, p 3, 3 levels, eig_level 1, 6 modes, FP64,
  * rtol 1e-8, max_iter 500, omega 0.6, nu_pre = nu_post = 2, eig_tol 1e-8, eig_max_iter 200,
  * max_rhs = num_modes + 4, no Kaczmarz sweeps, no per-level Ritz projection, one fine solve, plain
- * Q4 / H8 elements, FP64 CUDA-core Gram products in the eigensolver, no consistent sensitivities.
+ * Q4 / H8 elements, FP64 CUDA-core Gram products in the eigensolver, no consistent sensitivities, the early
+ * fine solve on.
  * Returns TOBK_OK. */
 int tobk_default_desc(tobk_desc* desc);
 

@@ -29,7 +29,7 @@ class tobk_desc(C.Structure):
                 ("eig_max_iter", C.c_int), ("max_rhs", C.c_int), ("eig_inner_iters", C.c_int),
                 ("fuse_load_adjoint", C.c_int), ("smoother", C.c_int), ("cheb_ratio", C.c_double),
                 ("kaczmarz_sweeps", C.c_int), ("ritz_levels", C.c_int), ("fine_steps", C.c_int),
-                ("element", C.c_int), ("eig_gram_tc", C.c_int), ("consistent_sens", C.c_int)]
+                ("element", C.c_int), ("eig_gram_tc", C.c_int), ("consistent_sens", C.c_int), ("early_fine", C.c_int)]
 
 
 class tobk_solve_info(C.Structure):

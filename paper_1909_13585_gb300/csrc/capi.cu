@@ -58,6 +58,7 @@ int tobk_default_desc(tobk_desc* d) {
   d->element = TOBK_ELEMENT_PLAIN;
   d->eig_gram_tc = 0;
   d->consistent_sens = 0;
+  d->early_fine = 1;
   return TOBK_OK;
 }
 

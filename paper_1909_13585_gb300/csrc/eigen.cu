@@ -241,7 +241,8 @@ static int gram_tc_status(tobk_handle* h) {
 // ------------------------------------------------------------------------------------------------
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info) {
+int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info,
+                EigenHook* hook) {
   cudaStream_t st = h->stream;
   const int64_t n = h->lv[j].g.n;
   const int64_t sd = n;
@@ -386,11 +387,14 @@ int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam
     }
     if (trace) std::fprintf(stderr, "[tobk eig]   worst residual %.3e, unconverged %d\n", worst, (int)sel.size());
     converged = true;
+    bool conv[64];
     for (int i = 0; i < q; ++i) {
       const double res = std::sqrt(h->hscal[128 + i] / std::max(h->hscal[256 + i], 1e-300));
-      if (!(hth[i] > 0.0 && res <= tol)) converged = false;
+      conv[i] = hth[i] > 0.0 && res <= tol;
+      if (!conv[i]) converged = false;
     }
     if (converged) break;
+    if (hook) hook->iteration(X, n, hth.data(), conv, q);
     // ---- expansion block (generalised Davidson): W = M r_s, r_s = -G x_s - theta_s K x_s for the
     // selected Ritz pairs, M = one multigrid V-cycle for K on this level and below
     nadd = (int)sel.size();

@@ -98,6 +98,17 @@ struct tobk_handle {
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int rhs_off = 0;
+  // Early fine solve of the multilevel path (compute_buckling): the fine systems K phi = G P psi of
+  // the coarse modes that have converged while the eigensolver still works on the others run on
+  // stream3, on RHS columns q .. q + early_gmax - 1 of every work buffer (the eigensolver's
+  // preconditioner uses columns 0 .. q - 1): coarse snapshot [early_gmax][n_l], prolongated modes,
+  // right-hand sides and solutions [early_gmax][n]
+  int early_gmax = 0;
+  cudaStream_t stream3 = nullptr;
+  cudaStream_t stream_hi = nullptr, stream_hi2 = nullptr;  // the eigensolve meanwhile (highest priority)
+  cudaEvent_t ev_snap = nullptr, ev_early = nullptr, ev_hi = nullptr;
+  double *ea_psi = nullptr, *ea_Psi = nullptr, *ea_rhs = nullptr, *ea_Phi = nullptr, *ea_scale = nullptr;
+  int la_iters = 0;  // CG iterations of the last linear analysis (sizes the early solve's queue)
   bool solve_only = false;
 
   // kernel-class timing
@@ -140,6 +151,13 @@ LevelOpDesc level_op(tobk_handle* h, int j);
 // host synchronisation or exit check (a preconditioner)
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
               int precision, tobk_solve_info* info, bool fixed_iters = false);
+// Enqueue-only multi-RHS CG at level s on RHS columns [off, off + nr) of every work buffer, on stream st,
+// without host synchronisation: begin (from X0), iteration pairs, end (iterate copied to X).  The
+// kernels deactivate a right-hand side once its recursive residual meets rtol ||b||.
+void cg_async_begin(tobk_handle* h, cudaStream_t st, int off, int s, const double* B, const double* X0, int nr,
+                    double rtol, int precision);
+int cg_async_pairs(tobk_handle* h, cudaStream_t st, int off, int s, int nr, int pairs, int precision);
+void cg_async_end(tobk_handle* h, cudaStream_t st, int off, int s, double* X, int nr);
 int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info);
 int setup_stress(tobk_handle* h);  // Gs from u, Galerkin G down to the eigen level
 int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info);
@@ -149,8 +167,17 @@ int compute_sensitivities(tobk_handle* h, double* dlam, double* dJ, bool out_on_
 constexpr int kCsSize = 2240;
 int consistent_adjoint_rhs(tobk_handle* h, double* g_out, tobk_solve_info* info);
 void launch_sens_consistent(tobk_handle* h, const double* pGp);
+// Called by eigen_solve after the convergence test of every outer iteration that did not finish:
+// X [>= q][n] the current Ritz vectors (device, on the handle's stream; overwritten by the next
+// iteration), theta [>= q] their Ritz values (host, descending; lambda = 1 / theta), conv[i] whether
+// pair i < q meets eig_tol.
+struct EigenHook {
+  virtual ~EigenHook() = default;
+  virtual void iteration(const double* X, int64_t n, const double* theta, const bool* conv, int q) = 0;
+};
 // eigensolver at level j: q lowest positive load factors, modes K_j-normalised -> out [q][n_j]
-int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info);
+int eigen_solve(tobk_handle* h, int j, int q, double* out_modes, double* out_lam_host, tobk_solve_info* info,
+                EigenHook* hook = nullptr);
 // Rayleigh-Ritz projection of (K^j, G^j) on span Psi (q columns, stride n_j; Algorithm 2 'R[Psi]'):
 // Psi is replaced by the K-normalised Ritz vectors, lam_host [q] by their load factors, ascending.
 int ritz_level(tobk_handle* h, int j, int q, double* Psi, double* lam_host);

@@ -135,6 +135,70 @@ static void finalize_modes(tobk_handle* h, const double* A, const double* lam_de
   ::tobk::note_launch(), k_permute_scale<<<dim3(nblk(n), q), 256, 0, st>>>(A, perm, scale, out, n, n);
 }
 
+// Early fine solve (Sec. 2.1 step 3 for part of the modes).  The coarse pairs converge one after the
+// other; once a few of them meet eig_tol, their fine systems K phi = G P psi are started on stream3
+// (RHS columns q.. of the work buffers) while the eigensolver iterates on the rest, so that the FP64-bound
+// fine solve fills the SMs the latency-bound eigensolver leaves idle.  The snapshot of a converged
+// pair is as good an eigenpair as its final iterate (both meet eig_tol).  Pairs are enqueued without
+// host synchronisation, one per further outer iteration; compute_buckling finishes the solve to rtol.
+struct EarlyFine : EigenHook {
+  tobk_handle* h;
+  int l, gmin;
+  bool started = false, failed = false;
+  std::vector<int> S;        // coarse indices solved early
+  std::vector<double> lamS;  // their load factors at the snapshot
+  int pairs = 0;             // iteration pairs enqueued
+  double scale_h[64];
+  EarlyFine(tobk_handle* hh, int level, int q) : h(hh), l(level), gmin(std::max(2, q / 3)) {}
+  void iteration(const double* X, int64_t nl, const double* theta, const bool* conv, int q) override {
+    if (failed) return;
+    cudaStream_t s3 = h->stream3;
+    if (started) {
+      if (cg_async_pairs(h, s3, q, 0, (int)S.size(), 1, h->desc.precision)) failed = true;
+      ++pairs;
+      return;
+    }
+    for (int i = 0; i < q; ++i)
+      if (conv[i] && (int)S.size() < h->early_gmax) S.push_back(i);
+    if ((int)S.size() < gmin) {
+      S.clear();
+      return;
+    }
+    const int g = (int)S.size();
+    const int64_t n = h->lv[0].g.n;
+    for (int k = 0; k < g; ++k) {
+      cudaMemcpyAsync(h->ea_psi + (size_t)k * nl, X + (size_t)S[k] * nl, sizeof(double) * nl,
+                      cudaMemcpyDeviceToDevice, h->stream);
+      lamS.push_back(1.0 / theta[S[k]]);
+      scale_h[k] = -theta[S[k]];  // Phi_0 = -Psi / lambda
+    }
+    cudaEventRecord(h->ev_snap, h->stream);
+    cudaStreamWaitEvent(s3, h->ev_snap, 0);
+    // Psi = P psi through columns q.. of the finer levels' b buffers
+    const double* src = h->ea_psi;
+    for (int j = l; j >= 1; --j) {
+      Level& C = h->lv[j];
+      Level& F = h->lv[j - 1];
+      double* dst = j == 1 ? h->ea_Psi : F.b + (size_t)q * F.g.n;
+      cudaMemsetAsync(dst, 0, sizeof(double) * g * F.g.n, s3);
+      launch_prolong_add(F.g, C.g, F.fixed, src, dst, g, F.g.n, C.g.n, s3);
+      src = dst;
+    }
+    {
+      cudaStream_t s0 = h->stream;
+      h->stream = s3;
+      apply_G_level(h, 0, h->ea_Psi, h->ea_rhs, g, n);
+      h->stream = s0;
+    }
+    cudaMemcpyAsync(h->ea_scale, scale_h, sizeof(double) * g, cudaMemcpyHostToDevice, s3);
+    ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), g), 256, 0, s3>>>(h->ea_Psi, h->ea_scale, h->ea_Phi, n);
+    cg_async_begin(h, s3, q, 0, h->ea_rhs, h->ea_Phi, g, h->desc.rtol, h->desc.precision);
+    if (cg_async_pairs(h, s3, q, 0, g, 2, h->desc.precision)) failed = true;
+    pairs = 2;
+    started = true;
+  }
+};
+
 int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
   if (!h->have_u || !h->have_G) return fail(h, TOBK_E_STATE, "solve_equilibrium must come first");
   cudaStream_t st = h->stream;
@@ -168,7 +232,53 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     // Sec. 2.1 step 1: coarse eigenpairs on Omega_l of the Galerkin pencil
     const int l = h->eig;
     double* Psi = h->lv[l].b;
-    rc = eigen_solve(h, l, q, Psi, lam_h, &ei);
+    const bool plain_steps =
+        h->desc.kaczmarz_sweeps == 0 && !h->desc.ritz_levels && std::max(1, h->desc.fine_steps) == 1;
+    const bool use_early = h->early_gmax > 0 && h->stream3 != nullptr && st != nullptr && h->use_graphs &&
+                           !h->prof_on && plain_steps;
+    EarlyFine early(h, l, q);
+    if (use_early) {
+      // the eigensolve on the handle's highest-priority stream pair, forked from and joined back to the
+      // caller's stream, so that its short kernels are scheduled ahead of the early fine solve's
+      cudaEventRecord(h->ev_hi, st);
+      cudaStreamWaitEvent(h->stream_hi, h->ev_hi, 0);
+      h->stream = h->stream_hi;
+      std::swap(h->stream2, h->stream_hi2);
+      rc = eigen_solve(h, l, q, Psi, lam_h, &ei, &early);
+      std::swap(h->stream2, h->stream_hi2);
+      h->stream = st;
+      cudaEventRecord(h->ev_hi, h->stream_hi);
+      cudaStreamWaitEvent(st, h->ev_hi, 0);
+    } else {
+      rc = eigen_solve(h, l, q, Psi, lam_h, &ei, nullptr);
+    }
+    std::vector<int> S;  // coarse modes whose fine solve ran early (kept if they are still the same pairs)
+    if (early.started) {
+      const int g = (int)early.S.size();
+      // pairs up to the linear analysis' iteration count of this design (the fine systems share its
+      // operator); the finishing solve below takes any that remain
+      const int want = std::max(h->la_iters > 0 ? (h->la_iters + 1) / 2 : 16, early.pairs);
+      if (!early.failed && want > early.pairs &&
+          cg_async_pairs(h, h->stream3, q, 0, g, want - early.pairs, h->desc.precision))
+        early.failed = true;
+      cg_async_end(h, h->stream3, q, 0, h->ea_Phi, g);
+      cudaEventRecord(h->ev_early, h->stream3);
+      bool same = rc == TOBK_OK && !early.failed;
+      for (int k = 0; k < g && same; ++k) {
+        const double a = lam_h[early.S[k]], b = early.lamS[k];
+        same = std::fabs(a - b) <= 1e-9 * std::fabs(b);
+      }
+      if (same) {
+        S = early.S;
+        for (int k = 0; k < g; ++k) {  // the pairs the early solve started from
+          cudaMemcpyAsync(Psi + (size_t)S[k] * h->lv[l].g.n, h->ea_psi + (size_t)k * h->lv[l].g.n,
+                          sizeof(double) * h->lv[l].g.n, cudaMemcpyDeviceToDevice, st);
+          lam_h[S[k]] = early.lamS[k];
+        }
+      } else {
+        cudaStreamWaitEvent(st, h->ev_early, 0);  // its buffers are free again after this point
+      }
+    }
     if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
     m_eig = pm.mark();
     if (h->cs_psi) {  // the coarse pairs, for the consistent sensitivities
@@ -215,7 +325,50 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     const double* src = h->lv[0].b;
     double* rhs = h->bwork;
     double* Phi = h->xwork;
-    for (int stp = 0; stp < steps; ++stp) {
+    if (!S.empty()) {
+      // the modes not solved early (compact in xwork / bwork), beside the early solve's last pairs
+      std::vector<int> B;
+      for (int i = 0; i < q; ++i)
+        if (std::find(S.begin(), S.end(), i) == S.end()) B.push_back(i);
+      const int nbq = (int)B.size(), g = (int)S.size();
+      double s_h[64];
+      for (int k = 0; k < nbq; ++k) {
+        cudaMemcpyAsync(h->xwork + (size_t)k * n, src + (size_t)B[k] * n, sizeof(double) * n,
+                        cudaMemcpyDeviceToDevice, st);
+        const double lb = lam_h[B[k]];
+        s_h[k] = (lb > 0.0 && std::isfinite(lb)) ? -1.0 / lb : 0.0;
+      }
+      apply_G_level(h, 0, h->xwork, h->bwork, nbq, n);
+      cudaMemcpyAsync(den, s_h, sizeof(double) * nbq, cudaMemcpyHostToDevice, st);
+      ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), nbq), 256, 0, st>>>(h->xwork, den, h->xwork, n);
+      m_prolong = pm.mark();
+      tobk_solve_info sb{}, sa{};
+      int brc = pcg_solve(h, 0, h->bwork, h->xwork, nbq, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &sb);
+      if (brc && brc != TOBK_E_NOT_CONVERGED) return brc;
+      // the early modes: their iterate, finished to rtol on the handle's stream
+      cudaStreamWaitEvent(st, h->ev_early, 0);
+      int arc = pcg_solve(h, 0, h->ea_rhs, h->ea_Phi, g, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &sa);
+      if (arc && arc != TOBK_E_NOT_CONVERGED) return arc;
+      ei.iterations += std::max(sb.iterations, 2 * early.pairs + sa.iterations);
+      m_solve = pm.mark();
+      // Phi in the coarse modes' order
+      Phi = h->bwork;
+      for (int k = 0; k < g; ++k)
+        cudaMemcpyAsync(Phi + (size_t)S[k] * n, h->ea_Phi + (size_t)k * n, sizeof(double) * n,
+                        cudaMemcpyDeviceToDevice, st);
+      for (int k = 0; k < nbq; ++k)
+        cudaMemcpyAsync(Phi + (size_t)B[k] * n, h->xwork + (size_t)k * n, sizeof(double) * n,
+                        cudaMemcpyDeviceToDevice, st);
+      double* KP = h->lv[0].z;
+      double* GP = h->lv[0].t;
+      apply_K_level(h, 0, Phi, KP, q, n);
+      apply_G_level(h, 0, Phi, GP, q, n);
+      launch_coldots(Phi, KP, q, n, n, num, h->gram_partial, st);
+      launch_coldots(Phi, GP, q, n, n, den, h->gram_partial, st);
+      ::tobk::note_launch(), k_rq<<<1, 64, 0, st>>>(num, den, q, lraw);
+      finalize_modes(h, Phi, lraw, num, h->modes, h->lam);
+    }
+    for (int stp = 0; stp < (S.empty() ? steps : 0); ++stp) {
       if (stp > 0) {  // the previous step's normalised modes and load factors
         src = h->modes;
         cudaMemcpyAsync(h->hscal, h->lam, sizeof(double) * q, cudaMemcpyDeviceToHost, st);

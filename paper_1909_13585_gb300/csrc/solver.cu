@@ -206,6 +206,15 @@ static void layout(tobk_handle* h, Arena& a) {
     h->gtc_nmax = std::max(ne, nf);
     h->gtc_err = a.take<unsigned>(2);
   }
+  if (h->early_gmax > 0) {
+    const int64_t nl = h->lv[h->eig].g.n;
+    const int ge = h->early_gmax;
+    h->ea_psi = a.take<double>((size_t)ge * nl);
+    h->ea_Psi = a.take<double>((size_t)ge * nf);
+    h->ea_rhs = a.take<double>((size_t)ge * nf);
+    h->ea_Phi = a.take<double>((size_t)ge * nf);
+    h->ea_scale = a.take<double>(64);
+  }
   if (h->desc.consistent_sens && h->eig > 0) {
     const int64_t nl = h->lv[h->eig].g.n;
     for (double** v : {&h->cs_psi, &h->cs_Kpsi, &h->cs_b, &h->cs_c, &h->cs_r, &h->cs_r0, &h->cs_z, &h->cs_p,
@@ -262,6 +271,14 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   h->eig_nb = h->q;  // block = wanted pairs: as few iterations as q + 2 or q + 4 (measured), less work each
   h->eig_mmax = 64;
   h->rmax = std::max({d->max_rhs, h->eig_nb, h->q + 1, 1});
+  // Sec. 2.1 steps 1-4 as they stand: columns beside the eigensolver's for the early fine solve
+  if (d->early_fine != 0 && d->early_fine != 1) return TOBK_E_ARG;
+  if (!solve_only && d->early_fine && d->eig_level > 1 && d->kaczmarz_sweeps == 0 && !d->ritz_levels &&
+      d->fine_steps <= 1 && stream != nullptr) {
+    const int want = std::max(2, h->q / 2);
+    h->rmax = std::max(h->rmax, std::min(kMaxRhs, h->q + want));
+    h->early_gmax = std::min(want, h->rmax - h->q);
+  }
   if (h->rmax > kMaxRhs || h->eig_mmax < 2 * h->eig_nb) {
     delete h;
     return TOBK_E_ARG;
@@ -306,6 +323,19 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
     destroy_handle(h);
     return TOBK_E_CUDA;
   }
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (h->early_gmax > 0 &&
+      (cudaStreamCreateWithPriority(&h->stream3, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+       cudaStreamCreateWithPriority(&h->stream_hi, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+       cudaStreamCreateWithPriority(&h->stream_hi2, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+       cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&h->ev_early, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&h->ev_hi, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    destroy_handle(h);
+    return TOBK_E_CUDA;
+  }
   cudaStream_t s = h->stream;
   cudaMemsetAsync(h->arena.base, 0, bytes, s);
   cudaMemcpyAsync(h->d_Ke0, h->tab.Ke0.data(), sizeof(double) * h->tab.Ke0.size(), cudaMemcpyHostToDevice, s);
@@ -330,6 +360,18 @@ void destroy_handle(tobk_handle* h) {
     cudaStreamSynchronize(h->stream2);
     cudaStreamDestroy(h->stream2);
   }
+  if (h->stream3) {
+    cudaStreamSynchronize(h->stream3);
+    cudaStreamDestroy(h->stream3);
+  }
+  for (cudaStream_t* sp : {&h->stream_hi, &h->stream_hi2})
+    if (*sp) {
+      cudaStreamSynchronize(*sp);
+      cudaStreamDestroy(*sp);
+    }
+  if (h->ev_hi) cudaEventDestroy(h->ev_hi);
+  if (h->ev_snap) cudaEventDestroy(h->ev_snap);
+  if (h->ev_early) cudaEventDestroy(h->ev_early);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto& p : h->prof_pending) {
@@ -835,6 +877,34 @@ static int run_cg_pair_halves(tobk_handle* h, int s, int nr, int n0, int precisi
   return rc;
 }
 
+void cg_async_begin(tobk_handle* h, cudaStream_t st, int off, int s, const double* B, const double* X0, int nr,
+                    double rtol, int precision) {
+  HalfScope hs(h, st, off);
+  const LevelOpDesc op = level_op(h, s);
+  const int64_t n = op.g.n;
+  const CGWork w = cgw(h, n);
+  cudaMemcpyAsync(w.x, X0, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, st);
+  launch_cg_init(op, B, w.x, w.r, true, rtol, nr, n, w.sc, w.partial, w.counters, st, cg_z0(h, s, precision));
+  cudaMemsetAsync(w.p0, 0, sizeof(double) * nr * n, st);
+  cudaMemsetAsync(w.q, 0, sizeof(double) * nr * n, st);
+}
+
+int cg_async_pairs(tobk_handle* h, cudaStream_t st, int off, int s, int nr, int pairs, int precision) {
+  HalfScope hs(h, st, off);
+  for (int k = 0; k < pairs; ++k) {
+    const int rc = run_cg_pair(h, s, nr, precision);
+    if (rc) return rc;
+  }
+  return TOBK_OK;
+}
+
+void cg_async_end(tobk_handle* h, cudaStream_t st, int off, int s, double* X, int nr) {
+  HalfScope hs(h, st, off);
+  const int64_t n = h->lv[s].g.n;
+  const CGWork w = cgw(h, n);
+  cudaMemcpyAsync(X, w.x, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, st);
+}
+
 int pcg_solve(tobk_handle* h, int s, const double* B, double* X, int nr, double rtol, int max_iter, bool use_x0,
               int precision, tobk_solve_info* info, bool fixed_iters) {
   if (nr < 1 || nr > h->rmax) return fail(h, TOBK_E_ARG, "bad RHS count");
@@ -1020,8 +1090,11 @@ int solve_equilibrium(tobk_handle* h, double* compliance, tobk_solve_info* info)
     launch_gram(h->u, 1, h->xwork, 1, n, n, h->dscal + 961, h->gram_partial, s);
     ::tobk::note_launch(), k_energy_scale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->u, n, h->dscal + 960);
   }
-  int rc = pcg_solve(h, 0, h->bwork, h->u, 1, h->desc.rtol, h->desc.max_iter, h->have_u0, h->desc.precision, info);
+  tobk_solve_info li{};
+  int rc = pcg_solve(h, 0, h->bwork, h->u, 1, h->desc.rtol, h->desc.max_iter, h->have_u0, h->desc.precision,
+                     info ? info : &li);
   if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
+  h->la_iters = (info ? info : &li)->iterations;
   launch_gram(h->bwork, 1, h->u, 1, n, n, h->dscal, h->gram_partial, s);
   cudaMemcpyAsync(h->hscal, h->dscal, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);

@@ -159,7 +159,9 @@ def test_consistent_sensitivities_graph_replay_is_bit_identical():
     p = CASES[0][1]()
     out = []
     for stream in (None, torch.cuda.Stream()):
-        s = pkg.Solver(p, stream=stream, consistent_sens=1)
+        # early_fine = 0: the fine solves after the eigensolve on both streams (the legacy stream has no
+        # second stream to start them on)
+        s = pkg.Solver(p, stream=stream, consistent_sens=1, early_fine=0)
         s.solve_equilibrium()
         s.compute_buckling()
         for _ in range(2):  # the second call replays the graph captured by the first
@@ -169,3 +171,26 @@ def test_consistent_sensitivities_graph_replay_is_bit_identical():
         s.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] > 0
+
+
+def test_consistent_sensitivities_with_the_early_fine_solve_match_oracle():
+    """On a caller's stream the early fine solve supplies part of the modes (their coarse pairs taken
+    when they met eig_tol); the consistent derivative then follows those pairs and still matches the
+    oracle within 1e-5."""
+    torch, pkg = require_gpu()
+    p = CASES[0][1]()
+    s = pkg.Solver(p, stream=torch.cuda.Stream(), consistent_sens=1)
+    s.solve_equilibrium()
+    lam, _ = s.compute_buckling()
+    dlam, _, info = s.compute_sensitivities()
+    torch.cuda.synchronize()
+    s.close()
+    assert info["converged"] == 1
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    dl_o, aux = consistent.consistent_sensitivities(op, u, p.num_modes, p.eig_level)
+    ok = (_gaps(aux["lam"]) > 1e-4) & (_gaps(np.sort(aux["mu"])) > 1e-4)
+    assert ok.sum() >= p.num_modes - 1
+    assert np.allclose(lam[ok], aux["lam"][ok], rtol=1e-6, atol=0)
+    for i in np.flatnonzero(ok):
+        assert rel_err(dlam[i], dl_o[i]) < 1e-5, (i, rel_err(dlam[i], dl_o[i]))
