@@ -100,13 +100,15 @@ struct tobk_handle {
   int rhs_off = 0;
   // Early fine solve of the multilevel path (compute_buckling): the fine systems K phi = G P psi of
   // the coarse modes that have converged while the eigensolver still works on the others run on
-  // stream3, on RHS columns q .. q + early_gmax - 1 of every work buffer (the eigensolver's
+  // streams of their own, on RHS columns q .. q + early_gmax - 1 of every work buffer (the eigensolver's
   // preconditioner uses columns 0 .. q - 1): coarse snapshot [early_gmax][n_l], prolongated modes,
   // right-hand sides and solutions [early_gmax][n]
   int early_gmax = 0;
-  cudaStream_t stream3 = nullptr;
+  static constexpr int kEarlyStreams = 4;  // groups of early modes take these in turn (lowest priority)
+  cudaStream_t stream3[kEarlyStreams] = {};
+  cudaEvent_t ev_early[kEarlyStreams] = {};
   cudaStream_t stream_hi = nullptr, stream_hi2 = nullptr;  // the eigensolve meanwhile (highest priority)
-  cudaEvent_t ev_snap = nullptr, ev_early = nullptr, ev_hi = nullptr;
+  cudaEvent_t ev_snap = nullptr, ev_hi = nullptr;
   double *ea_psi = nullptr, *ea_Psi = nullptr, *ea_rhs = nullptr, *ea_Phi = nullptr, *ea_scale = nullptr;
   int la_iters = 0;  // CG iterations of the last linear analysis (sizes the early solve's queue)
   bool solve_only = false;

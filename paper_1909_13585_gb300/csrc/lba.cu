@@ -136,50 +136,64 @@ static void finalize_modes(tobk_handle* h, const double* A, const double* lam_de
 }
 
 // Early fine solve (Sec. 2.1 step 3 for part of the modes).  The coarse pairs converge one after the
-// other; once a few of them meet eig_tol, their fine systems K phi = G P psi are started on stream3
-// (RHS columns q.. of the work buffers) while the eigensolver iterates on the rest, so that the FP64-bound
-// fine solve fills the SMs the latency-bound eigensolver leaves idle.  The snapshot of a converged
-// pair is as good an eigenpair as its final iterate (both meet eig_tol).  Pairs are enqueued without
-// host synchronisation, one per further outer iteration; compute_buckling finishes the solve to rtol.
+// other; whenever a few more of them meet eig_tol, their fine systems K phi = G P psi are started as a
+// group on a stream of its own (and its own RHS columns q + c0 .. of the work buffers) while the
+// eigensolver iterates on the rest, so that the FP64-bound fine solves fill the SMs the latency-bound
+// eigensolver leaves idle.  The snapshot of a converged pair is as good an eigenpair as its final
+// iterate (both meet eig_tol).  Iteration pairs are enqueued without host synchronisation, one per
+// group and further outer iteration; compute_buckling finishes the solves to rtol.
 struct EarlyFine : EigenHook {
+  struct Group {
+    int c0 = 0, pairs = 0;
+    cudaStream_t st = nullptr;
+    bool failed = false;
+    std::vector<int> S;        // coarse indices
+    std::vector<double> lam;   // their load factors at the snapshot
+  };
   tobk_handle* h;
-  int l, gmin;
-  bool started = false, failed = false;
-  std::vector<int> S;        // coarse indices solved early
-  std::vector<double> lamS;  // their load factors at the snapshot
-  int pairs = 0;             // iteration pairs enqueued
+  int l, gnew, used = 0;
+  std::vector<Group> groups;
+  std::vector<char> taken;
   double scale_h[64];
-  EarlyFine(tobk_handle* hh, int level, int q) : h(hh), l(level), gmin(std::max(2, q / 3)) {}
+  EarlyFine(tobk_handle* hh, int level, int q) : h(hh), l(level), gnew(std::max(2, q / 4)), taken(q, 0) {}
   void iteration(const double* X, int64_t nl, const double* theta, const bool* conv, int q) override {
-    if (failed) return;
-    cudaStream_t s3 = h->stream3;
-    if (started) {
-      if (cg_async_pairs(h, s3, q, 0, (int)S.size(), 1, h->desc.precision)) failed = true;
-      ++pairs;
-      return;
+    for (Group& G : groups) {
+      if (G.failed) continue;
+      if (cg_async_pairs(h, G.st, q + G.c0, 0, (int)G.S.size(), 1, h->desc.precision)) G.failed = true;
+      ++G.pairs;
     }
+    std::vector<int> idx;
     for (int i = 0; i < q; ++i)
-      if (conv[i] && (int)S.size() < h->early_gmax) S.push_back(i);
-    if ((int)S.size() < gmin) {
-      S.clear();
-      return;
-    }
-    const int g = (int)S.size();
+      if (conv[i] && !taken[i]) idx.push_back(i);
+    const int room = h->early_gmax - used;
+    if ((int)idx.size() < gnew || room < gnew) return;
+    if ((int)idx.size() > room) idx.resize(room);
+    Group G;
+    G.c0 = used;
+    G.S = idx;
+    G.st = h->stream3[groups.size() % tobk_handle::kEarlyStreams];
+    cudaStream_t s3 = G.st;
+    const int g = (int)idx.size();
     const int64_t n = h->lv[0].g.n;
     for (int k = 0; k < g; ++k) {
-      cudaMemcpyAsync(h->ea_psi + (size_t)k * nl, X + (size_t)S[k] * nl, sizeof(double) * nl,
+      taken[idx[k]] = 1;
+      cudaMemcpyAsync(h->ea_psi + (size_t)(G.c0 + k) * nl, X + (size_t)idx[k] * nl, sizeof(double) * nl,
                       cudaMemcpyDeviceToDevice, h->stream);
-      lamS.push_back(1.0 / theta[S[k]]);
-      scale_h[k] = -theta[S[k]];  // Phi_0 = -Psi / lambda
+      G.lam.push_back(1.0 / theta[idx[k]]);
+      scale_h[k] = -theta[idx[k]];  // Phi_0 = -Psi / lambda
     }
+    used += g;
     cudaEventRecord(h->ev_snap, h->stream);
     cudaStreamWaitEvent(s3, h->ev_snap, 0);
-    // Psi = P psi through columns q.. of the finer levels' b buffers
-    const double* src = h->ea_psi;
+    // Psi = P psi through the group's columns of the finer levels' b buffers
+    const double* src = h->ea_psi + (size_t)G.c0 * nl;
+    double* Psi = h->ea_Psi + (size_t)G.c0 * n;
+    double* rhs = h->ea_rhs + (size_t)G.c0 * n;
+    double* Phi = h->ea_Phi + (size_t)G.c0 * n;
     for (int j = l; j >= 1; --j) {
       Level& C = h->lv[j];
       Level& F = h->lv[j - 1];
-      double* dst = j == 1 ? h->ea_Psi : F.b + (size_t)q * F.g.n;
+      double* dst = j == 1 ? Psi : F.b + (size_t)(q + G.c0) * F.g.n;
       cudaMemsetAsync(dst, 0, sizeof(double) * g * F.g.n, s3);
       launch_prolong_add(F.g, C.g, F.fixed, src, dst, g, F.g.n, C.g.n, s3);
       src = dst;
@@ -187,15 +201,15 @@ struct EarlyFine : EigenHook {
     {
       cudaStream_t s0 = h->stream;
       h->stream = s3;
-      apply_G_level(h, 0, h->ea_Psi, h->ea_rhs, g, n);
+      apply_G_level(h, 0, Psi, rhs, g, n);
       h->stream = s0;
     }
-    cudaMemcpyAsync(h->ea_scale, scale_h, sizeof(double) * g, cudaMemcpyHostToDevice, s3);
-    ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), g), 256, 0, s3>>>(h->ea_Psi, h->ea_scale, h->ea_Phi, n);
-    cg_async_begin(h, s3, q, 0, h->ea_rhs, h->ea_Phi, g, h->desc.rtol, h->desc.precision);
-    if (cg_async_pairs(h, s3, q, 0, g, 2, h->desc.precision)) failed = true;
-    pairs = 2;
-    started = true;
+    cudaMemcpyAsync(h->ea_scale + G.c0, scale_h, sizeof(double) * g, cudaMemcpyHostToDevice, s3);
+    ::tobk::note_launch(), k_scale_cols<<<dim3(nblk(n), g), 256, 0, s3>>>(Psi, h->ea_scale + G.c0, Phi, n);
+    cg_async_begin(h, s3, q + G.c0, 0, rhs, Phi, g, h->desc.rtol, h->desc.precision);
+    if (cg_async_pairs(h, s3, q + G.c0, 0, g, 2, h->desc.precision)) G.failed = true;
+    G.pairs = 2;
+    groups.push_back(G);
   }
 };
 
@@ -234,7 +248,7 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     double* Psi = h->lv[l].b;
     const bool plain_steps =
         h->desc.kaczmarz_sweeps == 0 && !h->desc.ritz_levels && std::max(1, h->desc.fine_steps) == 1;
-    const bool use_early = h->early_gmax > 0 && h->stream3 != nullptr && st != nullptr && h->use_graphs &&
+    const bool use_early = h->early_gmax > 0 && h->stream3[0] != nullptr && st != nullptr && h->use_graphs &&
                            !h->prof_on && plain_steps;
     EarlyFine early(h, l, q);
     if (use_early) {
@@ -252,32 +266,40 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
     } else {
       rc = eigen_solve(h, l, q, Psi, lam_h, &ei, nullptr);
     }
-    std::vector<int> S;  // coarse modes whose fine solve ran early (kept if they are still the same pairs)
-    if (early.started) {
-      const int g = (int)early.S.size();
+    std::vector<int> S;  // coarse modes whose fine solve ran early (kept if they are still the same pairs),
+                         // their iterates compacted to columns 0 .. |S| - 1 of ea_rhs / ea_Phi
+    std::vector<int> Scol;  // the early column of each kept mode before compaction
+    if (!early.groups.empty()) {
+      const int64_t n0 = h->lv[0].g.n, nl = h->lv[l].g.n;
       // pairs up to the linear analysis' iteration count of this design (the fine systems share its
       // operator); the finishing solve below takes any that remain
-      const int want = std::max(h->la_iters > 0 ? (h->la_iters + 1) / 2 : 16, early.pairs);
-      if (!early.failed && want > early.pairs &&
-          cg_async_pairs(h, h->stream3, q, 0, g, want - early.pairs, h->desc.precision))
-        early.failed = true;
-      cg_async_end(h, h->stream3, q, 0, h->ea_Phi, g);
-      cudaEventRecord(h->ev_early, h->stream3);
-      bool same = rc == TOBK_OK && !early.failed;
-      for (int k = 0; k < g && same; ++k) {
-        const double a = lam_h[early.S[k]], b = early.lamS[k];
-        same = std::fabs(a - b) <= 1e-9 * std::fabs(b);
+      const int want = h->la_iters > 0 ? (h->la_iters + 1) / 2 : 16;
+      for (auto& G : early.groups) {
+        const int g = (int)G.S.size();
+        if (!G.failed && want > G.pairs &&
+            cg_async_pairs(h, G.st, q + G.c0, 0, g, want - G.pairs, h->desc.precision))
+          G.failed = true;
+        cg_async_end(h, G.st, q + G.c0, 0, h->ea_Phi + (size_t)G.c0 * n0, g);
       }
-      if (same) {
-        S = early.S;
-        for (int k = 0; k < g; ++k) {  // the pairs the early solve started from
-          cudaMemcpyAsync(Psi + (size_t)S[k] * h->lv[l].g.n, h->ea_psi + (size_t)k * h->lv[l].g.n,
-                          sizeof(double) * h->lv[l].g.n, cudaMemcpyDeviceToDevice, st);
-          lam_h[S[k]] = early.lamS[k];
+      for (int k = 0; k < tobk_handle::kEarlyStreams; ++k) cudaEventRecord(h->ev_early[k], h->stream3[k]);
+      for (auto& G : early.groups) {
+        bool same = rc == TOBK_OK && !G.failed;
+        for (size_t k = 0; k < G.S.size() && same; ++k) {
+          const double a = lam_h[G.S[k]], b = G.lam[k];
+          same = std::fabs(a - b) <= 1e-9 * std::fabs(b);
         }
-      } else {
-        cudaStreamWaitEvent(st, h->ev_early, 0);  // its buffers are free again after this point
+        if (!same) continue;
+        for (size_t k = 0; k < G.S.size(); ++k) {  // the pairs the early solve started from
+          const int i = G.S[k];
+          cudaMemcpyAsync(Psi + (size_t)i * nl, h->ea_psi + (size_t)(G.c0 + k) * nl, sizeof(double) * nl,
+                          cudaMemcpyDeviceToDevice, st);
+          lam_h[i] = G.lam[k];
+          S.push_back(i);
+          Scol.push_back(G.c0 + (int)k);
+        }
       }
+      if (S.empty())  // the early solves' buffers are free again after this point
+        for (int k = 0; k < tobk_handle::kEarlyStreams; ++k) cudaStreamWaitEvent(st, h->ev_early[k], 0);
     }
     if (rc && rc != TOBK_E_NOT_CONVERGED) return rc;
     m_eig = pm.mark();
@@ -345,11 +367,20 @@ int compute_buckling(tobk_handle* h, double* lambda, tobk_solve_info* info) {
       tobk_solve_info sb{}, sa{};
       int brc = pcg_solve(h, 0, h->bwork, h->xwork, nbq, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &sb);
       if (brc && brc != TOBK_E_NOT_CONVERGED) return brc;
-      // the early modes: their iterate, finished to rtol on the handle's stream
-      cudaStreamWaitEvent(st, h->ev_early, 0);
+      // the early modes: their iterates (compacted, in the order of S), finished to rtol on the handle's stream
+      for (int k = 0; k < tobk_handle::kEarlyStreams; ++k) cudaStreamWaitEvent(st, h->ev_early[k], 0);
+      int early_pairs = 0;
+      for (auto& G : early.groups) early_pairs = std::max(early_pairs, G.pairs);
+      for (int k = 0; k < g; ++k)
+        if (Scol[k] != k) {  // Scol is increasing, so a column is moved only down onto a free one
+          cudaMemcpyAsync(h->ea_rhs + (size_t)k * n, h->ea_rhs + (size_t)Scol[k] * n, sizeof(double) * n,
+                          cudaMemcpyDeviceToDevice, st);
+          cudaMemcpyAsync(h->ea_Phi + (size_t)k * n, h->ea_Phi + (size_t)Scol[k] * n, sizeof(double) * n,
+                          cudaMemcpyDeviceToDevice, st);
+        }
       int arc = pcg_solve(h, 0, h->ea_rhs, h->ea_Phi, g, h->desc.rtol, h->desc.max_iter, true, h->desc.precision, &sa);
       if (arc && arc != TOBK_E_NOT_CONVERGED) return arc;
-      ei.iterations += std::max(sb.iterations, 2 * early.pairs + sa.iterations);
+      ei.iterations += std::max(sb.iterations, 2 * early_pairs + sa.iterations);
       m_solve = pm.mark();
       // Phi in the coarse modes' order
       Phi = h->bwork;

@@ -275,7 +275,7 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   if (d->early_fine != 0 && d->early_fine != 1) return TOBK_E_ARG;
   if (!solve_only && d->early_fine && d->eig_level > 1 && d->kaczmarz_sweeps == 0 && !d->ritz_levels &&
       d->fine_steps <= 1 && stream != nullptr) {
-    const int want = std::max(2, h->q / 2);
+    const int want = std::max(2, h->q - 1);
     h->rmax = std::max(h->rmax, std::min(kMaxRhs, h->q + want));
     h->early_gmax = std::min(want, h->rmax - h->q);
   }
@@ -325,13 +325,19 @@ int create_handle(const tobk_desc* d, void* stream, tobk_handle** out, bool solv
   }
   int prio_low = 0, prio_high = 0;
   cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
-  if (h->early_gmax > 0 &&
-      (cudaStreamCreateWithPriority(&h->stream3, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
-       cudaStreamCreateWithPriority(&h->stream_hi, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
-       cudaStreamCreateWithPriority(&h->stream_hi2, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
-       cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
-       cudaEventCreateWithFlags(&h->ev_early, cudaEventDisableTiming) != cudaSuccess ||
-       cudaEventCreateWithFlags(&h->ev_hi, cudaEventDisableTiming) != cudaSuccess)) {
+  bool early_ok = true;
+  if (h->early_gmax > 0) {
+    for (int k = 0; k < tobk_handle::kEarlyStreams; ++k)
+      early_ok = early_ok &&
+                 cudaStreamCreateWithPriority(&h->stream3[k], cudaStreamNonBlocking, prio_low) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_early[k], cudaEventDisableTiming) == cudaSuccess;
+    early_ok = early_ok &&
+               cudaStreamCreateWithPriority(&h->stream_hi, cudaStreamNonBlocking, prio_high) == cudaSuccess &&
+               cudaStreamCreateWithPriority(&h->stream_hi2, cudaStreamNonBlocking, prio_high) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_hi, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!early_ok) {
     cudaGetLastError();
     destroy_handle(h);
     return TOBK_E_CUDA;
@@ -360,9 +366,12 @@ void destroy_handle(tobk_handle* h) {
     cudaStreamSynchronize(h->stream2);
     cudaStreamDestroy(h->stream2);
   }
-  if (h->stream3) {
-    cudaStreamSynchronize(h->stream3);
-    cudaStreamDestroy(h->stream3);
+  for (int k = 0; k < tobk_handle::kEarlyStreams; ++k) {
+    if (h->stream3[k]) {
+      cudaStreamSynchronize(h->stream3[k]);
+      cudaStreamDestroy(h->stream3[k]);
+    }
+    if (h->ev_early[k]) cudaEventDestroy(h->ev_early[k]);
   }
   for (cudaStream_t* sp : {&h->stream_hi, &h->stream_hi2})
     if (*sp) {
@@ -371,7 +380,6 @@ void destroy_handle(tobk_handle* h) {
     }
   if (h->ev_hi) cudaEventDestroy(h->ev_hi);
   if (h->ev_snap) cudaEventDestroy(h->ev_snap);
-  if (h->ev_early) cudaEventDestroy(h->ev_early);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto& p : h->prof_pending) {
