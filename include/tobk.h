@@ -133,7 +133,8 @@ typedef struct {
   int early_fine;    /* 1 (default): on the multilevel path of Sec. 2.1 (no Kaczmarz sweeps, Ritz projections
                         or extra fine steps) and on a stream of the caller's, the fine systems K phi =
                         G P psi of the coarse pairs that meet eig_tol while the eigensolver still iterates
-                        on others are solved beside it (a second stream, the same rtol); 0: all q after
+                        on others are solved beside it, in groups on streams of the handle's own, to the
+                        same rtol (the handle then holds 2q - 1 RHS columns of work space); 0: all q after
                         the eigensolve.  The load factors agree to the solver tolerances, not bit for bit */
 } tobk_desc;
 
