@@ -131,3 +131,50 @@ def test_exact_pairs_reduce_to_sensitivity_lambda():
     assert np.allclose(aux["lam"], lam, rtol=1e-10)
     assert np.abs(aux["W"]).max() <= 1e-8 * np.abs(aux["Phi"]).max()
     assert np.allclose(dl, ref, rtol=0, atol=1e-7 * np.abs(ref).max())
+
+
+def test_printed_formula_pin_rejects_a_wrong_adjoint():
+    """The agreement of the printed eq. consistentSensitivity with the adjoint chain depends on its
+    adjoint p = -2 (K + lambda G)^{-1} y: the opposite sign of p, or dropping the factor
+    1 / (1 - p^T G phi), misses the derivative by far more than the 1e-8 the correct form meets."""
+    p, q, L = _case("2d_l2")
+    op = lba.Problem(p)
+    u, _ = lba.linear_analysis(op)
+    dl, aux = consistent.consistent_sensitivities(op, u, q, L)
+    mp = consistent.multilevel_pairs(op, u, q, L)
+    order = aux["order"]
+    e = 5
+    _, dY, _ = consistent.forward_derivative(op, u, mp, e)
+    scale = np.abs(dl).max(axis=1)
+    good = consistent.paper_formula(op, u, mp, e, dY)
+    assert np.all(np.abs(good[order] - dl[:, e]) <= 1e-8 * scale)
+    # the same formula written out here with the two plausible slips
+    Gf, Kf = mp["Gf"], op.Kf
+    worst_sign = worst_factor = 0.0
+    x = np.asarray(p.x, dtype=np.float64)
+    from oracle import elements
+    _, _, dEk, dEs = elements.simp(x, p.penal, p.E0, p.Emin)
+    Ke0 = elements.stiffness_ke0(p.dim, p.nu)
+    Ge = assembly.element_stress_stiffness(p.nel, p.dim, u, p.nu)
+    dK = dEk[e] * consistent._element_operator(op, e, Ke0)
+    dGx = dEs[e] * consistent._element_operator(op, e, Ge[e])
+    du = op.to_full(-op.solve(dK @ np.asarray(u)[op.free]))
+    dG = dGx + assembly.restrict_free(op.G(du), op.fixed)
+    uf = np.asarray(u)[op.free]
+    for r in range(q):
+        i = order[r]
+        lam = mp["lam"][i]
+        s = np.sqrt(-(mp["Phi"][:, i] @ (Gf @ mp["Phi"][:, i])))
+        ph = mp["Phi"][:, i] / s
+        y = Kf @ ph + lam * (Gf @ ph)
+        dy = dY[:, i] / s
+        phf = op.to_full(ph)
+        z = op.solve(consistent.adjoint_rhs_pair(p.nel, p.dim, x, phf, phf, p.nu, p.penal, p.E0, p.Emin)[op.free])
+        first = ph @ ((dK + lam * dGx) @ ph) - lam * (z @ (dK @ uf))
+        pv = -2.0 * np.linalg.solve((Kf + lam * Gf).toarray(), y)
+        core = first + pv @ ((dK + lam * dG) @ ph) - pv @ dy
+        assert abs(core / (1.0 - pv @ (Gf @ ph)) - dl[r, e]) <= 1e-8 * scale[r]
+        wrong_sign = (first - pv @ ((dK + lam * dG) @ ph) + pv @ dy) / (1.0 + pv @ (Gf @ ph))
+        worst_sign = max(worst_sign, abs(wrong_sign - dl[r, e]) / scale[r])
+        worst_factor = max(worst_factor, abs(core - dl[r, e]) / scale[r])
+    assert worst_sign > 1e-3 and worst_factor > 1e-3, (worst_sign, worst_factor)
